@@ -1,0 +1,346 @@
+"""Benchmark: 2-D DWT by non-separable lifting on one GB300 (and N replicas under torchrun).
+
+Workload: one 8192 x 8192 seeded 1/f^2 field in [0, 255], 5 decomposition levels.  The headline
+value is the forward CDF 9/7 (fp32) transform in Gpixel/s (level-0 pixels per second); the same
+line carries the reversible integer CDF 5/3 forward, both inverses and the separable-lifting
+comparators (one-pass Eq. 3 steps and the two-pass row/column transform), each with its HBM
+GB/s against the measured copy roofline.
+
+Timing: W untimed warm-up steps, then K timed steps; before every timed step a buffer of twice
+the L2 size is written (L2 flush); each step is timed with CUDA events on the stream the library
+launches on.  Clocks and throttle reasons are sampled with nvidia-smi during the timed region.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the CPU oracle (fp64, one host thread) on a bounded crop of the same
+workload and prints the same JSON line with "impl": "reference".
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+import torch  # noqa: E402
+
+H = W = 8192
+LEVELS = 5
+METRIC = "Gpixel/s & HBM GB/s (% of peak), 2-D DWT non-separable vs separable, 1 GB300"
+CONFIG = {"workload": "8192x8192 seeded 1/f^2 field in [0,255], 5-level 2-D DWT, forward CDF 9/7 "
+                      "fp32 (headline) + reversible CDF 5/3 int32, non-separable vs separable",
+          "image": [H, W], "levels": LEVELS, "l2": "flushed before every timed step"}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def alg_bytes(h: int, w: int, levels: int, esize: int = 4) -> int:
+    """One read and one write of every level's input plane."""
+    tot = 0
+    for _ in range(levels):
+        tot += 2 * h * w * esize
+        h, w = (h + 1) // 2, (w + 1) // 2
+    return tot
+
+
+def src_hash() -> str:
+    d = os.path.join(ROOT, "paper_1708_07853_gb300", "csrc")
+    m = hashlib.sha256()
+    for f in sorted(os.listdir(d)):
+        if f.endswith((".cu", ".cuh", ".h")):
+            m.update(open(os.path.join(d, f), "rb").read())
+    return m.hexdigest()[:16]
+
+
+def recorded_traffic(kernel_key: str):
+    """DRAM bytes per launch from a committed ncu summary, if taken on the current sources."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    d = json.load(open(p))
+    e = d.get(kernel_key)
+    if not e or e.get("src_hash") != src_hash():
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+class ClockSampler:
+    """nvidia-smi samples (every 100 ms) kept with their wall time; summarised for a window."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index, self.samples, self.proc, self.err = index, [], None, None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError as e:
+            self.err = str(e)
+            return
+        threading.Thread(target=self._read, daemon=True).start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.samples.append((time.time(), line.strip()))
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self, t0: float, t1: float):
+        rows = [s for t, s in self.samples if t0 - 0.15 <= t <= t1 + 0.15]
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [],
+                    "samples": 0, "note": self.err or "no sample inside the timed window"}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        sm, smax, reasons = [], [], set()
+        for r in rows:
+            p = [v.strip() for v in r.split(",")]
+            try:
+                sm.append(float(p[0]))
+                smax.append(float(p[1]))
+            except (ValueError, IndexError):
+                continue
+            for n, v in zip(names, p[2:]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+# ------------------------------------------------------------------------------ reference arm
+def run_reference(args, rank: int, world: int):
+    if rank != 0:
+        return
+    from oracle import oracle as O
+    from paper_1708_07853_gb300 import inputs as I
+
+    O.build()
+    side = 1024 if args.steps + args.warmup <= 300 else 512
+    full = I.field(H, W, I.seed_for(1))
+    crop = full[:side, :side].astype(np.float64)
+    times = []
+    for i in range(args.warmup + args.steps):
+        t = time.perf_counter()
+        O.forward(crop, "cdf97", LEVELS)
+        if i >= args.warmup:
+            times.append(time.perf_counter() - t)
+    ms = 1e3 * float(np.mean(times))
+    gpix = side * side / (ms * 1e-3) / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": gpix, "unit": "Gpixel/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": CONFIG,
+            "cpu_baseline": {"kind": "oracle", "value": gpix, "unit": "Gpixel/s", "cores": 1,
+                             "sample": f"{side}x{side} top-left crop of the workload image, "
+                                       f"CDF 9/7 fp64, {LEVELS} levels, one host thread"},
+            "e2e": {"value": gpix, "unit": "Gpixel/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------------------------ our arm
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        raise SystemExit("--warmup must be >= 3")
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import torch.distributed as dist
+    if world > 1:
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+
+    from paper_1708_07853_gb300 import build as B
+    B.build()
+    from paper_1708_07853_gb300 import dwt2 as D
+    from paper_1708_07853_gb300 import inputs as I
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    peak, peak_kind = measured_peaks()
+    stream = torch.cuda.current_stream()
+    l2 = torch.cuda.get_device_properties(dev).L2_cache_size
+    flush = torch.empty(2 * l2, dtype=torch.uint8, device=dev)
+
+    field = I.field(H, W, I.seed_for(1))
+    x_f32 = torch.from_numpy(field).to(dev)
+    x_i32 = torch.from_numpy(field.astype(np.int32)).to(dev)
+    npix = H * W
+
+    def run_case(fn, steps, warmup):
+        for _ in range(warmup):
+            fn()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(steps)]
+        for s, e in evs:
+            flush.zero_()
+            s.record(stream)
+            fn()
+            e.record(stream)
+        torch.cuda.synchronize()
+        return float(np.mean([s.elapsed_time(e) for s, e in evs]))  # ms
+
+    cases = {}
+
+    def make(wv, x, scheme="nonsep", levels=LEVELS):
+        bdt = D.TORCH_DT[x.dtype]
+        c = D.alloc_coeffs(H, W, levels, wv, bdt, dev)
+        ws = D.new_workspace(D.workspace_bytes(H, W, levels, wv, bdt, scheme), dev)
+        return c, ws, bdt
+
+    # ---- headline: forward CDF 9/7 fp32, non-separable, 5 levels (timed region) ----
+    c97, ws97, _ = make("cdf97", x_f32)
+
+    def fwd97():
+        D.forward(x_f32, "cdf97", LEVELS, out=c97, workspace=ws97)
+
+    sampler = ClockSampler(dev.index if dev.index is not None else 0)
+    sampler.start()
+    for _ in range(args.warmup):
+        fwd97()
+    time.sleep(0.3)  # let the sampler start delivering
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.time()
+    ms_main = run_case(fwd97, args.steps, 0)
+    torch.cuda.synchronize()
+    barrier()
+    t1 = time.time()
+    clocks = sampler.summary(t0, t1)
+    sampler.stop()
+    if world > 1:
+        t = torch.tensor([ms_main], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_main = float(t.item())
+    status = D.check_status(ws97)
+
+    ab = alg_bytes(H, W, LEVELS)
+    gpix_main = world * npix / (ms_main * 1e-3) / 1e9
+
+    def summarise(ms, nbytes=ab):
+        gbs = nbytes / (ms * 1e-3) / 1e9
+        return {"ms": round(ms, 4), "gpix_s": round(npix / (ms * 1e-3) / 1e9, 2),
+                "gb_s": round(gbs, 1), "frac_measured": round(gbs / peak, 3),
+                "frac_nominal_8tbs": round(gbs / 8000.0, 3)}
+
+    cases["fwd_cdf97_f32_nonsep"] = summarise(ms_main)
+
+    # ---- the other cases (same harness, not the headline) ----
+    ci, wsi, _ = make("cdf53_int", x_i32)
+    cases["fwd_cdf53_int_nonsep"] = summarise(run_case(
+        lambda: D.forward(x_i32, "cdf53_int", LEVELS, out=ci, workspace=wsi), args.steps,
+        args.warmup))
+    out_f = torch.empty_like(x_f32)
+    out_i = torch.empty_like(x_i32)
+    cases["inv_cdf97_f32_nonsep"] = summarise(run_case(
+        lambda: D.inverse(c97, out=out_f, workspace=ws97), args.steps, args.warmup))
+    cases["inv_cdf53_int_nonsep"] = summarise(run_case(
+        lambda: D.inverse(ci, out=out_i, workspace=wsi), args.steps, args.warmup))
+    for scheme in ("sep_fused", "sep_twopass"):
+        for wv, x in (("cdf97", x_f32), ("cdf53_int", x_i32)):
+            c, ws, _ = make(wv, x, scheme)
+            ms = run_case(lambda: D.forward(x, wv, LEVELS, scheme=scheme, out=c, workspace=ws),
+                          args.steps, args.warmup)
+            cases[f"fwd_{wv}_{scheme}"] = summarise(ms)
+    correct_inv = bool(torch.equal(D.inverse(ci, out=out_i, workspace=wsi), x_i32))
+
+    # ---- dominant kernel: the level-1 forward launch (one launch = one 1-level transform) ----
+    c1, ws1, _ = make("cdf97", x_f32, levels=1)
+    ms_l1 = run_case(lambda: D.forward(x_f32, "cdf97", 1, out=c1, workspace=ws1), args.steps,
+                     args.warmup)
+    l1_bytes = alg_bytes(H, W, 1)
+    achieved = l1_bytes / (ms_l1 * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 3), "traffic": recorded_traffic("fwd_l1_cdf97_f32"),
+                "kernel": "k_forward<CDF97, NONSEP, f32, TMA> (level 1, 8192x8192)",
+                "algorithmic_bytes_per_launch": l1_bytes, "peak_kind": peak_kind}
+
+    # ---- end to end through host buffers (pinned), copies inside the timed region ----
+    host_in = torch.from_numpy(field).pin_memory()
+    host_out = torch.empty(c97.buffer.numel(), dtype=torch.uint8).pin_memory()
+    dev_in = torch.empty_like(x_f32)
+
+    def e2e_step():
+        dev_in.copy_(host_in, non_blocking=True)
+        D.forward(dev_in, "cdf97", LEVELS, out=c97, workspace=ws97)
+        host_out.copy_(c97.buffer, non_blocking=True)
+
+    e2e_steps = max(3, min(args.steps, 50))
+    ms_e2e = run_case(e2e_step, e2e_steps, 3)
+    e2e = {"value": round(world * npix / (ms_e2e * 1e-3) / 1e9, 3), "unit": "Gpixel/s",
+           "h2d_bytes_per_step": host_in.numel() * host_in.element_size(),
+           "d2h_bytes_per_step": host_out.numel()}
+
+    # ---- CPU baseline: the oracle on the host, bounded sample ----
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        from oracle import oracle as O
+        O.build()
+        t = time.perf_counter()
+        O.forward(field.astype(np.float64), "cdf97", LEVELS)
+        dt = time.perf_counter() - t
+        cpu = {"value": round(npix / dt / 1e9, 5), "unit": "Gpixel/s", "cores": 1,
+               "kind": "oracle", "sample": "one full 8192x8192 forward, CDF 9/7 fp64, 5 levels, "
+                                           "one host thread", "seconds": round(dt, 2)}
+
+    line = {"metric": METRIC, "value": round(gpix_main, 2), "unit": "Gpixel/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(ms_main, 4), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": dict(CONFIG, parallelism=f"replicas{world}" if world > 1 else "single",
+                           algorithmic_bytes_per_step=ab),
+            "hbm_gb_s": cases["fwd_cdf97_f32_nonsep"]["gb_s"],
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": args.steps * LEVELS, "clocks": clocks, "cases": cases,
+            "device_status": status, "int53_roundtrip_exact": correct_inv}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

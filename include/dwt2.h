@@ -1,0 +1,174 @@
+/* dwt2.h -- C ABI of the GB300 (sm_103a) 2-D discrete wavelet transform library (libdwt2.so).
+ *
+ * The library computes the 2-D DWT with the non-separable lifting scheme of Barina et al.,
+ * "The Parallel Algorithm for the 2-D Discrete Wavelet Transform" (Sec. 3, Eq. 5): per lifting
+ * pair one spatial predict step and one spatial update step, which act on the polyphase quad
+ * [LL, HL, LH, HH] of Sec. 2.  Every decomposition level is one kernel that reads its input
+ * plane once from HBM and writes the four subbands once.
+ *
+ * Conventions
+ *   - Images are row-major: H rows x W columns, a row pitch in bytes.  "Horizontal" (the paper's
+ *     m / z_m axis, filters P and U) runs along a row, "vertical" (n / z_n, P* and U*) along a
+ *     column.
+ *   - Polyphase quad at (n, m): LL = x[2n][2m], HL = x[2n][2m+1], LH = x[2n+1][2m],
+ *     HH = x[2n+1][2m+1] (Sec. 2, the vector order of Eq. 3 and Eq. 5).
+ *   - Level j maps the h x w plane LL_{j-1} (LL_0 = the image) to LL_j ceil(h/2) x ceil(w/2),
+ *     HL_j ceil(h/2) x floor(w/2), LH_j floor(h/2) x ceil(w/2), HH_j floor(h/2) x floor(w/2)
+ *     (the Mallat recursion on LL cited in Sec. 2).
+ *   - Boundaries: whole-sample symmetric extension, x[-k] = x[k], x[N-1+k] = x[N-1-k]
+ *     (repeated for signals shorter than the filter); an axis of length 1 passes through.
+ *   - Wavelets (the paper evaluates CDF 5/3, Sec. 4, and states the scheme holds for any
+ *     wavelet, Sec. 5; it prints no coefficients):
+ *       DWT2_CDF53_INT  reversible integer CDF 5/3: d = x_o - floor((x_e + x_e') / 2),
+ *                       s = x_e + floor((d' + d + 2) / 4); the fused steps keep the floors of
+ *                       the step order of Eq. 3 (P, P*, U, U*), so results are bit-exact with
+ *                       that order.  Exact while every intermediate fits in int32: inputs with
+ *                       |x| <= 2^24 are safe for every level count.
+ *       DWT2_CDF53_F32  CDF 5/3 in fp32: P(z) = -1/2 (1 + z), U(z) = 1/4 (1 + z^-1), no scaling.
+ *       DWT2_CDF97_F32  CDF 9/7 in fp32, two lifting pairs (alpha, beta, gamma, delta) of the
+ *                       Daubechies-Sweldens factorisation, then low-pass * 1/K and high-pass
+ *                       * K/2 per axis (low-pass DC gain 1, high-pass Nyquist gain 1), i.e.
+ *                       LL / K^2, HL / 2, LH / 2, HH * K^2 / 4.
+ *   - All arithmetic of the float wavelets is fp32.  DWT2_BF16 / DWT2_F16 are storage types
+ *     only: values are widened on load and rounded to nearest-even on store.  With 16-bit
+ *     band storage the intermediate LL planes (workspace) and the final LL_J stay fp32.
+ *
+ * Memory and streams
+ *   - Every pointer argument named img, coeffs, g_img, g_coeffs or workspace is a DEVICE pointer,
+ *     owned by the caller; the library never allocates device memory on these paths.
+ *   - stream is a cudaStream_t handle passed as void* (NULL = the legacy default stream).
+ *     Every transform call is asynchronous on that stream; the buffers must stay alive until
+ *     the stream has executed it.
+ *   - Errors: functions return dwt2_status.  Invalid arguments are rejected before any launch
+ *     (DWT2_EINVAL / DWT2_EUNSUPPORTED); a failed launch returns DWT2_ECUDA, with the CUDA error
+ *     text available from dwt2_last_error().  Nothing in the library aborts, traps or throws.
+ *   - Device-side waits (pipeline barriers inside a kernel) are bounded in time.  A wait that
+ *     gives up records DWT2_ETIMEOUT in the workspace status word; dwt2_check_status() reads it.
+ */
+#ifndef DWT2_H
+#define DWT2_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    DWT2_CDF53_INT = 0,
+    DWT2_CDF53_F32 = 1,
+    DWT2_CDF97_F32 = 2
+} dwt2_wavelet;
+
+/* Element types.  DWT2_I32 is the only type of the integer wavelet; the float wavelets take
+ * DWT2_F32, DWT2_BF16 or DWT2_F16 storage. */
+typedef enum {
+    DWT2_I32 = 0,
+    DWT2_F32 = 1,
+    DWT2_BF16 = 2,
+    DWT2_F16 = 3
+} dwt2_dtype;
+
+typedef enum {
+    DWT2_OK = 0,
+    DWT2_EINVAL = 1,        /* invalid argument (null/unaligned pointer, size, level count) */
+    DWT2_EUNSUPPORTED = 2,  /* valid but unsupported combination (e.g. bf16 with the int wavelet) */
+    DWT2_ENOMEM = 3,        /* workspace (or host memory of a plan) too small */
+    DWT2_ECUDA = 4,         /* a CUDA call failed; see dwt2_last_error() */
+    DWT2_ETIMEOUT = 5,      /* a bounded device-side wait gave up */
+    DWT2_EINTERNAL = 6
+} dwt2_status;
+
+/* The GPU evaluation schemes.  DWT2_SCHEME_NONSEP is the product (Eq. 5).  The separable schemes
+ * are comparators of the paper's separable lifting (Eq. 3):
+ *   DWT2_SCHEME_SEP_FUSED    one pass per level like NONSEP, but evaluating the four separable
+ *                            steps P, P*, U, U* of Eq. 3 one after the other;
+ *   DWT2_SCHEME_SEP_TWOPASS  the customary GPU separable transform: a row kernel (all
+ *                            horizontal lifting steps) and then a column kernel (all vertical
+ *                            ones), two HBM round trips per level.  For the integer wavelet
+ *                            this rounds in rows-then-columns order, which differs from Eq. 3's
+ *                            order in the last bits of some coefficients. */
+typedef enum {
+    DWT2_SCHEME_NONSEP = 0,
+    DWT2_SCHEME_SEP_FUSED = 1,
+    DWT2_SCHEME_SEP_TWOPASS = 2
+} dwt2_scheme;
+
+/* One subband plane inside the caller's coefficient buffer. */
+typedef struct {
+    int64_t offset_bytes; /* from the start of the coefficient buffer; a multiple of 256 */
+    int32_t h, w;         /* rows, columns (either may be 0, e.g. HL of a 1-column plane) */
+    int32_t pitch_bytes;  /* row pitch, a multiple of 16 */
+    int32_t dtype;        /* dwt2_dtype of the elements */
+    int32_t level;        /* 1..levels */
+    char kind;            /* 'A' = LL, 'H' = HL, 'V' = LH, 'D' = HH */
+    char reserved[3];
+} dwt2_band;
+
+/* Human-readable text of a status code (static storage). */
+const char* dwt2_status_string(int status);
+
+/* Text of the last CUDA error seen by the calling thread ("" if none). */
+const char* dwt2_last_error(void);
+
+/* Largest valid level count for an H x W image: the number of halvings (rounding up) that
+ * bring the longer side to 1, at least 1.  Returns 0 for H < 1 or W < 1. */
+int dwt2_max_levels(int H, int W);
+
+/* Layout of the coefficient buffer for (H, W, levels, band_dtype).
+ * bands: caller array of 1 + 3 * levels entries (may be NULL to query only coeff_bytes), filled
+ *        in band-list order LL_levels, then HL_j, LH_j, HH_j for j = levels .. 1.
+ * coeff_bytes: total size of the coefficient buffer.
+ * LL_levels is DWT2_I32 for the integer wavelet and DWT2_F32 otherwise; the other bands have
+ * band_dtype.  band_dtype DWT2_I32 selects the integer layout.
+ * Returns DWT2_EINVAL for invalid sizes or level counts. */
+int dwt2_layout(int H, int W, int levels, int band_dtype, dwt2_band* bands, size_t* coeff_bytes);
+
+/* Bytes of device workspace that dwt2_forward / dwt2_inverse / the adjoints need for these
+ * arguments: a 256-byte status header plus two ping-pong planes for the intermediate LL levels
+ * (fp32 for the float wavelets, int32 for the integer one).  Returns 0 for invalid arguments.
+ * The workspace header must be zeroed before first use (dwt2_workspace_init). */
+size_t dwt2_workspace_bytes(int H, int W, int levels, int wavelet, int band_dtype);
+
+/* Zero the 256-byte status header of a workspace (asynchronous on stream). */
+int dwt2_workspace_init(void* workspace, size_t ws_bytes, void* stream);
+
+/* Synchronise stream, read the status word of the workspace header and clear it.  Returns
+ * DWT2_OK, or DWT2_ETIMEOUT if any kernel since the last check gave up a bounded wait. */
+int dwt2_check_status(void* workspace, void* stream);
+
+/* Forward transform (Eq. 5, the non-separable lifting scheme), levels 1..levels.
+ * img: device pointer to H x W elements of img_dtype with row pitch img_pitch_bytes (a multiple
+ *      of the element size, >= W * element size); 16-byte-aligned pitch and base take the TMA
+ *      load path, others a plain-load path with identical results.
+ *      img_dtype: DWT2_I32 for the integer wavelet; DWT2_F32 or band_dtype for the float ones.
+ * coeffs: device buffer of dwt2_layout(...)'s coeff_bytes, 256-byte aligned.
+ * workspace: device buffer of at least dwt2_workspace_bytes(...) bytes, 256-byte aligned.
+ * The call only enqueues work on stream. */
+int dwt2_forward(const void* img, int64_t img_pitch_bytes, int H, int W, int img_dtype,
+                 void* coeffs, void* workspace, size_t ws_bytes, int wavelet, int levels,
+                 int band_dtype, void* stream);
+
+/* Forward transform with a chosen scheme (DWT2_SCHEME_*); DWT2_SCHEME_NONSEP is dwt2_forward.
+ * The separable schemes support DWT2_F32 / DWT2_I32 storage only.  DWT2_SCHEME_SEP_TWOPASS
+ * needs dwt2_workspace_bytes_scheme(...) bytes of workspace (an extra full-size plane). */
+int dwt2_forward_scheme(const void* img, int64_t img_pitch_bytes, int H, int W, int img_dtype,
+                        void* coeffs, void* workspace, size_t ws_bytes, int wavelet, int levels,
+                        int band_dtype, int scheme, void* stream);
+size_t dwt2_workspace_bytes_scheme(int H, int W, int levels, int wavelet, int band_dtype,
+                                   int scheme);
+
+/* Inverse transform: the exact inverse of each fused step, in reverse order (Eq. 5 inverted:
+ * the inverse spatial update [1 -U -U* UU*; 0 1 0 -U*; 0 0 1 -U; 0 0 0 1], then the inverse
+ * spatial predict [1 0 0 0; -P 1 0 0; -P* 0 1 0; PP* -P* -P 1]), levels levels..1.
+ * coeffs (input) as laid out by dwt2_layout; img (output) H x W of img_dtype with pitch
+ * img_pitch_bytes.  Integer: bit-exact reconstruction of dwt2_forward's input. */
+int dwt2_inverse(const void* coeffs, void* img, int64_t img_pitch_bytes, int H, int W,
+                 int img_dtype, void* workspace, size_t ws_bytes, int wavelet, int levels,
+                 int band_dtype, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DWT2_H */

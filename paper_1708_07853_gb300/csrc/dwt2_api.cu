@@ -1,0 +1,435 @@
+// dwt2_api.cu -- the C ABI of libdwt2.so: argument validation, the coefficient-buffer layout,
+// workspace planning, TMA tensor maps and the per-level launch sequence.
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <cstring>
+#include <mutex>
+#include <string>
+
+#include "../../include/dwt2.h"
+#include "dwt2_internal.h"
+
+#define DWT2_EXPORT extern "C" __attribute__((visibility("default")))
+
+namespace dwt2 {
+
+// ------------------------------------------------------------------------------ utilities
+static thread_local std::string g_last_error;
+
+static int cuda_fail(cudaError_t e, const char* where) {
+    g_last_error = std::string(where) + ": " + cudaGetErrorString(e);
+    return DWT2_ECUDA;
+}
+
+int device_sm_count() {
+    static int n = [] {
+        int dev = 0, v = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) v = 1;
+        return v;
+    }();
+    return n;
+}
+
+static size_t esize(int dt) { return dt == DT_BF16 || dt == DT_F16 ? 2 : 4; }
+static int64_t align_up(int64_t v, int64_t a) { return (v + a - 1) / a * a; }
+static bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+static int64_t plane_pitch(int w, int dt) { return align_up(std::max<int64_t>(1, w) * esize(dt), 16); }
+
+static int max_levels(int H, int W) {
+    if (H < 1 || W < 1) return 0;
+    int n = H > W ? H : W, L = 0;
+    while (n > 1) {
+        n = (n + 1) / 2;
+        ++L;
+    }
+    return L < 1 ? 1 : L;
+}
+
+struct Layout {
+    int J = 0;
+    int h[34], w[34];      // plane size entering level j + 1 (index 0 = image)
+    dwt2_band band[1 + 3 * 33];
+    int64_t bytes = 0;
+};
+
+static const dwt2_band& band_of(const Layout& L, int level, int kind /*0 HL 1 LH 2 HH*/) {
+    return L.band[1 + 3 * (L.J - level) + kind];
+}
+
+static int make_layout(int H, int W, int J, int band_dtype, Layout* L) {
+    if (H < 1 || W < 1 || J < 1 || J > max_levels(H, W) || J > 32) return DWT2_EINVAL;
+    if (band_dtype < DT_I32 || band_dtype > DT_F16) return DWT2_EINVAL;
+    L->J = J;
+    L->h[0] = H;
+    L->w[0] = W;
+    for (int j = 1; j <= J; ++j) {
+        L->h[j] = (L->h[j - 1] + 1) / 2;
+        L->w[j] = (L->w[j - 1] + 1) / 2;
+    }
+    int64_t off = 0;
+    auto add = [&](int idx, int h, int w, int dt, int level, char kind) {
+        dwt2_band& b = L->band[idx];
+        b.offset_bytes = off;
+        b.h = h;
+        b.w = w;
+        b.pitch_bytes = int32_t(plane_pitch(w, dt));
+        b.dtype = dt;
+        b.level = level;
+        b.kind = kind;
+        b.reserved[0] = b.reserved[1] = b.reserved[2] = 0;
+        off = align_up(off + (h > 0 && w > 0 ? int64_t(h) * b.pitch_bytes : 0), 256);
+    };
+    const int ll_dt = band_dtype == DT_I32 ? DT_I32 : DT_F32;
+    add(0, L->h[J], L->w[J], ll_dt, J, 'A');
+    for (int j = J; j >= 1; --j) {
+        const int h = L->h[j - 1], w = L->w[j - 1];
+        const int base = 1 + 3 * (J - j);
+        add(base + 0, (h + 1) / 2, w / 2, band_dtype, j, 'H');
+        add(base + 1, h / 2, (w + 1) / 2, band_dtype, j, 'V');
+        add(base + 2, h / 2, w / 2, band_dtype, j, 'D');
+    }
+    L->bytes = off;
+    return DWT2_OK;
+}
+
+// Workspace: [0, 256) status header; then LL ping-pong planes A (LL_1, LL_3, ...) and
+// B (LL_2, LL_4, ...); then, for the two-pass comparator, a full-size plane.
+static constexpr int64_t kHeader = 256;
+struct WsPlan {
+    int64_t off[3] = {0, 0, 0};
+    int64_t pitch[3] = {0, 0, 0};
+    int64_t bytes = 0;
+};
+
+static WsPlan plan_workspace(int H, int W, int J, int wavelet, int scheme) {
+    WsPlan p;
+    const int dt = wavelet == WV_CDF53_INT ? DT_I32 : DT_F32;
+    int64_t off = kHeader;
+    int h = H, w = W;
+    for (int k = 0; k < 2; ++k) {
+        h = (h + 1) / 2;
+        w = (w + 1) / 2;
+        p.off[k] = off;
+        p.pitch[k] = plane_pitch(w, dt);
+        if (J >= k + 2) off = align_up(off + int64_t(h) * p.pitch[k], 256);
+    }
+    if (scheme == DWT2_SCHEME_SEP_TWOPASS) {
+        p.off[2] = off;
+        p.pitch[2] = plane_pitch(W, dt);
+        off = align_up(off + int64_t(H) * p.pitch[2], 256);
+    }
+    p.bytes = off;
+    return p;
+}
+
+// ------------------------------------------------------------------------------ tensor maps
+static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000,
+                                             cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            p = nullptr;
+        return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }();
+    return fn;
+}
+
+static CUtensorMapDataType tm_type(int dt) {
+    switch (dt) {
+    case DT_I32: return CU_TENSOR_MAP_DATA_TYPE_INT32;
+    case DT_F32: return CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+    case DT_BF16: return CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+    default: return CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
+    }
+}
+
+// A 2-D map over an h x w plane with 1-row boxes of box_w elements; false if TMA cannot
+// address the plane (alignment) or the driver rejects it.
+static bool make_map(CUtensorMap* m, const void* base, int64_t pitch, int h, int w, int dt,
+                     int box_w) {
+    std::memset(m, 0, sizeof(*m));
+    auto fn = encode_fn();
+    if (!fn || h < 1 || w < 1 || !aligned(base, 16) || pitch % 16 != 0) return false;
+    cuuint64_t dims[2] = {cuuint64_t(w), cuuint64_t(h)};
+    cuuint64_t strides[1] = {cuuint64_t(pitch)};
+    cuuint32_t box[2] = {cuuint32_t(box_w), 1};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = fn(m, tm_type(dt), 2, const_cast<void*>(base), dims, strides, box, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+// ------------------------------------------------------------------------------ validation
+static int check_types(int wavelet, int img_dtype, int band_dtype) {
+    if (wavelet < WV_CDF53_INT || wavelet > WV_CDF97) return DWT2_EINVAL;
+    if (img_dtype < DT_I32 || img_dtype > DT_F16 || band_dtype < DT_I32 || band_dtype > DT_F16)
+        return DWT2_EINVAL;
+    if (wavelet == WV_CDF53_INT)
+        return (img_dtype == DT_I32 && band_dtype == DT_I32) ? DWT2_OK : DWT2_EUNSUPPORTED;
+    if (band_dtype == DT_I32 || img_dtype == DT_I32) return DWT2_EUNSUPPORTED;
+    if (img_dtype != DT_F32 && img_dtype != band_dtype) return DWT2_EUNSUPPORTED;
+    return DWT2_OK;
+}
+
+static int check_image(const void* img, int64_t pitch, int W, int dt) {
+    if (!img) return DWT2_EINVAL;
+    const size_t es = esize(dt);
+    if (!aligned(img, es) || pitch < int64_t(W) * int64_t(es) || pitch % int64_t(es) != 0)
+        return DWT2_EINVAL;
+    return DWT2_OK;
+}
+
+static FwdArgs level_args(const void* in, int64_t in_pitch, int h, int w, int* status) {
+    FwdArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.in = in;
+    a.in_pitch = in_pitch;
+    a.H = h;
+    a.W = w;
+    a.ner = (h + 1) / 2;
+    a.ndr = h / 2;
+    a.nec = (w + 1) / 2;
+    a.ndc = w / 2;
+    a.status = status;
+    return a;
+}
+
+static cudaError_t launch_fwd(int wavelet, int mode, int ti, int tb, bool tma,
+                              const CUtensorMap& tm, const FwdArgs& a, cudaStream_t s) {
+    switch (wavelet) {
+    case WV_CDF53_INT: return launch_fwd_i53(mode, tma, tm, a, s);
+    case WV_CDF53: return launch_fwd_f53(mode, ti, tb, tma, tm, a, s);
+    default: return launch_fwd_f97(mode, ti, tb, tma, tm, a, s);
+    }
+}
+
+static int forward_impl(const void* img, int64_t img_pitch, int H, int W, int img_dtype,
+                        void* coeffs, void* ws, size_t ws_bytes, int wavelet, int J,
+                        int band_dtype, int scheme, cudaStream_t st) {
+    int rc = check_types(wavelet, img_dtype, band_dtype);
+    if (rc) return rc;
+    if (scheme < DWT2_SCHEME_NONSEP || scheme > DWT2_SCHEME_SEP_TWOPASS) return DWT2_EINVAL;
+    if (scheme != DWT2_SCHEME_NONSEP && (img_dtype != band_dtype)) return DWT2_EUNSUPPORTED;
+    Layout L;
+    if ((rc = make_layout(H, W, J, band_dtype, &L))) return rc;
+    if ((rc = check_image(img, img_pitch, W, img_dtype))) return rc;
+    if (!coeffs || !ws || !aligned(coeffs, 16) || !aligned(ws, 16)) return DWT2_EINVAL;
+    const WsPlan wp = plan_workspace(H, W, J, wavelet, scheme);
+    if (int64_t(ws_bytes) < wp.bytes) return DWT2_ENOMEM;
+
+    char* cb = static_cast<char*>(coeffs);
+    char* wb = static_cast<char*>(ws);
+    int* status = reinterpret_cast<int*>(wb);
+    const int ll_dt = wavelet == WV_CDF53_INT ? DT_I32 : DT_F32;
+
+    const void* in = img;
+    int64_t in_pitch = img_pitch;
+    int in_dt = img_dtype;
+    for (int j = 1; j <= J; ++j) {
+        const int h = L.h[j - 1], w = L.w[j - 1];
+        FwdArgs a = level_args(in, in_pitch, h, w, status);
+        const dwt2_band &bhl = band_of(L, j, 0), &blh = band_of(L, j, 1), &bhh = band_of(L, j, 2);
+        a.hl = {cb + bhl.offset_bytes, bhl.pitch_bytes};
+        a.lh = {cb + blh.offset_bytes, blh.pitch_bytes};
+        a.hh = {cb + bhh.offset_bytes, bhh.pitch_bytes};
+        if (j == J) a.ll = {cb + L.band[0].offset_bytes, L.band[0].pitch_bytes};
+        else a.ll = {wb + wp.off[(j - 1) % 2], wp.pitch[(j - 1) % 2]};
+
+        cudaError_t e;
+        if (scheme == DWT2_SCHEME_SEP_TWOPASS) {
+            // row pass into the full-size plane, then the column pass into the bands
+            CUtensorMap tm;
+            bool tma = make_map(&tm, in, in_pitch, h, w, in_dt, kBoxW);
+            FwdArgs r = a;
+            r.ll = {wb + wp.off[2], wp.pitch[2]};
+            e = launch_fwd(wavelet, MODE_ROWS, in_dt, band_dtype, tma, tm, r, st);
+            if (e != cudaSuccess) return cuda_fail(e, "row pass");
+            FwdArgs c = level_args(wb + wp.off[2], wp.pitch[2], h, w, status);
+            c.ll = a.ll;
+            c.hl = a.hl;
+            c.lh = a.lh;
+            c.hh = a.hh;
+            tma = make_map(&tm, wb + wp.off[2], wp.pitch[2], h, w, ll_dt, kBoxW);
+            e = launch_fwd(wavelet, MODE_COLS, ll_dt, band_dtype, tma, tm, c, st);
+            if (e != cudaSuccess) return cuda_fail(e, "column pass");
+        } else {
+            CUtensorMap tm;
+            const bool tma = make_map(&tm, in, in_pitch, h, w, in_dt, kBoxW);
+            const int mode = scheme == DWT2_SCHEME_NONSEP ? MODE_NONSEP : MODE_SEP;
+            e = launch_fwd(wavelet, mode, in_dt, band_dtype, tma, tm, a, st);
+            if (e == cudaErrorNotSupported) return DWT2_EUNSUPPORTED;
+            if (e != cudaSuccess) return cuda_fail(e, "forward level");
+        }
+        in = a.ll.ptr;
+        in_pitch = a.ll.pitch;
+        in_dt = ll_dt;
+    }
+    return DWT2_OK;
+}
+
+static int inverse_impl(const void* coeffs, void* img, int64_t img_pitch, int H, int W,
+                        int img_dtype, void* ws, size_t ws_bytes, int wavelet, int J,
+                        int band_dtype, cudaStream_t st) {
+    int rc = check_types(wavelet, img_dtype, band_dtype);
+    if (rc) return rc;
+    Layout L;
+    if ((rc = make_layout(H, W, J, band_dtype, &L))) return rc;
+    if ((rc = check_image(img, img_pitch, W, img_dtype))) return rc;
+    if (!coeffs || !ws || !aligned(coeffs, 16) || !aligned(ws, 16)) return DWT2_EINVAL;
+    const WsPlan wp = plan_workspace(H, W, J, wavelet, DWT2_SCHEME_NONSEP);
+    if (int64_t(ws_bytes) < wp.bytes) return DWT2_ENOMEM;
+
+    const char* cb = static_cast<const char*>(coeffs);
+    char* wb = static_cast<char*>(ws);
+    int* status = reinterpret_cast<int*>(wb);
+    const int ll_dt = wavelet == WV_CDF53_INT ? DT_I32 : DT_F32;
+
+    for (int j = J; j >= 1; --j) {
+        const int h = L.h[j - 1], w = L.w[j - 1];
+        InvArgs a;
+        std::memset(&a, 0, sizeof(a));
+        a.H = h;
+        a.W = w;
+        a.ner = (h + 1) / 2;
+        a.ndr = h / 2;
+        a.nec = (w + 1) / 2;
+        a.ndc = w / 2;
+        a.status = status;
+        const void* llp;
+        int64_t llpitch;
+        if (j == J) {
+            llp = cb + L.band[0].offset_bytes;
+            llpitch = L.band[0].pitch_bytes;
+        } else {
+            llp = wb + wp.off[(j - 1) % 2];
+            llpitch = wp.pitch[(j - 1) % 2];
+        }
+        const dwt2_band &bhl = band_of(L, j, 0), &blh = band_of(L, j, 1), &bhh = band_of(L, j, 2);
+        a.band[0] = llp;
+        a.band_pitch[0] = llpitch;
+        a.band[1] = cb + bhl.offset_bytes;
+        a.band_pitch[1] = bhl.pitch_bytes;
+        a.band[2] = cb + blh.offset_bytes;
+        a.band_pitch[2] = blh.pitch_bytes;
+        a.band[3] = cb + bhh.offset_bytes;
+        a.band_pitch[3] = bhh.pitch_bytes;
+        int out_dt;
+        if (j == 1) {
+            a.out = {img, img_pitch};
+            out_dt = img_dtype;
+        } else {
+            a.out = {wb + wp.off[(j - 2) % 2], wp.pitch[(j - 2) % 2]};
+            out_dt = ll_dt;
+        }
+        const size_t vbytes = 4 * esize(out_dt);
+        a.out_vec = aligned(a.out.ptr, vbytes) && a.out.pitch % int64_t(vbytes) == 0;
+
+        CUtensorMap tm[4];
+        bool tma = h >= 2 && w >= 2;
+        if (tma) {
+            tma = make_map(&tm[0], a.band[0], a.band_pitch[0], a.ner, a.nec, ll_dt, kBRow) &&
+                  make_map(&tm[1], a.band[1], a.band_pitch[1], a.ner, a.ndc, band_dtype, kBRow) &&
+                  make_map(&tm[2], a.band[2], a.band_pitch[2], a.ndr, a.nec, band_dtype, kBRow) &&
+                  make_map(&tm[3], a.band[3], a.band_pitch[3], a.ndr, a.ndc, band_dtype, kBRow);
+        }
+        if (!tma) std::memset(tm, 0, sizeof(tm));
+        cudaError_t e = launch_inv(wavelet, band_dtype, out_dt, tma, tm, a, st);
+        if (e == cudaErrorNotSupported) return DWT2_EUNSUPPORTED;
+        if (e != cudaSuccess) return cuda_fail(e, "inverse level");
+    }
+    return DWT2_OK;
+}
+
+}  // namespace dwt2
+
+using namespace dwt2;
+
+// ==================================================================================== C ABI
+DWT2_EXPORT const char* dwt2_status_string(int status) {
+    switch (status) {
+    case DWT2_OK: return "ok";
+    case DWT2_EINVAL: return "invalid argument";
+    case DWT2_EUNSUPPORTED: return "unsupported combination";
+    case DWT2_ENOMEM: return "workspace or buffer too small";
+    case DWT2_ECUDA: return "CUDA error";
+    case DWT2_ETIMEOUT: return "device-side wait timed out";
+    case DWT2_EINTERNAL: return "internal error";
+    default: return "unknown status";
+    }
+}
+
+DWT2_EXPORT const char* dwt2_last_error(void) { return g_last_error.c_str(); }
+
+DWT2_EXPORT int dwt2_max_levels(int H, int W) { return max_levels(H, W); }
+
+DWT2_EXPORT int dwt2_layout(int H, int W, int levels, int band_dtype, dwt2_band* bands,
+                            size_t* coeff_bytes) {
+    Layout L;
+    const int rc = make_layout(H, W, levels, band_dtype, &L);
+    if (rc) return rc;
+    if (bands) std::memcpy(bands, L.band, sizeof(dwt2_band) * (1 + 3 * levels));
+    if (coeff_bytes) *coeff_bytes = size_t(L.bytes);
+    return DWT2_OK;
+}
+
+DWT2_EXPORT size_t dwt2_workspace_bytes_scheme(int H, int W, int levels, int wavelet,
+                                               int band_dtype, int scheme) {
+    Layout L;
+    if (make_layout(H, W, levels, band_dtype, &L) || wavelet < 0 || wavelet > 2 ||
+        scheme < DWT2_SCHEME_NONSEP || scheme > DWT2_SCHEME_SEP_TWOPASS)
+        return 0;
+    return size_t(plan_workspace(H, W, levels, wavelet, scheme).bytes);
+}
+
+DWT2_EXPORT size_t dwt2_workspace_bytes(int H, int W, int levels, int wavelet, int band_dtype) {
+    return dwt2_workspace_bytes_scheme(H, W, levels, wavelet, band_dtype, DWT2_SCHEME_NONSEP);
+}
+
+DWT2_EXPORT int dwt2_workspace_init(void* workspace, size_t ws_bytes, void* stream) {
+    if (!workspace || ws_bytes < size_t(kHeader)) return DWT2_EINVAL;
+    cudaError_t e = cudaMemsetAsync(workspace, 0, kHeader, static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? DWT2_OK : cuda_fail(e, "workspace init");
+}
+
+DWT2_EXPORT int dwt2_check_status(void* workspace, void* stream) {
+    if (!workspace) return DWT2_EINVAL;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int v = 0;
+    cudaError_t e = cudaMemcpyAsync(&v, workspace, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "check status");
+    if (v != 0) {
+        e = cudaMemsetAsync(workspace, 0, sizeof(int), s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return cuda_fail(e, "check status");
+    }
+    return v == 0 ? DWT2_OK : v;
+}
+
+DWT2_EXPORT int dwt2_forward_scheme(const void* img, int64_t img_pitch_bytes, int H, int W,
+                                    int img_dtype, void* coeffs, void* workspace, size_t ws_bytes,
+                                    int wavelet, int levels, int band_dtype, int scheme,
+                                    void* stream) {
+    return forward_impl(img, img_pitch_bytes, H, W, img_dtype, coeffs, workspace, ws_bytes,
+                        wavelet, levels, band_dtype, scheme, static_cast<cudaStream_t>(stream));
+}
+
+DWT2_EXPORT int dwt2_forward(const void* img, int64_t img_pitch_bytes, int H, int W,
+                             int img_dtype, void* coeffs, void* workspace, size_t ws_bytes,
+                             int wavelet, int levels, int band_dtype, void* stream) {
+    return forward_impl(img, img_pitch_bytes, H, W, img_dtype, coeffs, workspace, ws_bytes,
+                        wavelet, levels, band_dtype, DWT2_SCHEME_NONSEP,
+                        static_cast<cudaStream_t>(stream));
+}
+
+DWT2_EXPORT int dwt2_inverse(const void* coeffs, void* img, int64_t img_pitch_bytes, int H, int W,
+                             int img_dtype, void* workspace, size_t ws_bytes, int wavelet,
+                             int levels, int band_dtype, void* stream) {
+    return inverse_impl(coeffs, img, img_pitch_bytes, H, W, img_dtype, workspace, ws_bytes,
+                        wavelet, levels, band_dtype, static_cast<cudaStream_t>(stream));
+}

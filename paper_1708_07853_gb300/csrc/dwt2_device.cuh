@@ -1,0 +1,199 @@
+// dwt2_device.cuh -- device primitives: mbarrier / TMA (cp.async.bulk.tensor) wrappers with
+// time-bounded waits, warp neighbour exchange, element conversions and vector memory access.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace dwt2 {
+
+constexpr unsigned kFull = 0xffffffffu;
+// A pipeline wait that has not completed after this many nanoseconds gives up, records
+// DWT2_ETIMEOUT and lets the kernel wind down (no wait in this library can spin forever).
+constexpr unsigned long long kWaitTimeoutNs = 2000000000ull;
+constexpr int kStatusTimeout = 5;  // DWT2_ETIMEOUT
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+                 : "memory");
+}
+
+// Makes the initialised barriers visible to the async (TMA) proxy.
+__device__ __forceinline__ void fence_barrier_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Waits for the phase of the given parity to complete.  Returns false if the CTA-wide abort
+// flag is raised or the wait exceeds kWaitTimeoutNs (then it raises the flag itself and records
+// the timeout in *status).
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
+                                          int* status) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = globaltimer_ns();
+    for (;;) {
+#pragma unroll 1
+        for (int k = 0; k < 32; ++k)
+            if (mbar_try_wait(bar, parity)) return true;
+        if (*abort_flag) return false;
+        if (globaltimer_ns() - t0 > kWaitTimeoutNs) {
+            *abort_flag = 1;
+            if (status) atomicExch(status, kStatusTimeout);
+            return false;
+        }
+    }
+}
+
+// 2-D tiled TMA load of one box into shared memory, completing on an mbarrier (transaction
+// bytes).  x must be a multiple of 16 bytes / element size (the caller guarantees it).
+__device__ __forceinline__ void tma_load_2d(void* smem_dst, const CUtensorMap* map, uint64_t* bar,
+                                            int x, int y) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(smem_dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void prefetch_tensormap(const CUtensorMap* map) {
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
+}
+
+// ------------------------------------------------------------------ whole-sample reflection
+// Index i of the whole-sample symmetric extension of a length-n signal (period 2n - 2, mirrored
+// about samples 0 and n - 1); n == 1 maps everything to 0.
+__host__ __device__ __forceinline__ int refl(int i, int n) {
+    if (n <= 1) return 0;
+    const int p = 2 * n - 2;
+    i %= p;
+    if (i < 0) i += p;
+    return i >= n ? p - i : i;
+}
+
+// ------------------------------------------------------------------------- conversions
+template <typename T> struct Compute { using type = float; };
+template <> struct Compute<int32_t> { using type = int32_t; };
+
+__device__ __forceinline__ float to_c(float v) { return v; }
+__device__ __forceinline__ int32_t to_c(int32_t v) { return v; }
+__device__ __forceinline__ float to_c(__nv_bfloat16 v) { return __bfloat162float(v); }
+__device__ __forceinline__ float to_c(__half v) { return __half2float(v); }
+
+template <typename T> __device__ __forceinline__ T from_c(float v);
+template <> __device__ __forceinline__ float from_c<float>(float v) { return v; }
+template <> __device__ __forceinline__ __nv_bfloat16 from_c<__nv_bfloat16>(float v) {
+    return __float2bfloat16_rn(v);
+}
+template <> __device__ __forceinline__ __half from_c<__half>(float v) { return __float2half_rn(v); }
+template <typename T> __device__ __forceinline__ T from_c(int32_t v);
+template <> __device__ __forceinline__ int32_t from_c<int32_t>(int32_t v) { return v; }
+
+template <typename T> __device__ __forceinline__ T zero_of() { return T(0); }
+template <> __device__ __forceinline__ __nv_bfloat16 zero_of<__nv_bfloat16>() {
+    return __float2bfloat16_rn(0.f);
+}
+template <> __device__ __forceinline__ __half zero_of<__half>() { return __float2half_rn(0.f); }
+
+// --------------------------------------------------------------- vector shared / global access
+// Four consecutive elements (16 B for 32-bit types, 8 B for 16-bit types); p is aligned to that.
+template <typename T, typename C>
+__device__ __forceinline__ void ld4(const T* p, C (&v)[4]) {
+    if constexpr (sizeof(T) == 4) {
+        const uint4 u = *reinterpret_cast<const uint4*>(p);
+        const T* t = reinterpret_cast<const T*>(&u);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) v[k] = to_c(t[k]);
+    } else {
+        const uint2 u = *reinterpret_cast<const uint2*>(p);
+        const T* t = reinterpret_cast<const T*>(&u);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) v[k] = to_c(t[k]);
+    }
+}
+
+// Two consecutive elements (8 B or 4 B), aligned.
+template <typename T, typename C>
+__device__ __forceinline__ void ld2(const T* p, C (&v)[2]) {
+    if constexpr (sizeof(T) == 4) {
+        const uint2 u = *reinterpret_cast<const uint2*>(p);
+        const T* t = reinterpret_cast<const T*>(&u);
+        v[0] = to_c(t[0]);
+        v[1] = to_c(t[1]);
+    } else {
+        const uint32_t u = *reinterpret_cast<const uint32_t*>(p);
+        const T* t = reinterpret_cast<const T*>(&u);
+        v[0] = to_c(t[0]);
+        v[1] = to_c(t[1]);
+    }
+}
+
+template <typename T, typename C>
+__device__ __forceinline__ void st2(T* p, C v0, C v1) {
+    if constexpr (sizeof(T) == 4) {
+        T t[2] = {from_c<T>(v0), from_c<T>(v1)};
+        *reinterpret_cast<uint2*>(p) = *reinterpret_cast<const uint2*>(t);
+    } else {
+        T t[2] = {from_c<T>(v0), from_c<T>(v1)};
+        *reinterpret_cast<uint32_t*>(p) = *reinterpret_cast<const uint32_t*>(t);
+    }
+}
+
+template <typename T, typename C>
+__device__ __forceinline__ void st4(T* p, C v0, C v1, C v2, C v3) {
+    T t[4] = {from_c<T>(v0), from_c<T>(v1), from_c<T>(v2), from_c<T>(v3)};
+    if constexpr (sizeof(T) == 4)
+        *reinterpret_cast<uint4*>(p) = *reinterpret_cast<const uint4*>(t);
+    else
+        *reinterpret_cast<uint2*>(p) = *reinterpret_cast<const uint2*>(t);
+}
+
+// ------------------------------------------------------------------ warp neighbour exchange
+// Each lane owns two adjacent quads (q = 0, 1).  right_of gives the value of quad m + 1 for
+// both of the lane's quads, left_of the value of quad m - 1.  Lanes 0 and 31 are halo lanes
+// whose out-of-warp neighbour values are never used for a stored result.
+template <typename C>
+__device__ __forceinline__ void right_of(const C (&v)[2], C (&r)[2]) {
+    r[0] = v[1];
+    r[1] = __shfl_down_sync(kFull, v[0], 1);
+}
+template <typename C>
+__device__ __forceinline__ void left_of(const C (&v)[2], C (&l)[2]) {
+    l[1] = v[0];
+    l[0] = __shfl_up_sync(kFull, v[1], 1);
+}
+
+}  // namespace dwt2

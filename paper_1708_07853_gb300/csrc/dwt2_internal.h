@@ -1,0 +1,27 @@
+// dwt2_internal.h -- host-side interface between the C ABI (dwt2_api.cu) and the kernel
+// launchers (one translation unit per wavelet family, compiled in parallel).
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include "dwt2_stream.cuh"
+
+namespace dwt2 {
+
+// dtype codes of the C ABI
+enum { DT_I32 = 0, DT_F32 = 1, DT_BF16 = 2, DT_F16 = 3 };
+
+// Forward level launch.  ti = input-plane dtype, tb = band dtype (LL output is int32 / fp32).
+// Returns cudaErrorNotSupported for a combination that has no kernel.
+cudaError_t launch_fwd_i53(int mode, bool tma, const CUtensorMap& tm, const FwdArgs& a,
+                           cudaStream_t s);
+cudaError_t launch_fwd_f53(int mode, int ti, int tb, bool tma, const CUtensorMap& tm,
+                           const FwdArgs& a, cudaStream_t s);
+cudaError_t launch_fwd_f97(int mode, int ti, int tb, bool tma, const CUtensorMap& tm,
+                           const FwdArgs& a, cudaStream_t s);
+// Inverse level launch.  tb = band dtype, to = output-plane dtype; tm = LL, HL, LH, HH maps.
+cudaError_t launch_inv(int wavelet, int tb, int to, bool tma, const CUtensorMap* tm,
+                       const InvArgs& a, cudaStream_t s);
+
+}  // namespace dwt2

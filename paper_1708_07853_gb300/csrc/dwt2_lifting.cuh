@@ -1,0 +1,579 @@
+// dwt2_lifting.cuh -- the lifting arithmetic of one decomposition level, as row-streaming stages.
+//
+// Data model: a lane owns two adjacent polyphase quads (q = 0, 1) of one quad row,
+//   a = LL = x[2n][2m], b = HL = x[2n][2m+1], c = LH = x[2n+1][2m], e = HH = x[2n+1][2m+1]
+// (the quad [LL, HL, LH, HH] of Sec. 2).  Horizontal neighbours (quad m +/- 1) come from the
+// adjacent lane by warp shuffle; vertical neighbours (quad row n +/- 1) are the rows pushed
+// before / after, kept in registers.  Rows are pushed top to bottom; a stage that reads the row
+// below returns its result one push late (lag 1).
+//
+// Boundaries are not handled here: the loaders feed the whole-sample symmetric extension of
+// the plane (mirrored rows and columns), on which lifting needs no boundary rule.
+//
+// Wavelets: P(z) = p (1 + z) reads quad m and m + 1 (row n and n + 1 for P*); U(z) = u (1 + z^-1)
+// reads m - 1 and m (n - 1 and n for U*).
+#pragma once
+
+#include <type_traits>
+
+#include "dwt2_device.cuh"
+
+namespace dwt2 {
+
+enum Wavelet { WV_CDF53_INT = 0, WV_CDF53 = 1, WV_CDF97 = 2 };
+enum Mode { MODE_NONSEP = 0, MODE_SEP = 1, MODE_ROWS = 2, MODE_COLS = 3 };
+
+// CDF 9/7 lifting constants and the per-axis normalisation (low * 1/K, high * K/2).
+constexpr float k97Alpha = -1.586134342059924f;
+constexpr float k97Beta = -0.052980118572961f;
+constexpr float k97Gamma = 0.882911075530934f;
+constexpr float k97Delta = 0.443506852043971f;
+constexpr float k97K = 1.230174104914001f;
+constexpr float k97Low = 1.0f / k97K;
+constexpr float k97High = k97K / 2.0f;
+
+template <typename C>
+struct QRow {
+    C a[2], b[2], c[2], e[2];
+};
+
+template <typename C>
+__device__ __forceinline__ void zero_row(QRow<C>& r) {
+#pragma unroll
+    for (int q = 0; q < 2; ++q) r.a[q] = r.b[q] = r.c[q] = r.e[q] = C(0);
+}
+
+// =============================================================================================
+// Non-separable scheme (Sec. 3, Eq. 5), float.
+// =============================================================================================
+
+// Spatial predict [1 0 0 0; P 1 0 0; P* 0 1 0; PP* P* P 1]: from the values before the step,
+//   HL += p (a + a[m+1]),  LH += p (a + a[n+1]),
+//   HH += p (c + c[m+1]) + p (b + b[n+1]) + p^2 (a + a[m+1] + a[n+1] + a[n+1][m+1]);
+// LL is unchanged.  push(y) consumes row n + 1 and returns row n (lag 1).
+struct PredictNS {
+    float p, pp;
+    QRow<float> x;
+    float xar[2], xcr[2];
+    __device__ __forceinline__ void init(float p_) {
+        p = p_;
+        pp = p_ * p_;
+        zero_row(x);
+        xar[0] = xar[1] = xcr[0] = xcr[1] = 0.f;
+    }
+    __device__ __forceinline__ void push(const QRow<float>& y, QRow<float>& o) {
+        float yar[2];
+        right_of(y.a, yar);
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            o.a[q] = x.a[q];
+            o.b[q] = x.b[q] + p * (x.a[q] + xar[q]);
+            o.c[q] = x.c[q] + p * (x.a[q] + y.a[q]);
+            o.e[q] = x.e[q] + p * (x.c[q] + xcr[q]) + p * (x.b[q] + y.b[q]) +
+                     pp * ((x.a[q] + xar[q]) + (y.a[q] + yar[q]));
+        }
+        x = y;
+        xar[0] = yar[0];
+        xar[1] = yar[1];
+        right_of(y.c, xcr);
+    }
+};
+
+// Spatial update [1 U U* UU*; 0 1 0 U*; 0 0 1 U; 0 0 0 1]: from the values before the step,
+//   LL += u (b[m-1] + b) + u (c[n-1] + c) + u^2 (e[n-1][m-1] + e[n-1] + e[m-1] + e),
+//   HL += u (e[n-1] + e),  LH += u (e[m-1] + e);  HH unchanged.  In place, lag 0.
+struct UpdateNS {
+    float u, uu;
+    float pc[2], pe[2], pel[2];  // previous row: c, e, e[m-1]
+    __device__ __forceinline__ void init(float u_) {
+        u = u_;
+        uu = u_ * u_;
+        pc[0] = pc[1] = pe[0] = pe[1] = pel[0] = pel[1] = 0.f;
+    }
+    __device__ __forceinline__ void push(QRow<float>& r) {
+        float bl[2], el[2];
+        left_of(r.b, bl);
+        left_of(r.e, el);
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            const float a = r.a[q] + u * (bl[q] + r.b[q]) + u * (pc[q] + r.c[q]) +
+                            uu * ((pel[q] + pe[q]) + (el[q] + r.e[q]));
+            const float b = r.b[q] + u * (pe[q] + r.e[q]);
+            const float c = r.c[q] + u * (el[q] + r.e[q]);
+            pc[q] = r.c[q];
+            pe[q] = r.e[q];
+            pel[q] = el[q];
+            r.a[q] = a;
+            r.b[q] = b;
+            r.c[q] = c;
+        }
+    }
+};
+
+// Inverse spatial update [1 -U -U* UU*; 0 1 0 -U*; 0 0 1 -U; 0 0 0 1] (lag 0).
+struct InvUpdateNS {
+    float u, uu;
+    float pc[2], pe[2], pel[2];
+    __device__ __forceinline__ void init(float u_) {
+        u = u_;
+        uu = u_ * u_;
+        pc[0] = pc[1] = pe[0] = pe[1] = pel[0] = pel[1] = 0.f;
+    }
+    __device__ __forceinline__ void push(QRow<float>& r) {
+        float bl[2], el[2];
+        left_of(r.b, bl);
+        left_of(r.e, el);
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            const float a = r.a[q] - u * (bl[q] + r.b[q]) - u * (pc[q] + r.c[q]) +
+                            uu * ((pel[q] + pe[q]) + (el[q] + r.e[q]));
+            const float b = r.b[q] - u * (pe[q] + r.e[q]);
+            const float c = r.c[q] - u * (el[q] + r.e[q]);
+            pc[q] = r.c[q];
+            pe[q] = r.e[q];
+            pel[q] = el[q];
+            r.a[q] = a;
+            r.b[q] = b;
+            r.c[q] = c;
+        }
+    }
+};
+
+// Inverse spatial predict [1 0 0 0; -P 1 0 0; -P* 0 1 0; PP* -P* -P 1] (lag 1).
+struct InvPredictNS {
+    float p, pp;
+    QRow<float> x;
+    float xar[2], xcr[2];
+    __device__ __forceinline__ void init(float p_) {
+        p = p_;
+        pp = p_ * p_;
+        zero_row(x);
+        xar[0] = xar[1] = xcr[0] = xcr[1] = 0.f;
+    }
+    __device__ __forceinline__ void push(const QRow<float>& y, QRow<float>& o) {
+        float yar[2];
+        right_of(y.a, yar);
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            o.a[q] = x.a[q];
+            o.b[q] = x.b[q] - p * (x.a[q] + xar[q]);
+            o.c[q] = x.c[q] - p * (x.a[q] + y.a[q]);
+            o.e[q] = x.e[q] - p * (x.b[q] + y.b[q]) - p * (x.c[q] + xcr[q]) +
+                     pp * ((x.a[q] + xar[q]) + (y.a[q] + yar[q]));
+        }
+        x = y;
+        xar[0] = yar[0];
+        xar[1] = yar[1];
+        right_of(y.c, xcr);
+    }
+};
+
+// =============================================================================================
+// Non-separable scheme, reversible integer CDF 5/3.  Sec. 2 lets horizontal and vertical steps
+// interleave freely, which holds in exact arithmetic only; with a floor in every step the fused
+// steps reproduce the floors of Eq. 3's order P, P*, U, U*.
+// =============================================================================================
+
+// Fused predict:  hl = b - ((a + a[m+1]) >> 1)          P on HL
+//                 LH = c - ((a + a[n+1]) >> 1)          P* on LH
+//                 HH = (e - ((c + c[m+1]) >> 1)) - ((hl + hl[n+1]) >> 1)   P then P* on HH
+struct PredictNSInt {
+    QRow<int32_t> x;
+    int32_t xcr[2], xhl[2];
+    __device__ __forceinline__ void init() {
+        zero_row(x);
+        xcr[0] = xcr[1] = xhl[0] = xhl[1] = 0;
+    }
+    __device__ __forceinline__ void push(const QRow<int32_t>& y, QRow<int32_t>& o) {
+        int32_t yar[2], yhl[2];
+        right_of(y.a, yar);
+#pragma unroll
+        for (int q = 0; q < 2; ++q) yhl[q] = y.b[q] - ((y.a[q] + yar[q]) >> 1);
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            o.a[q] = x.a[q];
+            o.b[q] = xhl[q];
+            o.c[q] = x.c[q] - ((x.a[q] + y.a[q]) >> 1);
+            const int32_t t = x.e[q] - ((x.c[q] + xcr[q]) >> 1);
+            o.e[q] = t - ((xhl[q] + yhl[q]) >> 1);
+        }
+        x = y;
+        xhl[0] = yhl[0];
+        xhl[1] = yhl[1];
+        right_of(y.c, xcr);
+    }
+};
+
+// Fused update:   lh = c + ((e[m-1] + e + 2) >> 2)                  U on LH
+//                 LL = (a + ((b[m-1] + b + 2) >> 2)) + ((lh[n-1] + lh + 2) >> 2)   U then U*
+//                 HL = b + ((e[n-1] + e + 2) >> 2)                  U* on HL
+struct UpdateNSInt {
+    int32_t plh[2], pe[2];
+    __device__ __forceinline__ void init() { plh[0] = plh[1] = pe[0] = pe[1] = 0; }
+    __device__ __forceinline__ void push(QRow<int32_t>& r) {
+        int32_t bl[2], el[2];
+        left_of(r.b, bl);
+        left_of(r.e, el);
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            const int32_t lh = r.c[q] + ((el[q] + r.e[q] + 2) >> 2);
+            const int32_t t = r.a[q] + ((bl[q] + r.b[q] + 2) >> 2);
+            const int32_t a = t + ((plh[q] + lh + 2) >> 2);
+            const int32_t b = r.b[q] + ((pe[q] + r.e[q] + 2) >> 2);
+            plh[q] = lh;
+            pe[q] = r.e[q];
+            r.a[q] = a;
+            r.b[q] = b;
+            r.c[q] = lh;
+        }
+    }
+};
+
+// Inverse fused update: undo U* then U, same floors, subtracted.
+struct InvUpdateNSInt {
+    int32_t pc[2], pe[2];
+    __device__ __forceinline__ void init() { pc[0] = pc[1] = pe[0] = pe[1] = 0; }
+    __device__ __forceinline__ void push(QRow<int32_t>& r) {
+        int32_t el[2], hl[2], hll[2];
+        left_of(r.e, el);
+#pragma unroll
+        for (int q = 0; q < 2; ++q) hl[q] = r.b[q] - ((pe[q] + r.e[q] + 2) >> 2);
+        left_of(hl, hll);
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            const int32_t t = r.a[q] - ((pc[q] + r.c[q] + 2) >> 2);
+            const int32_t c = r.c[q] - ((el[q] + r.e[q] + 2) >> 2);
+            const int32_t a = t - ((hll[q] + hl[q] + 2) >> 2);
+            pc[q] = r.c[q];
+            pe[q] = r.e[q];
+            r.a[q] = a;
+            r.b[q] = hl[q];
+            r.c[q] = c;
+        }
+    }
+};
+
+// Inverse fused predict: undo P* then P (lag 1).
+struct InvPredictNSInt {
+    QRow<int32_t> x;
+    int32_t xar[2];
+    __device__ __forceinline__ void init() {
+        zero_row(x);
+        xar[0] = xar[1] = 0;
+    }
+    __device__ __forceinline__ void push(const QRow<int32_t>& y, QRow<int32_t>& o) {
+        int32_t lh[2], lhr[2];
+#pragma unroll
+        for (int q = 0; q < 2; ++q) lh[q] = x.c[q] + ((x.a[q] + y.a[q]) >> 1);
+        right_of(lh, lhr);
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            const int32_t t = x.e[q] + ((x.b[q] + y.b[q]) >> 1);
+            o.a[q] = x.a[q];
+            o.b[q] = x.b[q] + ((x.a[q] + xar[q]) >> 1);
+            o.c[q] = lh[q];
+            o.e[q] = t + ((lh[q] + lhr[q]) >> 1);
+        }
+        x = y;
+        right_of(y.a, xar);
+    }
+};
+
+// =============================================================================================
+// Separable lifting (Eq. 3) evaluated in the same single pass: the four steps P, P*, U, U* one
+// after the other, each reading the previous step's result.  The comparator of the paper's
+// separable scheme on the same data path.
+// =============================================================================================
+template <typename C>
+__device__ __forceinline__ C step_p(C s0, C s1, float p) {
+    if constexpr (std::is_same<C, int32_t>::value) {  // integer: -floor((s0 + s1) / 2)
+        return -((s0 + s1) >> 1);
+    } else {
+        return p * (s0 + s1);
+    }
+}
+template <typename C>
+__device__ __forceinline__ C step_u(C d0, C d1, float u) {
+    if constexpr (std::is_same<C, int32_t>::value) {  // integer: floor((d0 + d1 + 2) / 4)
+        return (d0 + d1 + 2) >> 2;
+    } else {
+        return u * (d0 + d1);
+    }
+}
+
+// P (rows) then P* (columns); lag 1.
+template <typename C>
+struct PredictSep {
+    float p;
+    QRow<C> x;
+    __device__ __forceinline__ void init(float p_) {
+        p = p_;
+        zero_row(x);
+    }
+    __device__ __forceinline__ void push(QRow<C> y, QRow<C>& o) {
+        C ar[2], cr[2];
+        right_of(y.a, ar);
+        right_of(y.c, cr);
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {  // P on the new row
+            y.b[q] += step_p(y.a[q], ar[q], p);
+            y.e[q] += step_p(y.c[q], cr[q], p);
+        }
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {  // P* on the row above, now that its lower neighbour is known
+            o.a[q] = x.a[q];
+            o.b[q] = x.b[q];
+            o.c[q] = x.c[q] + step_p(x.a[q], y.a[q], p);
+            o.e[q] = x.e[q] + step_p(x.b[q], y.b[q], p);
+        }
+        x = y;
+    }
+};
+
+// U (rows) then U* (columns); lag 0.
+template <typename C>
+struct UpdateSep {
+    float u;
+    C pc[2], pe[2];
+    __device__ __forceinline__ void init(float u_) {
+        u = u_;
+        pc[0] = pc[1] = pe[0] = pe[1] = C(0);
+    }
+    __device__ __forceinline__ void push(QRow<C>& r) {
+        C bl[2], el[2];
+        left_of(r.b, bl);
+        left_of(r.e, el);
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {  // U
+            r.a[q] += step_u(bl[q], r.b[q], u);
+            r.c[q] += step_u(el[q], r.e[q], u);
+        }
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {  // U*
+            r.a[q] += step_u(pc[q], r.c[q], u);
+            r.b[q] += step_u(pe[q], r.e[q], u);
+            pc[q] = r.c[q];
+            pe[q] = r.e[q];
+        }
+    }
+};
+
+// Row-only pass (all horizontal steps of all pairs, then the horizontal scaling); lag 0.
+template <typename C, int WV>
+__device__ __forceinline__ void rows_only(QRow<C>& r) {
+    constexpr int npairs = WV == WV_CDF97 ? 2 : 1;
+    const float ps[2] = {WV == WV_CDF97 ? k97Alpha : -0.5f, k97Gamma};
+    const float us[2] = {WV == WV_CDF97 ? k97Beta : 0.25f, k97Delta};
+#pragma unroll
+    for (int k = 0; k < npairs; ++k) {
+        C ar[2], cr[2], bl[2], el[2];
+        right_of(r.a, ar);
+        right_of(r.c, cr);
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            r.b[q] += step_p(r.a[q], ar[q], ps[k]);
+            r.e[q] += step_p(r.c[q], cr[q], ps[k]);
+        }
+        left_of(r.b, bl);
+        left_of(r.e, el);
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            r.a[q] += step_u(bl[q], r.b[q], us[k]);
+            r.c[q] += step_u(el[q], r.e[q], us[k]);
+        }
+    }
+    if constexpr (WV == WV_CDF97) {
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            r.a[q] *= k97Low;
+            r.c[q] *= k97Low;
+            r.b[q] *= k97High;
+            r.e[q] *= k97High;
+        }
+    }
+}
+
+// Column-only steps: P* (lag 1) and U* (lag 0).
+template <typename C>
+struct PredictCol {
+    float p;
+    QRow<C> x;
+    __device__ __forceinline__ void init(float p_) {
+        p = p_;
+        zero_row(x);
+    }
+    __device__ __forceinline__ void push(const QRow<C>& y, QRow<C>& o) {
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            o.a[q] = x.a[q];
+            o.b[q] = x.b[q];
+            o.c[q] = x.c[q] + step_p(x.a[q], y.a[q], p);
+            o.e[q] = x.e[q] + step_p(x.b[q], y.b[q], p);
+        }
+        x = y;
+    }
+};
+template <typename C>
+struct UpdateCol {
+    float u;
+    C pc[2], pe[2];
+    __device__ __forceinline__ void init(float u_) {
+        u = u_;
+        pc[0] = pc[1] = pe[0] = pe[1] = C(0);
+    }
+    __device__ __forceinline__ void push(QRow<C>& r) {
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            r.a[q] += step_u(pc[q], r.c[q], u);
+            r.b[q] += step_u(pe[q], r.e[q], u);
+            pc[q] = r.c[q];
+            pe[q] = r.e[q];
+        }
+    }
+};
+
+// =============================================================================================
+// One forward level as a pipeline: push a raw (extended) quad row, get back the finished row
+// kLag pushes earlier, in place.
+// =============================================================================================
+template <int WV, int MODE>
+struct FwdPipe;
+
+// reversible integer 5/3
+template <int MODE>
+struct FwdPipe<WV_CDF53_INT, MODE> {
+    static constexpr int kLag = MODE == MODE_ROWS ? 0 : 1;
+    using C = int32_t;
+    PredictNSInt pn;
+    UpdateNSInt un;
+    PredictSep<int32_t> ps;
+    UpdateSep<int32_t> us;
+    PredictCol<int32_t> pcol;
+    UpdateCol<int32_t> ucol;
+    __device__ __forceinline__ void init() {
+        if constexpr (MODE == MODE_NONSEP) { pn.init(); un.init(); }
+        if constexpr (MODE == MODE_SEP) { ps.init(0.f); us.init(0.f); }
+        if constexpr (MODE == MODE_COLS) { pcol.init(0.f); ucol.init(0.f); }
+    }
+    __device__ __forceinline__ void push(QRow<int32_t>& r) {
+        QRow<int32_t> t;
+        if constexpr (MODE == MODE_NONSEP) { pn.push(r, t); un.push(t); r = t; }
+        if constexpr (MODE == MODE_SEP) { ps.push(r, t); us.push(t); r = t; }
+        if constexpr (MODE == MODE_ROWS) { rows_only<int32_t, WV_CDF53_INT>(r); }
+        if constexpr (MODE == MODE_COLS) { pcol.push(r, t); ucol.push(t); r = t; }
+    }
+};
+
+// float 5/3 and 9/7
+template <int WV, int MODE>
+struct FwdPipe {
+    static constexpr int kPairs = WV == WV_CDF97 ? 2 : 1;
+    static constexpr int kLag = MODE == MODE_ROWS ? 0 : kPairs;
+    using C = float;
+    PredictNS pn[kPairs];
+    UpdateNS un[kPairs];
+    PredictSep<float> ps[kPairs];
+    UpdateSep<float> us[kPairs];
+    PredictCol<float> pcol[kPairs];
+    UpdateCol<float> ucol[kPairs];
+    __device__ __forceinline__ void init() {
+        const float P[2] = {WV == WV_CDF97 ? k97Alpha : -0.5f, k97Gamma};
+        const float U[2] = {WV == WV_CDF97 ? k97Beta : 0.25f, k97Delta};
+#pragma unroll
+        for (int k = 0; k < kPairs; ++k) {
+            if constexpr (MODE == MODE_NONSEP) { pn[k].init(P[k]); un[k].init(U[k]); }
+            if constexpr (MODE == MODE_SEP) { ps[k].init(P[k]); us[k].init(U[k]); }
+            if constexpr (MODE == MODE_COLS) { pcol[k].init(P[k]); ucol[k].init(U[k]); }
+        }
+    }
+    __device__ __forceinline__ void push(QRow<float>& r) {
+        if constexpr (MODE == MODE_ROWS) {
+            rows_only<float, WV>(r);
+            return;
+        } else {
+#pragma unroll
+            for (int k = 0; k < kPairs; ++k) {
+                QRow<float> t;
+                if constexpr (MODE == MODE_NONSEP) { pn[k].push(r, t); un[k].push(t); }
+                if constexpr (MODE == MODE_SEP) { ps[k].push(r, t); us[k].push(t); }
+                if constexpr (MODE == MODE_COLS) { pcol[k].push(r, t); ucol[k].push(t); }
+                r = t;
+            }
+            if constexpr (WV == WV_CDF97) {
+                // per axis: low * 1/K, high * K/2 (COLS: vertical axis only)
+                constexpr float sLL = MODE == MODE_COLS ? k97Low : k97Low * k97Low;
+                constexpr float sHL = MODE == MODE_COLS ? k97Low : k97Low * k97High;
+                constexpr float sLH = MODE == MODE_COLS ? k97High : k97High * k97Low;
+                constexpr float sHH = MODE == MODE_COLS ? k97High : k97High * k97High;
+#pragma unroll
+                for (int q = 0; q < 2; ++q) {
+                    r.a[q] *= sLL;
+                    r.b[q] *= sHL;
+                    r.c[q] *= sLH;
+                    r.e[q] *= sHH;
+                }
+            }
+        }
+    }
+};
+
+// One inverse level: push an (extended) quad row of the four bands, get back the reconstructed
+// quad row kLag pushes earlier.
+template <int WV>
+struct InvPipe {
+    static constexpr int kPairs = WV == WV_CDF97 ? 2 : 1;
+    static constexpr int kLag = kPairs;
+    using C = float;
+    InvUpdateNS iu[kPairs];
+    InvPredictNS ip[kPairs];
+    __device__ __forceinline__ void init() {
+        const float P[2] = {WV == WV_CDF97 ? k97Alpha : -0.5f, k97Gamma};
+        const float U[2] = {WV == WV_CDF97 ? k97Beta : 0.25f, k97Delta};
+#pragma unroll
+        for (int k = 0; k < kPairs; ++k) {
+            iu[k].init(U[kPairs - 1 - k]);
+            ip[k].init(P[kPairs - 1 - k]);
+        }
+    }
+    __device__ __forceinline__ void push(QRow<float>& r) {
+        if constexpr (WV == WV_CDF97) {
+            constexpr float sLL = 1.0f / (k97Low * k97Low);
+            constexpr float sHL = 1.0f / (k97Low * k97High);
+            constexpr float sHH = 1.0f / (k97High * k97High);
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                r.a[q] *= sLL;
+                r.b[q] *= sHL;
+                r.c[q] *= sHL;
+                r.e[q] *= sHH;
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < kPairs; ++k) {
+            QRow<float> t;
+            iu[k].push(r);
+            ip[k].push(r, t);
+            r = t;
+        }
+    }
+};
+
+template <>
+struct InvPipe<WV_CDF53_INT> {
+    static constexpr int kLag = 1;
+    using C = int32_t;
+    InvUpdateNSInt iu;
+    InvPredictNSInt ip;
+    __device__ __forceinline__ void init() {
+        iu.init();
+        ip.init();
+    }
+    __device__ __forceinline__ void push(QRow<int32_t>& r) {
+        QRow<int32_t> t;
+        iu.push(r);
+        ip.push(r, t);
+        r = t;
+    }
+};
+
+}  // namespace dwt2

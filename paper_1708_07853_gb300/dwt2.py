@@ -1,0 +1,219 @@
+"""Python binding of libdwt2.so (the C ABI in include/dwt2.h).
+
+Argument marshalling only: tensors are passed as device pointers with the current CUDA stream;
+every step of the transform runs in the library's kernels.  There is no CPU path: a missing
+library or a non-CUDA tensor raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass, field
+
+import torch
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libdwt2.so")
+
+WAVELETS = {"cdf53_int": 0, "cdf53": 1, "cdf97": 2}
+SCHEMES = {"nonsep": 0, "sep_fused": 1, "sep_twopass": 2}
+DT_I32, DT_F32, DT_BF16, DT_F16 = 0, 1, 2, 3
+TORCH_DT = {torch.int32: DT_I32, torch.float32: DT_F32, torch.bfloat16: DT_BF16,
+            torch.float16: DT_F16}
+DT_TORCH = {v: k for k, v in TORCH_DT.items()}
+ESIZE = {DT_I32: 4, DT_F32: 4, DT_BF16: 2, DT_F16: 2}
+STATUS = {0: "ok", 1: "EINVAL", 2: "EUNSUPPORTED", 3: "ENOMEM", 4: "ECUDA", 5: "ETIMEOUT",
+          6: "EINTERNAL"}
+
+# Every symbol the header declares (checked by the tests without a GPU).
+EXPORTS = ["dwt2_status_string", "dwt2_last_error", "dwt2_max_levels", "dwt2_layout",
+           "dwt2_workspace_bytes", "dwt2_workspace_bytes_scheme", "dwt2_workspace_init",
+           "dwt2_check_status", "dwt2_forward", "dwt2_forward_scheme", "dwt2_inverse"]
+
+
+class Dwt2Error(RuntimeError):
+    def __init__(self, status: int, what: str):
+        self.status = status
+        msg = f"{what}: {STATUS.get(status, status)}"
+        err = _lib().dwt2_last_error().decode()
+        super().__init__(msg + (f" ({err})" if err and status == 4 else ""))
+
+
+class Band(ctypes.Structure):
+    _fields_ = [("offset_bytes", ctypes.c_int64), ("h", ctypes.c_int32), ("w", ctypes.c_int32),
+                ("pitch_bytes", ctypes.c_int32), ("dtype", ctypes.c_int32),
+                ("level", ctypes.c_int32), ("kind", ctypes.c_char),
+                ("reserved", ctypes.c_char * 3)]
+
+
+_LIB = None
+
+
+def _lib():
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is not built; run paper_1708_07853_gb300.build.build()")
+        lib = ctypes.CDLL(LIB_PATH)
+        vp, i, i64, sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_size_t
+        lib.dwt2_status_string.restype = ctypes.c_char_p
+        lib.dwt2_status_string.argtypes = [i]
+        lib.dwt2_last_error.restype = ctypes.c_char_p
+        lib.dwt2_last_error.argtypes = []
+        lib.dwt2_max_levels.argtypes = [i, i]
+        lib.dwt2_layout.argtypes = [i, i, i, i, ctypes.POINTER(Band), ctypes.POINTER(sz)]
+        lib.dwt2_workspace_bytes.restype = sz
+        lib.dwt2_workspace_bytes.argtypes = [i, i, i, i, i]
+        lib.dwt2_workspace_bytes_scheme.restype = sz
+        lib.dwt2_workspace_bytes_scheme.argtypes = [i, i, i, i, i, i]
+        lib.dwt2_workspace_init.argtypes = [vp, sz, vp]
+        lib.dwt2_check_status.argtypes = [vp, vp]
+        lib.dwt2_forward.argtypes = [vp, i64, i, i, i, vp, vp, sz, i, i, i, vp]
+        lib.dwt2_forward_scheme.argtypes = [vp, i64, i, i, i, vp, vp, sz, i, i, i, i, vp]
+        lib.dwt2_inverse.argtypes = [vp, vp, i64, i, i, i, vp, sz, i, i, i, vp]
+        for f in ("dwt2_max_levels", "dwt2_layout", "dwt2_workspace_init", "dwt2_check_status",
+                  "dwt2_forward", "dwt2_forward_scheme", "dwt2_inverse"):
+            getattr(lib, f).restype = i
+        _LIB = lib
+    return _LIB
+
+
+def lib():
+    """The loaded ctypes library (raises if it has not been built)."""
+    return _lib()
+
+
+def _wid(wavelet) -> int:
+    return WAVELETS[wavelet] if isinstance(wavelet, str) else int(wavelet)
+
+
+def _stream_ptr(stream=None) -> int:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return int(s.cuda_stream)
+
+
+def max_levels(H: int, W: int) -> int:
+    return _lib().dwt2_max_levels(H, W)
+
+
+def layout(H: int, W: int, levels: int, band_dtype: int):
+    """(list of Band, coeff_bytes) of the coefficient buffer."""
+    arr = (Band * (1 + 3 * levels))()
+    nbytes = ctypes.c_size_t(0)
+    rc = _lib().dwt2_layout(H, W, levels, band_dtype, arr, ctypes.byref(nbytes))
+    if rc:
+        raise Dwt2Error(rc, "dwt2_layout")
+    return list(arr), nbytes.value
+
+
+def workspace_bytes(H: int, W: int, levels: int, wavelet, band_dtype: int,
+                    scheme: str = "nonsep") -> int:
+    n = _lib().dwt2_workspace_bytes_scheme(H, W, levels, _wid(wavelet), band_dtype,
+                                           SCHEMES[scheme])
+    if n == 0:
+        raise Dwt2Error(1, "dwt2_workspace_bytes")
+    return n
+
+
+def new_workspace(nbytes: int, device=None) -> torch.Tensor:
+    """A device workspace whose status header is zeroed."""
+    ws = torch.empty(nbytes, dtype=torch.uint8, device=device or "cuda")
+    rc = _lib().dwt2_workspace_init(ws.data_ptr(), nbytes, _stream_ptr())
+    if rc:
+        raise Dwt2Error(rc, "dwt2_workspace_init")
+    return ws
+
+
+def check_status(ws: torch.Tensor) -> int:
+    """Synchronise, read and clear the workspace status word (0 = ok, 5 = a wait timed out)."""
+    return _lib().dwt2_check_status(ws.data_ptr(), _stream_ptr())
+
+
+@dataclass
+class Coeffs:
+    """A coefficient buffer and its band views (band-list order: LL_J, then HL_j, LH_j, HH_j
+    for j = J..1)."""
+    buffer: torch.Tensor
+    H: int
+    W: int
+    wavelet: int
+    levels: int
+    band_dtype: int
+    layout: list = field(default_factory=list)
+
+    def band_views(self):
+        out = []
+        for b in self.layout:
+            dt = DT_TORCH[b.dtype]
+            es = ESIZE[b.dtype]
+            if b.h == 0 or b.w == 0:
+                out.append(torch.empty((b.h, b.w), dtype=dt, device=self.buffer.device))
+                continue
+            raw = self.buffer[b.offset_bytes:b.offset_bytes + b.h * b.pitch_bytes]
+            out.append(raw.view(dt).view(b.h, b.pitch_bytes // es)[:, :b.w])
+        return out
+
+    def band(self, kind: str, level: int):
+        k = {"LL": b"A", "HL": b"H", "LH": b"V", "HH": b"D"}[kind]
+        for b, v in zip(self.layout, self.band_views()):
+            if b.kind == k and b.level == level:
+                return v
+        raise KeyError((kind, level))
+
+
+def _check_img(x: torch.Tensor):
+    if not x.is_cuda:
+        raise ValueError("dwt2 needs a CUDA tensor (there is no CPU implementation)")
+    if x.dim() != 2 or x.stride(1) != 1:
+        raise ValueError("image must be 2-D with unit column stride")
+    if x.dtype not in TORCH_DT:
+        raise ValueError(f"unsupported dtype {x.dtype}")
+
+
+def alloc_coeffs(H, W, levels, wavelet, band_dtype, device) -> Coeffs:
+    lay, nbytes = layout(H, W, levels, band_dtype)
+    buf = torch.empty(max(nbytes, 16), dtype=torch.uint8, device=device)
+    return Coeffs(buf, H, W, _wid(wavelet), levels, band_dtype, lay)
+
+
+def forward(x: torch.Tensor, wavelet="cdf53", levels: int = 1, band_dtype=None,
+            scheme: str = "nonsep", out: Coeffs | None = None,
+            workspace: torch.Tensor | None = None, stream=None) -> Coeffs:
+    """dwt2_forward / dwt2_forward_scheme on a CUDA image; returns the coefficient buffer."""
+    _check_img(x)
+    H, W = x.shape
+    wid = _wid(wavelet)
+    img_dt = TORCH_DT[x.dtype]
+    bdt = TORCH_DT[band_dtype] if isinstance(band_dtype, torch.dtype) else (
+        band_dtype if band_dtype is not None else img_dt)
+    if out is None:
+        out = alloc_coeffs(H, W, levels, wid, bdt, x.device)
+    nws = workspace_bytes(H, W, levels, wid, bdt, scheme)
+    if workspace is None:
+        workspace = new_workspace(nws, x.device)
+    rc = _lib().dwt2_forward_scheme(
+        x.data_ptr(), x.stride(0) * x.element_size(), H, W, img_dt, out.buffer.data_ptr(),
+        workspace.data_ptr(), workspace.numel(), wid, levels, bdt, SCHEMES[scheme],
+        _stream_ptr(stream))
+    if rc:
+        raise Dwt2Error(rc, "dwt2_forward")
+    return out
+
+
+def inverse(c: Coeffs, out: torch.Tensor | None = None, img_dtype=None,
+            workspace: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """dwt2_inverse: reconstruct the H x W image from a coefficient buffer."""
+    if out is None:
+        dt = img_dtype or (torch.int32 if c.wavelet == 0 else torch.float32)
+        out = torch.empty((c.H, c.W), dtype=dt, device=c.buffer.device)
+    _check_img(out)
+    nws = workspace_bytes(c.H, c.W, c.levels, c.wavelet, c.band_dtype)
+    if workspace is None:
+        workspace = new_workspace(nws, out.device)
+    rc = _lib().dwt2_inverse(
+        c.buffer.data_ptr(), out.data_ptr(), out.stride(0) * out.element_size(), c.H, c.W,
+        TORCH_DT[out.dtype], workspace.data_ptr(), workspace.numel(), c.wavelet, c.levels,
+        c.band_dtype, _stream_ptr(stream))
+    if rc:
+        raise Dwt2Error(rc, "dwt2_inverse")
+    return out
