@@ -165,6 +165,45 @@ def run_reference(args, rank: int, world: int):
 
 
 # ------------------------------------------------------------------------------------ our arm
+def run_only(args, D, dev, x_f32, x_i32, flush, stream):
+    """One case, W warm-up and K timed calls (the command the profiler captures)."""
+    wv, x, lv, inv, scheme = {
+        "fwd_l1_cdf97": ("cdf97", x_f32, 1, False, "nonsep"),
+        "fwd_cdf97": ("cdf97", x_f32, LEVELS, False, "nonsep"),
+        "inv_cdf97": ("cdf97", x_f32, LEVELS, True, "nonsep"),
+        "fwd_cdf53_int": ("cdf53_int", x_i32, LEVELS, False, "nonsep"),
+        "inv_cdf53_int": ("cdf53_int", x_i32, LEVELS, True, "nonsep"),
+        "twopass_cdf97": ("cdf97", x_f32, LEVELS, False, "sep_twopass"),
+    }[args.only]
+    bdt = D.TORCH_DT[x.dtype]
+    c = D.alloc_coeffs(H, W, lv, wv, bdt, dev)
+    ws = D.new_workspace(D.workspace_bytes(H, W, lv, wv, bdt, scheme), dev)
+    out = torch.empty_like(x)
+    D.forward(x, wv, lv, scheme=scheme, out=c, workspace=ws)
+
+    def step():
+        if inv:
+            D.inverse(c, out=out, workspace=ws)
+        else:
+            D.forward(x, wv, lv, scheme=scheme, out=c, workspace=ws)
+
+    for _ in range(args.warmup):
+        step()
+    evs = []
+    for _ in range(args.steps):
+        flush.zero_()
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.record(stream)
+        step()
+        e.record(stream)
+        evs.append((s, e))
+    torch.cuda.synchronize()
+    ms = float(np.mean([s.elapsed_time(e) for s, e in evs]))
+    print(json.dumps({"only": args.only, "ms": ms, "levels": lv,
+                      "gb_s": alg_bytes(H, W, lv) / (ms * 1e-3) / 1e9,
+                      "status": D.check_status(ws)}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -172,6 +211,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--only", default=None,
+                    choices=["fwd_l1_cdf97", "fwd_cdf97", "inv_cdf97", "fwd_cdf53_int",
+                             "inv_cdf53_int", "twopass_cdf97"],
+                    help="run one case only (for profiler captures); prints a short line")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
@@ -209,6 +252,9 @@ def main():
     x_f32 = torch.from_numpy(field).to(dev)
     x_i32 = torch.from_numpy(field.astype(np.int32)).to(dev)
     npix = H * W
+
+    if args.only:
+        return run_only(args, D, dev, x_f32, x_i32, flush, stream)
 
     def run_case(fn, steps, warmup):
         for _ in range(warmup):

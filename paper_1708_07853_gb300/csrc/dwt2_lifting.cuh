@@ -44,245 +44,9 @@ __device__ __forceinline__ void zero_row(QRow<C>& r) {
 }
 
 // =============================================================================================
-// Non-separable scheme (Sec. 3, Eq. 5), float.
-// =============================================================================================
-
-// Spatial predict [1 0 0 0; P 1 0 0; P* 0 1 0; PP* P* P 1]: from the values before the step,
-//   HL += p (a + a[m+1]),  LH += p (a + a[n+1]),
-//   HH += p (c + c[m+1]) + p (b + b[n+1]) + p^2 (a + a[m+1] + a[n+1] + a[n+1][m+1]);
-// LL is unchanged.  push(y) consumes row n + 1 and returns row n (lag 1).
-struct PredictNS {
-    float p, pp;
-    QRow<float> x;
-    float xar[2], xcr[2];
-    __device__ __forceinline__ void init(float p_) {
-        p = p_;
-        pp = p_ * p_;
-        zero_row(x);
-        xar[0] = xar[1] = xcr[0] = xcr[1] = 0.f;
-    }
-    __device__ __forceinline__ void push(const QRow<float>& y, QRow<float>& o) {
-        float yar[2];
-        right_of(y.a, yar);
-#pragma unroll
-        for (int q = 0; q < 2; ++q) {
-            o.a[q] = x.a[q];
-            o.b[q] = x.b[q] + p * (x.a[q] + xar[q]);
-            o.c[q] = x.c[q] + p * (x.a[q] + y.a[q]);
-            o.e[q] = x.e[q] + p * (x.c[q] + xcr[q]) + p * (x.b[q] + y.b[q]) +
-                     pp * ((x.a[q] + xar[q]) + (y.a[q] + yar[q]));
-        }
-        x = y;
-        xar[0] = yar[0];
-        xar[1] = yar[1];
-        right_of(y.c, xcr);
-    }
-};
-
-// Spatial update [1 U U* UU*; 0 1 0 U*; 0 0 1 U; 0 0 0 1]: from the values before the step,
-//   LL += u (b[m-1] + b) + u (c[n-1] + c) + u^2 (e[n-1][m-1] + e[n-1] + e[m-1] + e),
-//   HL += u (e[n-1] + e),  LH += u (e[m-1] + e);  HH unchanged.  In place, lag 0.
-struct UpdateNS {
-    float u, uu;
-    float pc[2], pe[2], pel[2];  // previous row: c, e, e[m-1]
-    __device__ __forceinline__ void init(float u_) {
-        u = u_;
-        uu = u_ * u_;
-        pc[0] = pc[1] = pe[0] = pe[1] = pel[0] = pel[1] = 0.f;
-    }
-    __device__ __forceinline__ void push(QRow<float>& r) {
-        float bl[2], el[2];
-        left_of(r.b, bl);
-        left_of(r.e, el);
-#pragma unroll
-        for (int q = 0; q < 2; ++q) {
-            const float a = r.a[q] + u * (bl[q] + r.b[q]) + u * (pc[q] + r.c[q]) +
-                            uu * ((pel[q] + pe[q]) + (el[q] + r.e[q]));
-            const float b = r.b[q] + u * (pe[q] + r.e[q]);
-            const float c = r.c[q] + u * (el[q] + r.e[q]);
-            pc[q] = r.c[q];
-            pe[q] = r.e[q];
-            pel[q] = el[q];
-            r.a[q] = a;
-            r.b[q] = b;
-            r.c[q] = c;
-        }
-    }
-};
-
-// Inverse spatial update [1 -U -U* UU*; 0 1 0 -U*; 0 0 1 -U; 0 0 0 1] (lag 0).
-struct InvUpdateNS {
-    float u, uu;
-    float pc[2], pe[2], pel[2];
-    __device__ __forceinline__ void init(float u_) {
-        u = u_;
-        uu = u_ * u_;
-        pc[0] = pc[1] = pe[0] = pe[1] = pel[0] = pel[1] = 0.f;
-    }
-    __device__ __forceinline__ void push(QRow<float>& r) {
-        float bl[2], el[2];
-        left_of(r.b, bl);
-        left_of(r.e, el);
-#pragma unroll
-        for (int q = 0; q < 2; ++q) {
-            const float a = r.a[q] - u * (bl[q] + r.b[q]) - u * (pc[q] + r.c[q]) +
-                            uu * ((pel[q] + pe[q]) + (el[q] + r.e[q]));
-            const float b = r.b[q] - u * (pe[q] + r.e[q]);
-            const float c = r.c[q] - u * (el[q] + r.e[q]);
-            pc[q] = r.c[q];
-            pe[q] = r.e[q];
-            pel[q] = el[q];
-            r.a[q] = a;
-            r.b[q] = b;
-            r.c[q] = c;
-        }
-    }
-};
-
-// Inverse spatial predict [1 0 0 0; -P 1 0 0; -P* 0 1 0; PP* -P* -P 1] (lag 1).
-struct InvPredictNS {
-    float p, pp;
-    QRow<float> x;
-    float xar[2], xcr[2];
-    __device__ __forceinline__ void init(float p_) {
-        p = p_;
-        pp = p_ * p_;
-        zero_row(x);
-        xar[0] = xar[1] = xcr[0] = xcr[1] = 0.f;
-    }
-    __device__ __forceinline__ void push(const QRow<float>& y, QRow<float>& o) {
-        float yar[2];
-        right_of(y.a, yar);
-#pragma unroll
-        for (int q = 0; q < 2; ++q) {
-            o.a[q] = x.a[q];
-            o.b[q] = x.b[q] - p * (x.a[q] + xar[q]);
-            o.c[q] = x.c[q] - p * (x.a[q] + y.a[q]);
-            o.e[q] = x.e[q] - p * (x.b[q] + y.b[q]) - p * (x.c[q] + xcr[q]) +
-                     pp * ((x.a[q] + xar[q]) + (y.a[q] + yar[q]));
-        }
-        x = y;
-        xar[0] = yar[0];
-        xar[1] = yar[1];
-        right_of(y.c, xcr);
-    }
-};
-
-// =============================================================================================
-// Non-separable scheme, reversible integer CDF 5/3.  Sec. 2 lets horizontal and vertical steps
-// interleave freely, which holds in exact arithmetic only; with a floor in every step the fused
-// steps reproduce the floors of Eq. 3's order P, P*, U, U*.
-// =============================================================================================
-
-// Fused predict:  hl = b - ((a + a[m+1]) >> 1)          P on HL
-//                 LH = c - ((a + a[n+1]) >> 1)          P* on LH
-//                 HH = (e - ((c + c[m+1]) >> 1)) - ((hl + hl[n+1]) >> 1)   P then P* on HH
-struct PredictNSInt {
-    QRow<int32_t> x;
-    int32_t xcr[2], xhl[2];
-    __device__ __forceinline__ void init() {
-        zero_row(x);
-        xcr[0] = xcr[1] = xhl[0] = xhl[1] = 0;
-    }
-    __device__ __forceinline__ void push(const QRow<int32_t>& y, QRow<int32_t>& o) {
-        int32_t yar[2], yhl[2];
-        right_of(y.a, yar);
-#pragma unroll
-        for (int q = 0; q < 2; ++q) yhl[q] = y.b[q] - ((y.a[q] + yar[q]) >> 1);
-#pragma unroll
-        for (int q = 0; q < 2; ++q) {
-            o.a[q] = x.a[q];
-            o.b[q] = xhl[q];
-            o.c[q] = x.c[q] - ((x.a[q] + y.a[q]) >> 1);
-            const int32_t t = x.e[q] - ((x.c[q] + xcr[q]) >> 1);
-            o.e[q] = t - ((xhl[q] + yhl[q]) >> 1);
-        }
-        x = y;
-        xhl[0] = yhl[0];
-        xhl[1] = yhl[1];
-        right_of(y.c, xcr);
-    }
-};
-
-// Fused update:   lh = c + ((e[m-1] + e + 2) >> 2)                  U on LH
-//                 LL = (a + ((b[m-1] + b + 2) >> 2)) + ((lh[n-1] + lh + 2) >> 2)   U then U*
-//                 HL = b + ((e[n-1] + e + 2) >> 2)                  U* on HL
-struct UpdateNSInt {
-    int32_t plh[2], pe[2];
-    __device__ __forceinline__ void init() { plh[0] = plh[1] = pe[0] = pe[1] = 0; }
-    __device__ __forceinline__ void push(QRow<int32_t>& r) {
-        int32_t bl[2], el[2];
-        left_of(r.b, bl);
-        left_of(r.e, el);
-#pragma unroll
-        for (int q = 0; q < 2; ++q) {
-            const int32_t lh = r.c[q] + ((el[q] + r.e[q] + 2) >> 2);
-            const int32_t t = r.a[q] + ((bl[q] + r.b[q] + 2) >> 2);
-            const int32_t a = t + ((plh[q] + lh + 2) >> 2);
-            const int32_t b = r.b[q] + ((pe[q] + r.e[q] + 2) >> 2);
-            plh[q] = lh;
-            pe[q] = r.e[q];
-            r.a[q] = a;
-            r.b[q] = b;
-            r.c[q] = lh;
-        }
-    }
-};
-
-// Inverse fused update: undo U* then U, same floors, subtracted.
-struct InvUpdateNSInt {
-    int32_t pc[2], pe[2];
-    __device__ __forceinline__ void init() { pc[0] = pc[1] = pe[0] = pe[1] = 0; }
-    __device__ __forceinline__ void push(QRow<int32_t>& r) {
-        int32_t el[2], hl[2], hll[2];
-        left_of(r.e, el);
-#pragma unroll
-        for (int q = 0; q < 2; ++q) hl[q] = r.b[q] - ((pe[q] + r.e[q] + 2) >> 2);
-        left_of(hl, hll);
-#pragma unroll
-        for (int q = 0; q < 2; ++q) {
-            const int32_t t = r.a[q] - ((pc[q] + r.c[q] + 2) >> 2);
-            const int32_t c = r.c[q] - ((el[q] + r.e[q] + 2) >> 2);
-            const int32_t a = t - ((hll[q] + hl[q] + 2) >> 2);
-            pc[q] = r.c[q];
-            pe[q] = r.e[q];
-            r.a[q] = a;
-            r.b[q] = hl[q];
-            r.c[q] = c;
-        }
-    }
-};
-
-// Inverse fused predict: undo P* then P (lag 1).
-struct InvPredictNSInt {
-    QRow<int32_t> x;
-    int32_t xar[2];
-    __device__ __forceinline__ void init() {
-        zero_row(x);
-        xar[0] = xar[1] = 0;
-    }
-    __device__ __forceinline__ void push(const QRow<int32_t>& y, QRow<int32_t>& o) {
-        int32_t lh[2], lhr[2];
-#pragma unroll
-        for (int q = 0; q < 2; ++q) lh[q] = x.c[q] + ((x.a[q] + y.a[q]) >> 1);
-        right_of(lh, lhr);
-#pragma unroll
-        for (int q = 0; q < 2; ++q) {
-            const int32_t t = x.e[q] + ((x.b[q] + y.b[q]) >> 1);
-            o.a[q] = x.a[q];
-            o.b[q] = x.b[q] + ((x.a[q] + xar[q]) >> 1);
-            o.c[q] = lh[q];
-            o.e[q] = t + ((lh[q] + lhr[q]) >> 1);
-        }
-        x = y;
-        right_of(y.a, xar);
-    }
-};
-
-// =============================================================================================
-// Separable lifting (Eq. 3) evaluated in the same single pass: the four steps P, P*, U, U* one
-// after the other, each reading the previous step's result.  The comparator of the paper's
-// separable scheme on the same data path.
+// One lifting term.  Float: p (s0 + s1) and u (d0 + d1).  Reversible integer CDF 5/3: the
+// predict term is -floor((s0 + s1) / 2) and the update term floor((d0 + d1 + 2) / 4), both by
+// arithmetic shift (floor for negative values too).
 // =============================================================================================
 template <typename C>
 __device__ __forceinline__ C step_p(C s0, C s1, float p) {
@@ -301,6 +65,159 @@ __device__ __forceinline__ C step_u(C d0, C d1, float u) {
     }
 }
 
+// =============================================================================================
+// Non-separable scheme (Sec. 3, Eq. 5).
+//
+// Each fused step reads only the values before the step (one synchronisation point per step).
+// The tensor-product entries PP* and UU* are evaluated as the product of their 1-D factors
+// (P* applied to P's result, U* to U's), recomputed from the step's inputs: it is the same
+// linear map, and in fp32 it avoids the large cancelling p^2 (a + a[m+1] + a[n+1] + ...) sum of
+// the expanded form (about two bits better for CDF 9/7).  For the integer wavelet this order is
+// forced: Sec. 2 lets horizontal and vertical steps interleave freely, which holds in exact
+// arithmetic only, so the fused steps reproduce the floors of Eq. 3's order P, P*, U, U*.
+// =============================================================================================
+
+// Spatial predict [1 0 0 0; P 1 0 0; P* 0 1 0; PP* P* P 1]:
+//   hl  = b + P(a)             = b + p (a + a[m+1])
+//   LH  = c + P*(a)            = c + p (a + a[n+1])
+//   HH  = e + P(c) + P*(hl)    = e + p (c + c[m+1]) + p (hl + hl[n+1])
+//       ( = e + P(c) + P*(b) + PP*(a) )
+// LL is unchanged ("the predict step is completely responsible for HH", Sec. 3).
+// push(y) consumes quad row n + 1 and returns row n (lag 1); hl[n+1] is computed from the raw
+// row n + 1 when it arrives.
+template <typename C>
+struct PredictNS {
+    float p;
+    QRow<C> x;
+    C xhl[2], xcr[2];
+    __device__ __forceinline__ void init(float p_) {
+        p = p_;
+        zero_row(x);
+        xhl[0] = xhl[1] = xcr[0] = xcr[1] = C(0);
+    }
+    __device__ __forceinline__ void push(const QRow<C>& y, QRow<C>& o) {
+        C yar[2], yhl[2];
+        right_of(y.a, yar);
+#pragma unroll
+        for (int q = 0; q < 2; ++q) yhl[q] = y.b[q] + step_p(y.a[q], yar[q], p);
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            o.a[q] = x.a[q];
+            o.b[q] = xhl[q];
+            o.c[q] = x.c[q] + step_p(x.a[q], y.a[q], p);
+            const C t = x.e[q] + step_p(x.c[q], xcr[q], p);
+            o.e[q] = t + step_p(xhl[q], yhl[q], p);
+        }
+        x = y;
+        xhl[0] = yhl[0];
+        xhl[1] = yhl[1];
+        right_of(y.c, xcr);
+    }
+};
+
+// Spatial update [1 U U* UU*; 0 1 0 U*; 0 0 1 U; 0 0 0 1]:
+//   lh  = c + U(e)             = c + u (e[m-1] + e)
+//   LL  = a + U(b) + U*(lh)    = a + u (b[m-1] + b) + u (lh[n-1] + lh)
+//       ( = a + U(b) + U*(c) + UU*(e) )
+//   HL  = b + U*(e)            = b + u (e[n-1] + e)
+//   LH  = lh
+// HH is unchanged ("the update step is responsible for LL").  In place, lag 0.
+template <typename C>
+struct UpdateNS {
+    float u;
+    C plh[2], pe[2];  // row n - 1: lh, e
+    __device__ __forceinline__ void init(float u_) {
+        u = u_;
+        plh[0] = plh[1] = pe[0] = pe[1] = C(0);
+    }
+    __device__ __forceinline__ void push(QRow<C>& r) {
+        C bl[2], el[2];
+        left_of(r.b, bl);
+        left_of(r.e, el);
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            const C lh = r.c[q] + step_u(el[q], r.e[q], u);
+            const C t = r.a[q] + step_u(bl[q], r.b[q], u);
+            const C a = t + step_u(plh[q], lh, u);
+            const C b = r.b[q] + step_u(pe[q], r.e[q], u);
+            plh[q] = lh;
+            pe[q] = r.e[q];
+            r.a[q] = a;
+            r.b[q] = b;
+            r.c[q] = lh;
+        }
+    }
+};
+
+// Inverse spatial update [1 -U -U* UU*; 0 1 0 -U*; 0 0 1 -U; 0 0 0 1], evaluated as the
+// forward update's terms undone in reverse order (same terms, subtracted):
+//   hl = HL - u (e[n-1] + e);  t = LL - u (LH[n-1] + LH);  c = LH - u (e[m-1] + e);
+//   a  = t - u (hl[m-1] + hl).   Lag 0.
+template <typename C>
+struct InvUpdateNS {
+    float u;
+    C pc[2], pe[2];  // row n - 1: stored LH, e
+    __device__ __forceinline__ void init(float u_) {
+        u = u_;
+        pc[0] = pc[1] = pe[0] = pe[1] = C(0);
+    }
+    __device__ __forceinline__ void push(QRow<C>& r) {
+        C el[2], hl[2], hll[2];
+        left_of(r.e, el);
+#pragma unroll
+        for (int q = 0; q < 2; ++q) hl[q] = r.b[q] - step_u(pe[q], r.e[q], u);
+        left_of(hl, hll);
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            const C t = r.a[q] - step_u(pc[q], r.c[q], u);
+            const C c = r.c[q] - step_u(el[q], r.e[q], u);
+            const C a = t - step_u(hll[q], hl[q], u);
+            pc[q] = r.c[q];
+            pe[q] = r.e[q];
+            r.a[q] = a;
+            r.b[q] = hl[q];
+            r.c[q] = c;
+        }
+    }
+};
+
+// Inverse spatial predict [1 0 0 0; -P 1 0 0; -P* 0 1 0; PP* -P* -P 1], as the forward terms
+// undone in reverse order:
+//   c = LH - p (a + a[n+1]);  t = HH - p (HL + HL[n+1]);  b = HL - p (a + a[m+1]);
+//   e = t - p (c + c[m+1]).   Lag 1.
+template <typename C>
+struct InvPredictNS {
+    float p;
+    QRow<C> x;
+    C xar[2];
+    __device__ __forceinline__ void init(float p_) {
+        p = p_;
+        zero_row(x);
+        xar[0] = xar[1] = C(0);
+    }
+    __device__ __forceinline__ void push(const QRow<C>& y, QRow<C>& o) {
+        C c[2], cr[2];
+#pragma unroll
+        for (int q = 0; q < 2; ++q) c[q] = x.c[q] - step_p(x.a[q], y.a[q], p);
+        right_of(c, cr);
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            const C t = x.e[q] - step_p(x.b[q], y.b[q], p);
+            o.a[q] = x.a[q];
+            o.b[q] = x.b[q] - step_p(x.a[q], xar[q], p);
+            o.c[q] = c[q];
+            o.e[q] = t - step_p(c[q], cr[q], p);
+        }
+        x = y;
+        right_of(y.a, xar);
+    }
+};
+
+// =============================================================================================
+// Separable lifting (Eq. 3) evaluated in the same single pass: the four steps P, P*, U, U* one
+// after the other, each reading the previous step's result.  The comparator of the paper's
+// separable scheme on the same data path.
+// =============================================================================================
 // P (rows) then P* (columns); lag 1.
 template <typename C>
 struct PredictSep {
@@ -444,14 +361,14 @@ template <int MODE>
 struct FwdPipe<WV_CDF53_INT, MODE> {
     static constexpr int kLag = MODE == MODE_ROWS ? 0 : 1;
     using C = int32_t;
-    PredictNSInt pn;
-    UpdateNSInt un;
+    PredictNS<int32_t> pn;
+    UpdateNS<int32_t> un;
     PredictSep<int32_t> ps;
     UpdateSep<int32_t> us;
     PredictCol<int32_t> pcol;
     UpdateCol<int32_t> ucol;
     __device__ __forceinline__ void init() {
-        if constexpr (MODE == MODE_NONSEP) { pn.init(); un.init(); }
+        if constexpr (MODE == MODE_NONSEP) { pn.init(0.f); un.init(0.f); }
         if constexpr (MODE == MODE_SEP) { ps.init(0.f); us.init(0.f); }
         if constexpr (MODE == MODE_COLS) { pcol.init(0.f); ucol.init(0.f); }
     }
@@ -470,8 +387,8 @@ struct FwdPipe {
     static constexpr int kPairs = WV == WV_CDF97 ? 2 : 1;
     static constexpr int kLag = MODE == MODE_ROWS ? 0 : kPairs;
     using C = float;
-    PredictNS pn[kPairs];
-    UpdateNS un[kPairs];
+    PredictNS<float> pn[kPairs];
+    UpdateNS<float> un[kPairs];
     PredictSep<float> ps[kPairs];
     UpdateSep<float> us[kPairs];
     PredictCol<float> pcol[kPairs];
@@ -524,8 +441,8 @@ struct InvPipe {
     static constexpr int kPairs = WV == WV_CDF97 ? 2 : 1;
     static constexpr int kLag = kPairs;
     using C = float;
-    InvUpdateNS iu[kPairs];
-    InvPredictNS ip[kPairs];
+    InvUpdateNS<float> iu[kPairs];
+    InvPredictNS<float> ip[kPairs];
     __device__ __forceinline__ void init() {
         const float P[2] = {WV == WV_CDF97 ? k97Alpha : -0.5f, k97Gamma};
         const float U[2] = {WV == WV_CDF97 ? k97Beta : 0.25f, k97Delta};
@@ -562,11 +479,11 @@ template <>
 struct InvPipe<WV_CDF53_INT> {
     static constexpr int kLag = 1;
     using C = int32_t;
-    InvUpdateNSInt iu;
-    InvPredictNSInt ip;
+    InvUpdateNS<int32_t> iu;
+    InvPredictNS<int32_t> ip;
     __device__ __forceinline__ void init() {
-        iu.init();
-        ip.init();
+        iu.init(0.f);
+        ip.init(0.f);
     }
     __device__ __forceinline__ void push(QRow<int32_t>& r) {
         QRow<int32_t> t;

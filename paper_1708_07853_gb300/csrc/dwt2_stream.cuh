@@ -161,7 +161,8 @@ __global__ void __launch_bounds__(kThreads)
         if (TMA && lane == 0) {  // let the last copies land before the CTA can exit
             volatile int no_abort = 0;
             for (int i = max(0, issued - kStages); i < issued; ++i)
-                mbar_wait(&full[i % kStages], (i / kStages) & 1, &no_abort, args.status);
+                if (!mbar_wait(&full[i % kStages], (i / kStages) & 1, &no_abort, args.status))
+                    break;
         }
         return;
     }
@@ -328,7 +329,8 @@ __global__ void __launch_bounds__(kThreads)
         if (TMA && lane == 0) {
             volatile int no_abort = 0;
             for (int i = max(0, issued - kStages); i < issued; ++i)
-                mbar_wait(&full[i % kStages], (i / kStages) & 1, &no_abort, args.status);
+                if (!mbar_wait(&full[i % kStages], (i / kStages) & 1, &no_abort, args.status))
+                    break;
         }
         return;
     }
