@@ -168,6 +168,30 @@ int dwt2_inverse(const void* coeffs, void* img, int64_t img_pitch_bytes, int H, 
                  int img_dtype, void* workspace, size_t ws_bytes, int wavelet, int levels,
                  int band_dtype, void* stream);
 
+/* ---------------------------------------------------------------------------------------------
+ * Forward transform without a caller-provided workspace.  The paper has no counterpart: this
+ * entry point exists for callers that cannot allocate device memory (for example code whose host
+ * application owns all device memory and passes in only the input and output buffers, or a
+ * real-time loop that must never call the allocator).  Instead of a workspace it uses a scratch
+ * array of DWT2_STATIC_SCRATCH_BYTES built into the library, which every GPU that loads this part
+ * of the library keeps until the process exits.
+ *   - Arguments are those of dwt2_forward without workspace / ws_bytes.
+ *   - Returns DWT2_ENOMEM (with a message in dwt2_last_error) when the transform needs more
+ *     scratch than DWT2_STATIC_SCRATCH_BYTES, i.e. dwt2_workspace_bytes(...) of these arguments
+ *     exceeds it; 4096 x 4096 fp32 or int32 fits at any level count, and one level fits at any
+ *     size.
+ *   - It allocates nothing: no cudaMalloc, no cudaFree, no allocating library call.
+ *   - The first call on each device looks up the scratch's device address on the current
+ *     device; make that first call before any stream capture.
+ *   - Every call clears the status word at the start of the scratch on stream; the scratch keeps
+ *     the previous call's contents otherwise.  All calls share the one scratch array: calls
+ *     that may run at the same time on the GPU (other streams, other host threads) race and must
+ *     be ordered by the caller.  Device-side wait timeouts are recorded only in that scratch and
+ *     are not reported by this entry point. */
+#define DWT2_STATIC_SCRATCH_BYTES (24u << 20)
+int dwt2_forward_static(const void* img, int64_t img_pitch_bytes, int H, int W, int img_dtype,
+                        void* coeffs, int wavelet, int levels, int band_dtype, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

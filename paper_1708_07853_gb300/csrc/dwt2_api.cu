@@ -17,6 +17,9 @@ namespace dwt2 {
 // ------------------------------------------------------------------------------ utilities
 static thread_local std::string g_last_error;
 
+// Records a message for dwt2_last_error() (used by entry points in other translation units).
+void set_last_error(const char* msg) { g_last_error = msg ? msg : ""; }
+
 static int cuda_fail(cudaError_t e, const char* where) {
     g_last_error = std::string(where) + ": " + cudaGetErrorString(e);
     return DWT2_ECUDA;

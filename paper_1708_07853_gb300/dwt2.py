@@ -28,7 +28,8 @@ STATUS = {0: "ok", 1: "EINVAL", 2: "EUNSUPPORTED", 3: "ENOMEM", 4: "ECUDA", 5: "
 # Every symbol the header declares (checked by the tests without a GPU).
 EXPORTS = ["dwt2_status_string", "dwt2_last_error", "dwt2_max_levels", "dwt2_layout",
            "dwt2_workspace_bytes", "dwt2_workspace_bytes_scheme", "dwt2_workspace_init",
-           "dwt2_check_status", "dwt2_forward", "dwt2_forward_scheme", "dwt2_inverse"]
+           "dwt2_check_status", "dwt2_forward", "dwt2_forward_scheme", "dwt2_inverse",
+           "dwt2_forward_static"]
 
 
 class Dwt2Error(RuntimeError):
@@ -71,8 +72,9 @@ def _lib():
         lib.dwt2_forward.argtypes = [vp, i64, i, i, i, vp, vp, sz, i, i, i, vp]
         lib.dwt2_forward_scheme.argtypes = [vp, i64, i, i, i, vp, vp, sz, i, i, i, i, vp]
         lib.dwt2_inverse.argtypes = [vp, vp, i64, i, i, i, vp, sz, i, i, i, vp]
+        lib.dwt2_forward_static.argtypes = [vp, i64, i, i, i, vp, i, i, i, vp]
         for f in ("dwt2_max_levels", "dwt2_layout", "dwt2_workspace_init", "dwt2_check_status",
-                  "dwt2_forward", "dwt2_forward_scheme", "dwt2_inverse"):
+                  "dwt2_forward", "dwt2_forward_scheme", "dwt2_inverse", "dwt2_forward_static"):
             getattr(lib, f).restype = i
         _LIB = lib
     return _LIB
