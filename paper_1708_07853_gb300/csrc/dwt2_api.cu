@@ -150,13 +150,21 @@ static CUtensorMapDataType tm_type(int dt) {
     }
 }
 
-// A 2-D map over an h x w plane with 1-row boxes of box_w elements; false if TMA cannot
-// address the plane (alignment) or the driver rejects it.
-static bool make_map(CUtensorMap* m, const void* base, int64_t pitch, int h, int w, int dt,
-                     int box_w) {
+// A 2-D map over an h x w plane with 1-row boxes of box_w elements.
+// MAP_OK: use TMA.  MAP_INELIGIBLE: the plane cannot be addressed by TMA (base or pitch not
+// 16-byte aligned, empty plane): use the plain-load path.  MAP_ERROR: an eligible plane was
+// rejected by the driver, which is a library bug and is reported, never silently worked around.
+enum MapResult { MAP_OK = 0, MAP_INELIGIBLE = 1, MAP_ERROR = 2 };
+
+static MapResult make_map(CUtensorMap* m, const void* base, int64_t pitch, int h, int w, int dt,
+                          int box_w) {
     std::memset(m, 0, sizeof(*m));
+    if (h < 1 || w < 1 || !aligned(base, 16) || pitch % 16 != 0) return MAP_INELIGIBLE;
     auto fn = encode_fn();
-    if (!fn || h < 1 || w < 1 || !aligned(base, 16) || pitch % 16 != 0) return false;
+    if (!fn) {
+        g_last_error = "cuTensorMapEncodeTiled is not available from the driver";
+        return MAP_ERROR;
+    }
     cuuint64_t dims[2] = {cuuint64_t(w), cuuint64_t(h)};
     cuuint64_t strides[1] = {cuuint64_t(pitch)};
     cuuint32_t box[2] = {cuuint32_t(box_w), 1};
@@ -164,7 +172,13 @@ static bool make_map(CUtensorMap* m, const void* base, int64_t pitch, int h, int
     CUresult r = fn(m, tm_type(dt), 2, const_cast<void*>(base), dims, strides, box, estr,
                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    return r == CUDA_SUCCESS;
+    if (r != CUDA_SUCCESS) {
+        g_last_error = "cuTensorMapEncodeTiled failed (CUresult " + std::to_string(int(r)) +
+                       ") for a " + std::to_string(h) + "x" + std::to_string(w) + " plane, box " +
+                       std::to_string(box_w);
+        return MAP_ERROR;
+    }
+    return MAP_OK;
 }
 
 // ------------------------------------------------------------------------------ validation
@@ -247,7 +261,9 @@ static int forward_impl(const void* img, int64_t img_pitch, int H, int W, int im
         if (scheme == DWT2_SCHEME_SEP_TWOPASS) {
             // row pass into the full-size plane, then the column pass into the bands
             CUtensorMap tm;
-            bool tma = make_map(&tm, in, in_pitch, h, w, in_dt, kBoxW);
+            MapResult mr = make_map(&tm, in, in_pitch, h, w, in_dt, kBoxW);
+            if (mr == MAP_ERROR) return DWT2_EINTERNAL;
+            bool tma = mr == MAP_OK;
             FwdArgs r = a;
             r.ll = {wb + wp.off[2], wp.pitch[2]};
             e = launch_fwd(wavelet, MODE_ROWS, in_dt, band_dtype, tma, tm, r, st);
@@ -257,12 +273,16 @@ static int forward_impl(const void* img, int64_t img_pitch, int H, int W, int im
             c.hl = a.hl;
             c.lh = a.lh;
             c.hh = a.hh;
-            tma = make_map(&tm, wb + wp.off[2], wp.pitch[2], h, w, ll_dt, kBoxW);
+            mr = make_map(&tm, wb + wp.off[2], wp.pitch[2], h, w, ll_dt, kBoxW);
+            if (mr == MAP_ERROR) return DWT2_EINTERNAL;
+            tma = mr == MAP_OK;
             e = launch_fwd(wavelet, MODE_COLS, ll_dt, band_dtype, tma, tm, c, st);
             if (e != cudaSuccess) return cuda_fail(e, "column pass");
         } else {
             CUtensorMap tm;
-            const bool tma = make_map(&tm, in, in_pitch, h, w, in_dt, kBoxW);
+            const MapResult mr = make_map(&tm, in, in_pitch, h, w, in_dt, kBoxW);
+            if (mr == MAP_ERROR) return DWT2_EINTERNAL;
+            const bool tma = mr == MAP_OK;
             const int mode = scheme == DWT2_SCHEME_NONSEP ? MODE_NONSEP : MODE_SEP;
             e = launch_fwd(wavelet, mode, in_dt, band_dtype, tma, tm, a, st);
             if (e == cudaErrorNotSupported) return DWT2_EUNSUPPORTED;
@@ -332,13 +352,20 @@ static int inverse_impl(const void* coeffs, void* img, int64_t img_pitch, int H,
         const size_t vbytes = 4 * esize(out_dt);
         a.out_vec = aligned(a.out.ptr, vbytes) && a.out.pitch % int64_t(vbytes) == 0;
 
+        // TMA needs all four band planes non-empty (h, w >= 2); the plain-load path covers the
+        // rest (and planes whose base or pitch TMA cannot address).
         CUtensorMap tm[4];
         bool tma = h >= 2 && w >= 2;
         if (tma) {
-            tma = make_map(&tm[0], a.band[0], a.band_pitch[0], a.ner, a.nec, ll_dt, kBRow) &&
-                  make_map(&tm[1], a.band[1], a.band_pitch[1], a.ner, a.ndc, band_dtype, kBRow) &&
-                  make_map(&tm[2], a.band[2], a.band_pitch[2], a.ndr, a.nec, band_dtype, kBRow) &&
-                  make_map(&tm[3], a.band[3], a.band_pitch[3], a.ndr, a.ndc, band_dtype, kBRow);
+            const MapResult r[4] = {
+                make_map(&tm[0], a.band[0], a.band_pitch[0], a.ner, a.nec, ll_dt, kBoxW),
+                make_map(&tm[1], a.band[1], a.band_pitch[1], a.ner, a.ndc, band_dtype, kBoxW),
+                make_map(&tm[2], a.band[2], a.band_pitch[2], a.ndr, a.nec, band_dtype, kBoxW),
+                make_map(&tm[3], a.band[3], a.band_pitch[3], a.ndr, a.ndc, band_dtype, kBoxW)};
+            for (int k = 0; k < 4; ++k) {
+                if (r[k] == MAP_ERROR) return DWT2_EINTERNAL;
+                if (r[k] != MAP_OK) tma = false;
+            }
         }
         if (!tma) std::memset(tm, 0, sizeof(tm));
         cudaError_t e = launch_inv(wavelet, band_dtype, out_dt, tma, tm, a, st);

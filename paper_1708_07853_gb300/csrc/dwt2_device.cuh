@@ -93,6 +93,16 @@ __device__ __forceinline__ void prefetch_tensormap(const CUtensorMap* map) {
     asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(map)) : "memory");
 }
 
+// Programmatic dependent launch: wait until the grid this one depends on (the previous level)
+// has completed and its memory is visible; then let the next grid start its own prologue.  Both
+// are no-ops for a grid launched without the programmatic-serialization attribute.
+__device__ __forceinline__ void grid_dependency_wait() {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+__device__ __forceinline__ void allow_dependent_launch() {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 // ------------------------------------------------------------------ whole-sample reflection
 // Index i of the whole-sample symmetric extension of a length-n signal (period 2n - 2, mirrored
 // about samples 0 and n - 1); n == 1 maps everything to 0.
@@ -182,18 +192,53 @@ __device__ __forceinline__ void st4(T* p, C v0, C v1, C v2, C v3) {
 }
 
 // ------------------------------------------------------------------ warp neighbour exchange
-// Each lane owns two adjacent quads (q = 0, 1).  right_of gives the value of quad m + 1 for
-// both of the lane's quads, left_of the value of quad m - 1.  Lanes 0 and 31 are halo lanes
-// whose out-of-warp neighbour values are never used for a stored result.
-template <typename C>
-__device__ __forceinline__ void right_of(const C (&v)[2], C (&r)[2]) {
-    r[0] = v[1];
-    r[1] = __shfl_down_sync(kFull, v[0], 1);
+// Each lane owns N adjacent quads (q = 0 .. N-1).  right_of gives the value of quad m + 1 for
+// every quad of the lane, left_of the value of quad m - 1; the one value that crosses into the
+// next / previous lane moves by warp shuffle.  Lanes 0 and 31 are halo lanes whose out-of-warp
+// neighbour values are never used for a stored result.
+template <typename C, int N>
+__device__ __forceinline__ void right_of(const C (&v)[N], C (&r)[N]) {
+#pragma unroll
+    for (int q = 0; q + 1 < N; ++q) r[q] = v[q + 1];
+    r[N - 1] = __shfl_down_sync(kFull, v[0], 1);
 }
-template <typename C>
-__device__ __forceinline__ void left_of(const C (&v)[2], C (&l)[2]) {
-    l[1] = v[0];
-    l[0] = __shfl_up_sync(kFull, v[1], 1);
+template <typename C, int N>
+__device__ __forceinline__ void left_of(const C (&v)[N], C (&l)[N]) {
+#pragma unroll
+    for (int q = N - 1; q > 0; --q) l[q] = v[q - 1];
+    l[0] = __shfl_up_sync(kFull, v[N - 1], 1);
+}
+
+// N consecutive elements (N = 2, 4, 8) from aligned shared memory.
+template <int N, typename T, typename C>
+__device__ __forceinline__ void ldN(const T* p, C (&v)[N]) {
+    if constexpr (N == 2) {
+        ld2(p, v);
+    } else if constexpr (N == 4) {
+        ld4(p, v);
+    } else {
+        C a[4], b[4];
+        ld4(p, a);
+        ld4(p + 4, b);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            v[k] = a[k];
+            v[4 + k] = b[k];
+        }
+    }
+}
+
+// N consecutive elements (N = 2, 4, 8) to aligned global memory.
+template <int N, typename T, typename C>
+__device__ __forceinline__ void stN(T* p, const C (&v)[N]) {
+    if constexpr (N == 2) {
+        st2(p, v[0], v[1]);
+    } else if constexpr (N == 4) {
+        st4(p, v[0], v[1], v[2], v[3]);
+    } else {
+        st4(p, v[0], v[1], v[2], v[3]);
+        st4(p + 4, v[4], v[5], v[6], v[7]);
+    }
 }
 
 }  // namespace dwt2

@@ -1,6 +1,6 @@
 // dwt2_lifting.cuh -- the lifting arithmetic of one decomposition level, as row-streaming stages.
 //
-// Data model: a lane owns two adjacent polyphase quads (q = 0, 1) of one quad row,
+// Data model: a lane owns kQ adjacent polyphase quads (q = 0 .. kQ-1) of one quad row,
 //   a = LL = x[2n][2m], b = HL = x[2n][2m+1], c = LH = x[2n+1][2m], e = HH = x[2n+1][2m+1]
 // (the quad [LL, HL, LH, HH] of Sec. 2).  Horizontal neighbours (quad m +/- 1) come from the
 // adjacent lane by warp shuffle; vertical neighbours (quad row n +/- 1) are the rows pushed
@@ -20,6 +20,8 @@
 
 namespace dwt2 {
 
+constexpr int kQ = 2;  // polyphase quads per lane (adjacent along a row)
+
 enum Wavelet { WV_CDF53_INT = 0, WV_CDF53 = 1, WV_CDF97 = 2 };
 enum Mode { MODE_NONSEP = 0, MODE_SEP = 1, MODE_ROWS = 2, MODE_COLS = 3 };
 
@@ -34,13 +36,13 @@ constexpr float k97High = k97K / 2.0f;
 
 template <typename C>
 struct QRow {
-    C a[2], b[2], c[2], e[2];
+    C a[kQ], b[kQ], c[kQ], e[kQ];
 };
 
 template <typename C>
 __device__ __forceinline__ void zero_row(QRow<C>& r) {
 #pragma unroll
-    for (int q = 0; q < 2; ++q) r.a[q] = r.b[q] = r.c[q] = r.e[q] = C(0);
+    for (int q = 0; q < kQ; ++q) r.a[q] = r.b[q] = r.c[q] = r.e[q] = C(0);
 }
 
 // =============================================================================================
@@ -89,19 +91,20 @@ template <typename C>
 struct PredictNS {
     float p;
     QRow<C> x;
-    C xhl[2], xcr[2];
+    C xhl[kQ], xcr[kQ];
     __device__ __forceinline__ void init(float p_) {
         p = p_;
         zero_row(x);
-        xhl[0] = xhl[1] = xcr[0] = xcr[1] = C(0);
+#pragma unroll
+        for (int q = 0; q < kQ; ++q) xhl[q] = xcr[q] = C(0);
     }
     __device__ __forceinline__ void push(const QRow<C>& y, QRow<C>& o) {
-        C yar[2], yhl[2];
+        C yar[kQ], yhl[kQ];
         right_of(y.a, yar);
 #pragma unroll
-        for (int q = 0; q < 2; ++q) yhl[q] = y.b[q] + step_p(y.a[q], yar[q], p);
+        for (int q = 0; q < kQ; ++q) yhl[q] = y.b[q] + step_p(y.a[q], yar[q], p);
 #pragma unroll
-        for (int q = 0; q < 2; ++q) {
+        for (int q = 0; q < kQ; ++q) {
             o.a[q] = x.a[q];
             o.b[q] = xhl[q];
             o.c[q] = x.c[q] + step_p(x.a[q], y.a[q], p);
@@ -109,8 +112,8 @@ struct PredictNS {
             o.e[q] = t + step_p(xhl[q], yhl[q], p);
         }
         x = y;
-        xhl[0] = yhl[0];
-        xhl[1] = yhl[1];
+#pragma unroll
+        for (int q = 0; q < kQ; ++q) xhl[q] = yhl[q];
         right_of(y.c, xcr);
     }
 };
@@ -125,17 +128,18 @@ struct PredictNS {
 template <typename C>
 struct UpdateNS {
     float u;
-    C plh[2], pe[2];  // row n - 1: lh, e
+    C plh[kQ], pe[kQ];  // row n - 1: lh, e
     __device__ __forceinline__ void init(float u_) {
         u = u_;
-        plh[0] = plh[1] = pe[0] = pe[1] = C(0);
+#pragma unroll
+        for (int q = 0; q < kQ; ++q) plh[q] = pe[q] = C(0);
     }
     __device__ __forceinline__ void push(QRow<C>& r) {
-        C bl[2], el[2];
+        C bl[kQ], el[kQ];
         left_of(r.b, bl);
         left_of(r.e, el);
 #pragma unroll
-        for (int q = 0; q < 2; ++q) {
+        for (int q = 0; q < kQ; ++q) {
             const C lh = r.c[q] + step_u(el[q], r.e[q], u);
             const C t = r.a[q] + step_u(bl[q], r.b[q], u);
             const C a = t + step_u(plh[q], lh, u);
@@ -156,19 +160,20 @@ struct UpdateNS {
 template <typename C>
 struct InvUpdateNS {
     float u;
-    C pc[2], pe[2];  // row n - 1: stored LH, e
+    C pc[kQ], pe[kQ];  // row n - 1: stored LH, e
     __device__ __forceinline__ void init(float u_) {
         u = u_;
-        pc[0] = pc[1] = pe[0] = pe[1] = C(0);
+#pragma unroll
+        for (int q = 0; q < kQ; ++q) pc[q] = pe[q] = C(0);
     }
     __device__ __forceinline__ void push(QRow<C>& r) {
-        C el[2], hl[2], hll[2];
+        C el[kQ], hl[kQ], hll[kQ];
         left_of(r.e, el);
 #pragma unroll
-        for (int q = 0; q < 2; ++q) hl[q] = r.b[q] - step_u(pe[q], r.e[q], u);
+        for (int q = 0; q < kQ; ++q) hl[q] = r.b[q] - step_u(pe[q], r.e[q], u);
         left_of(hl, hll);
 #pragma unroll
-        for (int q = 0; q < 2; ++q) {
+        for (int q = 0; q < kQ; ++q) {
             const C t = r.a[q] - step_u(pc[q], r.c[q], u);
             const C c = r.c[q] - step_u(el[q], r.e[q], u);
             const C a = t - step_u(hll[q], hl[q], u);
@@ -189,19 +194,20 @@ template <typename C>
 struct InvPredictNS {
     float p;
     QRow<C> x;
-    C xar[2];
+    C xar[kQ];
     __device__ __forceinline__ void init(float p_) {
         p = p_;
         zero_row(x);
-        xar[0] = xar[1] = C(0);
+#pragma unroll
+        for (int q = 0; q < kQ; ++q) xar[q] = C(0);
     }
     __device__ __forceinline__ void push(const QRow<C>& y, QRow<C>& o) {
-        C c[2], cr[2];
+        C c[kQ], cr[kQ];
 #pragma unroll
-        for (int q = 0; q < 2; ++q) c[q] = x.c[q] - step_p(x.a[q], y.a[q], p);
+        for (int q = 0; q < kQ; ++q) c[q] = x.c[q] - step_p(x.a[q], y.a[q], p);
         right_of(c, cr);
 #pragma unroll
-        for (int q = 0; q < 2; ++q) {
+        for (int q = 0; q < kQ; ++q) {
             const C t = x.e[q] - step_p(x.b[q], y.b[q], p);
             o.a[q] = x.a[q];
             o.b[q] = x.b[q] - step_p(x.a[q], xar[q], p);
@@ -228,16 +234,16 @@ struct PredictSep {
         zero_row(x);
     }
     __device__ __forceinline__ void push(QRow<C> y, QRow<C>& o) {
-        C ar[2], cr[2];
+        C ar[kQ], cr[kQ];
         right_of(y.a, ar);
         right_of(y.c, cr);
 #pragma unroll
-        for (int q = 0; q < 2; ++q) {  // P on the new row
+        for (int q = 0; q < kQ; ++q) {  // P on the new row
             y.b[q] += step_p(y.a[q], ar[q], p);
             y.e[q] += step_p(y.c[q], cr[q], p);
         }
 #pragma unroll
-        for (int q = 0; q < 2; ++q) {  // P* on the row above, now that its lower neighbour is known
+        for (int q = 0; q < kQ; ++q) {  // P* on the row above, now that its lower neighbour is known
             o.a[q] = x.a[q];
             o.b[q] = x.b[q];
             o.c[q] = x.c[q] + step_p(x.a[q], y.a[q], p);
@@ -251,22 +257,23 @@ struct PredictSep {
 template <typename C>
 struct UpdateSep {
     float u;
-    C pc[2], pe[2];
+    C pc[kQ], pe[kQ];
     __device__ __forceinline__ void init(float u_) {
         u = u_;
-        pc[0] = pc[1] = pe[0] = pe[1] = C(0);
+#pragma unroll
+        for (int q = 0; q < kQ; ++q) pc[q] = pe[q] = C(0);
     }
     __device__ __forceinline__ void push(QRow<C>& r) {
-        C bl[2], el[2];
+        C bl[kQ], el[kQ];
         left_of(r.b, bl);
         left_of(r.e, el);
 #pragma unroll
-        for (int q = 0; q < 2; ++q) {  // U
+        for (int q = 0; q < kQ; ++q) {  // U
             r.a[q] += step_u(bl[q], r.b[q], u);
             r.c[q] += step_u(el[q], r.e[q], u);
         }
 #pragma unroll
-        for (int q = 0; q < 2; ++q) {  // U*
+        for (int q = 0; q < kQ; ++q) {  // U*
             r.a[q] += step_u(pc[q], r.c[q], u);
             r.b[q] += step_u(pe[q], r.e[q], u);
             pc[q] = r.c[q];
@@ -279,29 +286,29 @@ struct UpdateSep {
 template <typename C, int WV>
 __device__ __forceinline__ void rows_only(QRow<C>& r) {
     constexpr int npairs = WV == WV_CDF97 ? 2 : 1;
-    const float ps[2] = {WV == WV_CDF97 ? k97Alpha : -0.5f, k97Gamma};
-    const float us[2] = {WV == WV_CDF97 ? k97Beta : 0.25f, k97Delta};
+    const float ps[kQ] = {WV == WV_CDF97 ? k97Alpha : -0.5f, k97Gamma};
+    const float us[kQ] = {WV == WV_CDF97 ? k97Beta : 0.25f, k97Delta};
 #pragma unroll
     for (int k = 0; k < npairs; ++k) {
-        C ar[2], cr[2], bl[2], el[2];
+        C ar[kQ], cr[kQ], bl[kQ], el[kQ];
         right_of(r.a, ar);
         right_of(r.c, cr);
 #pragma unroll
-        for (int q = 0; q < 2; ++q) {
+        for (int q = 0; q < kQ; ++q) {
             r.b[q] += step_p(r.a[q], ar[q], ps[k]);
             r.e[q] += step_p(r.c[q], cr[q], ps[k]);
         }
         left_of(r.b, bl);
         left_of(r.e, el);
 #pragma unroll
-        for (int q = 0; q < 2; ++q) {
+        for (int q = 0; q < kQ; ++q) {
             r.a[q] += step_u(bl[q], r.b[q], us[k]);
             r.c[q] += step_u(el[q], r.e[q], us[k]);
         }
     }
     if constexpr (WV == WV_CDF97) {
 #pragma unroll
-        for (int q = 0; q < 2; ++q) {
+        for (int q = 0; q < kQ; ++q) {
             r.a[q] *= k97Low;
             r.c[q] *= k97Low;
             r.b[q] *= k97High;
@@ -321,7 +328,7 @@ struct PredictCol {
     }
     __device__ __forceinline__ void push(const QRow<C>& y, QRow<C>& o) {
 #pragma unroll
-        for (int q = 0; q < 2; ++q) {
+        for (int q = 0; q < kQ; ++q) {
             o.a[q] = x.a[q];
             o.b[q] = x.b[q];
             o.c[q] = x.c[q] + step_p(x.a[q], y.a[q], p);
@@ -333,14 +340,15 @@ struct PredictCol {
 template <typename C>
 struct UpdateCol {
     float u;
-    C pc[2], pe[2];
+    C pc[kQ], pe[kQ];
     __device__ __forceinline__ void init(float u_) {
         u = u_;
-        pc[0] = pc[1] = pe[0] = pe[1] = C(0);
+#pragma unroll
+        for (int q = 0; q < kQ; ++q) pc[q] = pe[q] = C(0);
     }
     __device__ __forceinline__ void push(QRow<C>& r) {
 #pragma unroll
-        for (int q = 0; q < 2; ++q) {
+        for (int q = 0; q < kQ; ++q) {
             r.a[q] += step_u(pc[q], r.c[q], u);
             r.b[q] += step_u(pe[q], r.e[q], u);
             pc[q] = r.c[q];
@@ -394,8 +402,8 @@ struct FwdPipe {
     PredictCol<float> pcol[kPairs];
     UpdateCol<float> ucol[kPairs];
     __device__ __forceinline__ void init() {
-        const float P[2] = {WV == WV_CDF97 ? k97Alpha : -0.5f, k97Gamma};
-        const float U[2] = {WV == WV_CDF97 ? k97Beta : 0.25f, k97Delta};
+        const float P[kQ] = {WV == WV_CDF97 ? k97Alpha : -0.5f, k97Gamma};
+        const float U[kQ] = {WV == WV_CDF97 ? k97Beta : 0.25f, k97Delta};
 #pragma unroll
         for (int k = 0; k < kPairs; ++k) {
             if constexpr (MODE == MODE_NONSEP) { pn[k].init(P[k]); un[k].init(U[k]); }
@@ -423,7 +431,7 @@ struct FwdPipe {
                 constexpr float sLH = MODE == MODE_COLS ? k97High : k97High * k97Low;
                 constexpr float sHH = MODE == MODE_COLS ? k97High : k97High * k97High;
 #pragma unroll
-                for (int q = 0; q < 2; ++q) {
+                for (int q = 0; q < kQ; ++q) {
                     r.a[q] *= sLL;
                     r.b[q] *= sHL;
                     r.c[q] *= sLH;
@@ -444,8 +452,8 @@ struct InvPipe {
     InvUpdateNS<float> iu[kPairs];
     InvPredictNS<float> ip[kPairs];
     __device__ __forceinline__ void init() {
-        const float P[2] = {WV == WV_CDF97 ? k97Alpha : -0.5f, k97Gamma};
-        const float U[2] = {WV == WV_CDF97 ? k97Beta : 0.25f, k97Delta};
+        const float P[kQ] = {WV == WV_CDF97 ? k97Alpha : -0.5f, k97Gamma};
+        const float U[kQ] = {WV == WV_CDF97 ? k97Beta : 0.25f, k97Delta};
 #pragma unroll
         for (int k = 0; k < kPairs; ++k) {
             iu[k].init(U[kPairs - 1 - k]);
@@ -458,7 +466,7 @@ struct InvPipe {
             constexpr float sHL = 1.0f / (k97Low * k97High);
             constexpr float sHH = 1.0f / (k97High * k97High);
 #pragma unroll
-            for (int q = 0; q < 2; ++q) {
+            for (int q = 0; q < kQ; ++q) {
                 r.a[q] *= sLL;
                 r.b[q] *= sHL;
                 r.c[q] *= sHL;

@@ -4,9 +4,9 @@
 // results with vector stores.  One HBM read of the input and one write of the output per level.
 //
 // Geometry (all in polyphase quads; a quad is 2 x 2 pixels):
-//   CTA   = a strip of kCtaQ = 240 output quad columns x rpc output quad rows;
-//   warp  = a window of 64 quad columns (32 lanes x 2 quads) whose 2 outer quads on each side are
-//           halo (lanes 0 and 31 compute but never store), i.e. 60 output quads per warp;
+//   CTA   = a strip of kCtaQ output quad columns (4 warps x 30 lanes x kQ) x rpc quad rows;
+//   warp  = a window of 32 x kQ quad columns (kQ adjacent quads per lane); lanes 0 and 31 are halo
+//           (they compute but never store: the lifting reaches 2 quads to each side);
 //   rows  = the CTA streams its rpc rows plus 2 halo quad rows above and below.
 // Boundaries: the producer maps every (extended) row to its whole-sample-symmetric source row;
 // warps whose window crosses the left or right image edge read each column from its mirrored
@@ -18,22 +18,26 @@
 namespace dwt2 {
 
 constexpr int kNW = 4;                   // consumer warps per CTA
-constexpr int kHQ = 2;                   // halo quads on each side of a warp window
-constexpr int kWarpQ = 64;               // quads in a warp window
-constexpr int kWarpOut = kWarpQ - 2 * kHQ;  // 60 output quads per warp
-constexpr int kCtaQ = kNW * kWarpOut;    // 240 output quads per CTA strip
+constexpr int kHQ = kQ;                  // halo quads on each side of a warp window (one lane)
+constexpr int kWarpQ = 32 * kQ;          // quads in a warp window
+constexpr int kWarpOut = kWarpQ - 2 * kHQ;  // output quads per warp (30 lanes)
+constexpr int kCtaQ = kNW * kWarpOut;    // output quads per CTA strip
 constexpr int kThreads = 32 * (kNW + 1);
 constexpr int kStages = 8;               // quad rows in flight per CTA
 constexpr int kVHalo = 2;                // halo quad rows above and below a CTA's rows
 
 // Forward: a stage holds 2 pixel rows of the strip's pixel columns [2*qx0 - kXL, +kSRow), loaded
-// as two 256-wide boxes per row (every TMA destination starts on a 128-byte boundary).
+// as 256-wide boxes (every TMA destination starts on a 128-byte boundary).
 constexpr int kXL = 8;
 constexpr int kBoxW = 256;
-constexpr int kSRow = 2 * kBoxW;  // 512 >= kXL + 2*kCtaQ + 2*kHQ
+constexpr int kBoxes = (kXL + 2 * kCtaQ + 2 * kHQ + kBoxW - 1) / kBoxW;
+constexpr int kSRow = kBoxes * kBoxW;
 // Inverse: a stage holds one row of each band, quad columns [qx0 - kXLB, +kBRow).
 constexpr int kXLB = 8;
-constexpr int kBRow = 256;  // >= kXLB + kCtaQ + kHQ, one TMA box
+constexpr int kBBoxes = (kXLB + kCtaQ + kHQ + kBoxW - 1) / kBoxW;
+constexpr int kBRow = kBBoxes * kBoxW;
+static_assert(kSRow >= kXL + 2 * kCtaQ + 2 * kHQ, "forward stage row too short");
+static_assert(kBRow >= kXLB + kCtaQ + kHQ, "inverse stage row too short");
 
 struct PlaneOut {
     void* ptr;
@@ -66,11 +70,17 @@ __device__ __forceinline__ T* row_ptr(const PlaneOut& p, int r) {
     return reinterpret_cast<T*>(static_cast<char*>(p.ptr) + static_cast<int64_t>(r) * p.pitch);
 }
 
-// Stores two adjacent quads' values of one band row (aligned pair, clipped at the band width).
-template <typename T, typename C>
-__device__ __forceinline__ void put2(T* p, C v0, C v1, int m0, int width) {
-    if (m0 + 1 < width) st2(p, v0, v1);
-    else if (m0 < width) *p = from_c<T>(v0);
+// Stores N consecutive values of an output row starting at column c0 (an aligned vector store
+// when allowed and wholly inside the row, else element by element, clipped at the width).
+template <int N, typename T, typename C>
+__device__ __forceinline__ void putN(T* p, const C (&v)[N], int c0, int width, bool vec) {
+    if (vec && c0 + N - 1 < width) {
+        stN<N>(p, v);
+    } else {
+#pragma unroll
+        for (int k = 0; k < N; ++k)
+            if (c0 + k >= 0 && c0 + k < width) p[k] = from_c<T>(v[k]);
+    }
 }
 
 // Bytes of dynamic shared memory of the kernels (+128 to align the base to 128 bytes).
@@ -123,6 +133,10 @@ __global__ void __launch_bounds__(kThreads)
     }
     if (TMA && warp == kNW && lane == 0) prefetch_tensormap(&tmap);
     __syncthreads();
+    // Everything above overlaps the previous level's tail; nothing below may touch global memory
+    // before that level has finished writing this level's input (and reading what we overwrite).
+    grid_dependency_wait();
+    allow_dependent_launch();
 
     if (warp == kNW) {  // ------------------------------------------------------ producer
         int issued = 0;
@@ -138,10 +152,11 @@ __global__ void __launch_bounds__(kThreads)
             if constexpr (TMA) {
                 if (lane == 0) {
                     mbar_arrive_expect_tx(&full[s], 2 * kSRow * sizeof(TI));
-                    tma_load_2d(dst, &tmap, &full[s], xs, r0);
-                    tma_load_2d(dst + kBoxW, &tmap, &full[s], xs + kBoxW, r0);
-                    tma_load_2d(dst + kSRow, &tmap, &full[s], xs, r1);
-                    tma_load_2d(dst + kSRow + kBoxW, &tmap, &full[s], xs + kBoxW, r1);
+#pragma unroll
+                    for (int b = 0; b < kBoxes; ++b) {
+                        tma_load_2d(dst + b * kBoxW, &tmap, &full[s], xs + b * kBoxW, r0);
+                        tma_load_2d(dst + kSRow + b * kBoxW, &tmap, &full[s], xs + b * kBoxW, r1);
+                    }
                 }
             } else {
                 const TI* row0 = reinterpret_cast<const TI*>(static_cast<const char*>(args.in) +
@@ -169,13 +184,10 @@ __global__ void __launch_bounds__(kThreads)
 
     // ------------------------------------------------------------------------- consumers
     const int wq = qx0 - kHQ + warp * kWarpOut;  // first quad of the warp window
-    const int col0 = 2 * wq + 4 * lane;          // first pixel column of this lane
+    const int m0 = wq + kQ * lane;               // first quad of this lane
+    const int col0 = 2 * m0;                     // first pixel column of this lane
     const bool edge = (2 * wq < 0) || (2 * wq + 2 * kWarpQ > args.W);
     const int sc = col0 - xs;
-    int ec[4];
-#pragma unroll
-    for (int k = 0; k < 4; ++k) ec[k] = min(max(refl(col0 + k, args.W) - xs, 0), kSRow - 1);
-    const int m0 = wq + 2 * lane;
     const bool store_lane = lane >= 1 && lane <= 30;
 
     Pipe pipe;
@@ -186,52 +198,52 @@ __global__ void __launch_bounds__(kThreads)
         if (!__all_sync(kFull, ok)) break;
         const TI* r0 = stages + size_t(s) * 2 * kSRow;
         const TI* r1 = r0 + kSRow;
-        C v0[4], v1[4];
+        C v0[2 * kQ], v1[2 * kQ];
         if (!edge) {
-            ld4(r0 + sc, v0);
-            ld4(r1 + sc, v1);
+            ldN<2 * kQ>(r0 + sc, v0);
+            ldN<2 * kQ>(r1 + sc, v1);
         } else {
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                v0[k] = to_c(r0[ec[k]]);
-                v1[k] = to_c(r1[ec[k]]);
+            for (int k = 0; k < 2 * kQ; ++k) {
+                const int c = min(max(refl(col0 + k, args.W) - xs, 0), kSRow - 1);
+                v0[k] = to_c(r0[c]);
+                v1[k] = to_c(r1[c]);
             }
         }
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty[s]);
 
         QRow<C> row;
-        row.a[0] = v0[0]; row.b[0] = v0[1]; row.a[1] = v0[2]; row.b[1] = v0[3];
-        row.c[0] = v1[0]; row.e[0] = v1[1]; row.c[1] = v1[2]; row.e[1] = v1[3];
+#pragma unroll
+        for (int q = 0; q < kQ; ++q) {
+            row.a[q] = v0[2 * q];
+            row.b[q] = v0[2 * q + 1];
+            row.c[q] = v1[2 * q];
+            row.e[q] = v1[2 * q + 1];
+        }
         pipe.push(row);
 
         const int qo = qfirst + i - Pipe::kLag;
         if (qo < n0 || qo >= n1 || !store_lane) continue;
         if constexpr (MODE == MODE_ROWS) {
-            // interleaved output plane: pixel rows 2qo (a b a b) and 2qo + 1 (c e c e)
-            const int c0 = 2 * m0;
-            TL* o0 = row_ptr<TL>(args.ll, 2 * qo) + c0;
-            if (c0 + 3 < args.W) {
-                st4(o0, row.a[0], row.b[0], row.a[1], row.b[1]);
-                if (2 * qo + 1 < args.H) {
-                    TL* o1 = row_ptr<TL>(args.ll, 2 * qo + 1) + c0;
-                    st4(o1, row.c[0], row.e[0], row.c[1], row.e[1]);
-                }
-            } else {
-                const C va[4] = {row.a[0], row.b[0], row.a[1], row.b[1]};
-                const C vc[4] = {row.c[0], row.e[0], row.c[1], row.e[1]};
-                for (int k = 0; k < 4; ++k)
-                    if (c0 + k < args.W) {
-                        o0[k] = from_c<TL>(va[k]);
-                        if (2 * qo + 1 < args.H) row_ptr<TL>(args.ll, 2 * qo + 1)[c0 + k] = from_c<TL>(vc[k]);
-                    }
+            // interleaved output plane: pixel rows 2qo (a b a b ...) and 2qo + 1 (c e c e ...)
+            C va[2 * kQ], vc[2 * kQ];
+#pragma unroll
+            for (int q = 0; q < kQ; ++q) {
+                va[2 * q] = row.a[q];
+                va[2 * q + 1] = row.b[q];
+                vc[2 * q] = row.c[q];
+                vc[2 * q + 1] = row.e[q];
             }
+            putN<2 * kQ>(row_ptr<TL>(args.ll, 2 * qo) + col0, va, col0, args.W, true);
+            if (2 * qo + 1 < args.H)
+                putN<2 * kQ>(row_ptr<TL>(args.ll, 2 * qo + 1) + col0, vc, col0, args.W, true);
         } else {
-            put2(row_ptr<TL>(args.ll, qo) + m0, row.a[0], row.a[1], m0, args.nec);
-            put2(row_ptr<TB>(args.hl, qo) + m0, row.b[0], row.b[1], m0, args.ndc);
+            putN<kQ>(row_ptr<TL>(args.ll, qo) + m0, row.a, m0, args.nec, true);
+            putN<kQ>(row_ptr<TB>(args.hl, qo) + m0, row.b, m0, args.ndc, true);
             if (qo < args.ndr) {
-                put2(row_ptr<TB>(args.lh, qo) + m0, row.c[0], row.c[1], m0, args.nec);
-                put2(row_ptr<TB>(args.hh, qo) + m0, row.e[0], row.e[1], m0, args.ndc);
+                putN<kQ>(row_ptr<TB>(args.lh, qo) + m0, row.c, m0, args.nec, true);
+                putN<kQ>(row_ptr<TB>(args.hh, qo) + m0, row.e, m0, args.ndc, true);
             }
         }
     }
@@ -277,6 +289,8 @@ __global__ void __launch_bounds__(kThreads)
         prefetch_tensormap(&tm_hh);
     }
     __syncthreads();
+    grid_dependency_wait();
+    allow_dependent_launch();
 
     auto stage_ll = [&](int s) { return reinterpret_cast<TL*>(smem + s * kStageBytes); };
     auto stage_b = [&](int s, int k) {  // k = 0 HL, 1 LH, 2 HH
@@ -299,15 +313,20 @@ __global__ void __launch_bounds__(kThreads)
             if constexpr (TMA) {
                 if (lane == 0) {
                     mbar_arrive_expect_tx(&full[s], uint32_t(kStageBytes));
-                    tma_load_2d(stage_ll(s), &tm_ll, &full[s], xb, re);
-                    tma_load_2d(stage_b(s, 0), &tm_hl, &full[s], xb, re);
-                    tma_load_2d(stage_b(s, 1), &tm_lh, &full[s], xb, ro);
-                    tma_load_2d(stage_b(s, 2), &tm_hh, &full[s], xb, ro);
+#pragma unroll
+                    for (int b = 0; b < kBBoxes; ++b) {
+                        const int x = xb + b * kBoxW;
+                        tma_load_2d(stage_ll(s) + b * kBoxW, &tm_ll, &full[s], x, re);
+                        tma_load_2d(stage_b(s, 0) + b * kBoxW, &tm_hl, &full[s], x, re);
+                        tma_load_2d(stage_b(s, 1) + b * kBoxW, &tm_lh, &full[s], x, ro);
+                        tma_load_2d(stage_b(s, 2) + b * kBoxW, &tm_hh, &full[s], x, ro);
+                    }
                 }
             } else {
                 const int rows[4] = {re, re, ro, ro};
                 const int widths[4] = {args.nec, args.ndc, args.nec, args.ndc};
                 const int heights[4] = {args.ner, args.ner, args.ndr, args.ndr};
+#pragma unroll
                 for (int b = 0; b < 4; ++b) {
                     const bool row_ok = rows[b] >= 0 && rows[b] < heights[b];
                     const char* src = static_cast<const char*>(args.band[b]) +
@@ -337,17 +356,10 @@ __global__ void __launch_bounds__(kThreads)
 
     // ------------------------------------------------------------------------- consumers
     const int wq = qx0 - kHQ + warp * kWarpOut;
-    const int m0 = wq + 2 * lane;
+    const int m0 = wq + kQ * lane;
     const bool edge = (2 * wq < 0) || (2 * wq + 2 * kWarpQ > args.W);
     const int sidx = m0 - xb;  // smem index of the lane's first quad (fast path)
-    int ie[2], io[2];          // edge path: smem indices of the even / odd source columns
-    bool odd_zero = args.W <= 1;
-#pragma unroll
-    for (int j = 0; j < 2; ++j) {
-        const int m = m0 + j;
-        ie[j] = min(max((refl(2 * m, args.W) >> 1) - xb, 0), kBRow - 1);
-        io[j] = odd_zero ? 0 : min(max(((refl(2 * m + 1, args.W) - 1) >> 1) - xb, 0), kBRow - 1);
-    }
+    const bool odd_zero = args.W <= 1;
     const bool store_lane = lane >= 1 && lane <= 30;
 
     Pipe pipe;
@@ -362,17 +374,22 @@ __global__ void __launch_bounds__(kThreads)
         const TB* slh = stage_b(s, 1);
         const TB* shh = stage_b(s, 2);
         if (!edge) {
-            ld2(sll + sidx, row.a);
-            ld2(shl + sidx, row.b);
-            ld2(slh + sidx, row.c);
-            ld2(shh + sidx, row.e);
+            ldN<kQ>(sll + sidx, row.a);
+            ldN<kQ>(shl + sidx, row.b);
+            ldN<kQ>(slh + sidx, row.c);
+            ldN<kQ>(shh + sidx, row.e);
         } else {
+            // even pixel column 2m -> LL / LH column; odd 2m + 1 -> HL / HH column (reflected)
 #pragma unroll
-            for (int j = 0; j < 2; ++j) {
-                row.a[j] = to_c(sll[ie[j]]);
-                row.c[j] = to_c(slh[ie[j]]);
-                row.b[j] = odd_zero ? C(0) : C(to_c(shl[io[j]]));
-                row.e[j] = odd_zero ? C(0) : C(to_c(shh[io[j]]));
+            for (int j = 0; j < kQ; ++j) {
+                const int m = m0 + j;
+                const int ie = min(max((refl(2 * m, args.W) >> 1) - xb, 0), kBRow - 1);
+                const int io =
+                    odd_zero ? 0 : min(max(((refl(2 * m + 1, args.W) - 1) >> 1) - xb, 0), kBRow - 1);
+                row.a[j] = to_c(sll[ie]);
+                row.c[j] = to_c(slh[ie]);
+                row.b[j] = odd_zero ? C(0) : C(to_c(shl[io]));
+                row.e[j] = odd_zero ? C(0) : C(to_c(shh[io]));
             }
         }
         __syncwarp();
@@ -382,22 +399,17 @@ __global__ void __launch_bounds__(kThreads)
         const int qo = qfirst + i - Pipe::kLag;
         if (qo < n0 || qo >= n1 || !store_lane) continue;
         const int c0 = 2 * m0;
-        const bool has_odd_row = 2 * qo + 1 < args.H;
-        TO* o0 = row_ptr<TO>(args.out, 2 * qo) + c0;
-        TO* o1 = row_ptr<TO>(args.out, 2 * qo + 1) + c0;
-        if (args.out_vec && c0 + 3 < args.W) {
-            st4(o0, row.a[0], row.b[0], row.a[1], row.b[1]);
-            if (has_odd_row) st4(o1, row.c[0], row.e[0], row.c[1], row.e[1]);
-        } else {
-            const C va[4] = {row.a[0], row.b[0], row.a[1], row.b[1]};
-            const C vc[4] = {row.c[0], row.e[0], row.c[1], row.e[1]};
+        C va[2 * kQ], vc[2 * kQ];
 #pragma unroll
-            for (int k = 0; k < 4; ++k)
-                if (c0 + k >= 0 && c0 + k < args.W) {
-                    o0[k] = from_c<TO>(va[k]);
-                    if (has_odd_row) o1[k] = from_c<TO>(vc[k]);
-                }
+        for (int q = 0; q < kQ; ++q) {
+            va[2 * q] = row.a[q];
+            va[2 * q + 1] = row.b[q];
+            vc[2 * q] = row.c[q];
+            vc[2 * q + 1] = row.e[q];
         }
+        putN<2 * kQ>(row_ptr<TO>(args.out, 2 * qo) + c0, va, c0, args.W, args.out_vec != 0);
+        if (2 * qo + 1 < args.H)
+            putN<2 * kQ>(row_ptr<TO>(args.out, 2 * qo + 1) + c0, vc, c0, args.W, args.out_vec != 0);
     }
 }
 
@@ -409,12 +421,14 @@ struct LaunchGeom {
     int rpc;
 };
 
-// Picks rows per CTA so that the grid fills the GPU about once (a multiple of the SM count
-// times the resident CTAs per SM) without making a CTA's 4 halo rows a large overhead.
-inline LaunchGeom pick_geometry(int ner, int nec, int sms, int ctas_per_sm) {
+// Rows per CTA.  Large planes: about one wave of CTAs (SM count x resident CTAs per SM) with at
+// least 16 quad rows each, so the 4 halo rows of a CTA stay a small overhead on HBM reads.
+// Small planes (a few MB, served from L2 after the previous level wrote them): as many CTAs as
+// fit, down to 4 rows each, because there the per-row latency of a CTA, not bytes, sets the time.
+inline LaunchGeom pick_geometry(int ner, int nec, int64_t plane_bytes, int sms, int ctas_per_sm) {
     const int strips = (nec + kCtaQ - 1) / kCtaQ;
     const int target = sms * (ctas_per_sm > 0 ? ctas_per_sm : 1);
-    const int min_rows = 16;
+    const int min_rows = plane_bytes < (int64_t(24) << 20) ? 4 : 16;
     const int rb_max = (ner + min_rows - 1) / min_rows;
     int rb = target / strips;
     if (rb < 1) rb = 1;
@@ -426,6 +440,23 @@ inline LaunchGeom pick_geometry(int ner, int nec, int sms, int ctas_per_sm) {
     g.grid = dim3(strips, rb, 1);
     g.rpc = rpc;
     return g;
+}
+
+// Launch with programmatic stream serialization (the kernels wait for their predecessor with
+// griddepcontrol.wait before touching global memory).
+template <typename K, typename... Args>
+cudaError_t launch_pdl(K kernel, dim3 grid, size_t smem, cudaStream_t st, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = dim3(kThreads, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, args...);
 }
 
 int device_sm_count();
@@ -446,10 +477,10 @@ cudaError_t launch_forward_t(const CUtensorMap& tm, FwdArgs a, cudaStream_t st) 
         cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
         return occupancy_of(k, smem);
     }();
-    const LaunchGeom g = pick_geometry(a.ner, a.nec, device_sm_count(), occ);
+    const LaunchGeom g = pick_geometry(a.ner, a.nec, int64_t(a.H) * a.W * int64_t(sizeof(TI)),
+                                       device_sm_count(), occ);
     a.rpc = g.rpc;
-    k<<<g.grid, kThreads, smem, st>>>(tm, a);
-    return cudaGetLastError();
+    return launch_pdl(k, g.grid, smem, st, tm, a);
 }
 
 template <int WV, typename TB, typename TL, typename TO, bool TMA>
@@ -460,10 +491,10 @@ cudaError_t launch_inverse_t(const CUtensorMap* tm, InvArgs a, cudaStream_t st) 
         cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
         return occupancy_of(k, smem);
     }();
-    const LaunchGeom g = pick_geometry(a.ner, a.nec, device_sm_count(), occ);
+    const LaunchGeom g = pick_geometry(a.ner, a.nec, int64_t(a.H) * a.W * int64_t(sizeof(TL)),
+                                       device_sm_count(), occ);
     a.rpc = g.rpc;
-    k<<<g.grid, kThreads, smem, st>>>(tm[0], tm[1], tm[2], tm[3], a);
-    return cudaGetLastError();
+    return launch_pdl(k, g.grid, smem, st, tm[0], tm[1], tm[2], tm[3], a);
 }
 
 }  // namespace dwt2

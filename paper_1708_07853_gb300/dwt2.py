@@ -37,7 +37,7 @@ class Dwt2Error(RuntimeError):
         self.status = status
         msg = f"{what}: {STATUS.get(status, status)}"
         err = _lib().dwt2_last_error().decode()
-        super().__init__(msg + (f" ({err})" if err and status == 4 else ""))
+        super().__init__(msg + (f" ({err})" if err and status in (3, 4, 6) else ""))
 
 
 class Band(ctypes.Structure):
