@@ -221,6 +221,60 @@ def run_only(args, D, dev, x_f32, x_i32, flush, stream):
                       "status": D.check_status(ws)}), flush=True)
 
 
+def storage_bytes(h: int, w: int, levels: int, in_es: int, band_es: int, ll_es: int = 4) -> int:
+    """Algorithmic bytes of a forward with band storage band_es: per level one read of the
+    input plane and one write of the four bands (LL planes fp32)."""
+    tot = 0
+    for j in range(levels):
+        ner, nec = (h + 1) // 2, (w + 1) // 2
+        tot += h * w * (in_es if j == 0 else ll_es) + ner * nec * ll_es + (h * w - ner * nec) * band_es
+        h, w = ner, nec
+    return tot
+
+
+def run_precision(args, D, I, dev, flush, stream):
+    """Config 3: 16384 x 16384, field + uniform noise in [0, 255], CDF 9/7, 5 levels."""
+    from oracle import oracle as O
+    O.build()
+    n, lv = 16384, LEVELS
+    x = I.field_plus_noise(n, n, I.seed_for(2))
+    want = O.forward(x.astype(np.float64), "cdf97", lv)
+    shapes = O.band_shapes(n, n, lv)
+    xg = torch.from_numpy(x).to(dev)
+    report = {}
+    for name, dt in (("f32", torch.float32), ("bf16", torch.bfloat16), ("f16", torch.float16)):
+        c = D.forward(xg, "cdf97", lv, band_dtype=dt)
+        bands = {}
+        for (kind, j, h, w), v, wv in zip(shapes, c.band_views(), want):
+            if wv.size == 0:
+                continue
+            d = v.float().cpu().numpy().astype(np.float64) - wv
+            bands[f"{kind}{j}"] = {"max": float(np.abs(d).max()), "rms": float(np.sqrt((d * d).mean()))}
+        r = D.inverse(c, img_dtype=torch.float32)
+        rd = (r.double() - xg.double())
+        ws = D.new_workspace(D.workspace_bytes(n, n, lv, "cdf97", D.TORCH_DT[dt]), dev)
+        for _ in range(args.warmup):
+            D.forward(xg, "cdf97", lv, band_dtype=dt, out=c, workspace=ws)
+        evs = []
+        for _ in range(args.steps):
+            flush()
+            s0, e0 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s0.record(stream)
+            D.forward(xg, "cdf97", lv, band_dtype=dt, out=c, workspace=ws)
+            e0.record(stream)
+            evs.append((s0, e0))
+        torch.cuda.synchronize()
+        ms = float(np.mean([a.elapsed_time(b) for a, b in evs]))
+        nbytes = storage_bytes(n, n, lv, 4, 2 if dt != torch.float32 else 4)
+        report[name] = {"bands": bands, "roundtrip_max": float(rd.abs().max()),
+                        "roundtrip_rms": float(rd.pow(2).mean().sqrt()), "ms": round(ms, 4),
+                        "gpix_s": round(n * n / (ms * 1e-3) / 1e9, 2),
+                        "algorithmic_bytes": nbytes, "gb_s": round(nbytes / (ms * 1e-3) / 1e9, 1)}
+    print(json.dumps({"precision": "16384x16384 field+noise in [0,255], CDF 9/7, 5 levels, "
+                                   "fp32 arithmetic; band storage fp32 / bf16 / fp16, LL fp32",
+                      "report": report}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -228,6 +282,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--precision", action="store_true",
+                    help="16384x16384 CDF 9/7, 5 levels: per-band error of fp32 / bf16 / fp16 band "
+                         "storage against the fp64 oracle, and the time of each")
     ap.add_argument("--only", default=None,
                     choices=["fwd_l1_cdf97", "fwd_cdf97", "inv_cdf97", "fwd_cdf53_int",
                              "inv_cdf53_int", "twopass_cdf97"],
@@ -264,6 +321,9 @@ def main():
     stream = torch.cuda.current_stream()
     l2 = torch.cuda.get_device_properties(dev).L2_cache_size
     flush = L2Flush(2 * l2, dev)
+
+    if args.precision:
+        return run_precision(args, D, I, dev, flush, stream)
 
     field = I.field(H, W, I.seed_for(1))
     x_f32 = torch.from_numpy(field).to(dev)
