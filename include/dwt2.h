@@ -168,6 +168,25 @@ int dwt2_inverse(const void* coeffs, void* img, int64_t img_pitch_bytes, int H, 
                  int img_dtype, void* workspace, size_t ws_bytes, int wavelet, int levels,
                  int band_dtype, void* stream);
 
+/* Adjoints (transposes) of the float transforms, for gradients (float wavelets, DWT2_F32 image
+ * and band storage only; the integer wavelet returns DWT2_EUNSUPPORTED).
+ *   dwt2_forward_adjoint  applies W^T, the transpose of dwt2_forward: g_coeffs (laid out by
+ *                         dwt2_layout) -> g_img (H x W).  Levels levels..1, each level the
+ *                         transposed fused steps in reverse order: the transpose of the spatial
+ *                         update (U*^T then U^T), then of the spatial predict (P*^T then P^T).
+ *   dwt2_inverse_adjoint  applies W^-T, the transpose of dwt2_inverse: g_img -> g_coeffs.
+ *                         Levels 1..levels.
+ * The whole-sample symmetric boundary of the forward becomes, in the transpose, taps that add
+ * twice into the sample a mirrored read used twice, and no reads from beyond the edge.  Padding
+ * bytes of g_coeffs (between and after band rows) are neither read nor written.  Workspace and
+ * stream as for dwt2_forward / dwt2_inverse. */
+int dwt2_forward_adjoint(const void* g_coeffs, void* g_img, int64_t g_img_pitch_bytes, int H,
+                         int W, int img_dtype, void* workspace, size_t ws_bytes, int wavelet,
+                         int levels, int band_dtype, void* stream);
+int dwt2_inverse_adjoint(const void* g_img, int64_t g_img_pitch_bytes, int H, int W, int img_dtype,
+                         void* g_coeffs, void* workspace, size_t ws_bytes, int wavelet, int levels,
+                         int band_dtype, void* stream);
+
 /* ---------------------------------------------------------------------------------------------
  * Forward transform without a caller-provided workspace.  The paper has no counterpart: this
  * entry point exists for callers that cannot allocate device memory (for example code whose host

@@ -1,0 +1,114 @@
+"""torch.autograd Functions over the library's forward / inverse transforms.
+
+Both are linear, so nothing is saved for backward but the shapes: the backward of the forward
+transform W is its transpose W^T (dwt2_forward_adjoint), the backward of the inverse W^-1 is
+W^-T (dwt2_inverse_adjoint); every level's gradient is computed by the hand-written adjoint
+kernels, from the coarsest level down (W^T) or from the finest up (W^-T).
+
+Coefficients travel as one flat float32 tensor per image, laid out exactly as dwt2_layout
+describes (fp32 storage makes every band, and the padding between rows and bands, a whole
+number of floats).  `band_views` gives the LL / HL / LH / HH planes as views into it; the
+padding entries are zero in forward outputs and in gradients.
+"""
+from __future__ import annotations
+
+import torch
+
+from . import dwt2 as D
+
+
+def coeff_floats(H: int, W: int, levels: int) -> int:
+    _, nbytes = D.layout(H, W, levels, D.DT_F32)
+    return nbytes // 4
+
+
+def band_views(c: torch.Tensor, H: int, W: int, levels: int):
+    """Band planes (LL_J, then HL_j, LH_j, HH_j for j = J..1) as views into a flat coefficient
+    tensor of shape (..., coeff_floats)."""
+    lay, _ = D.layout(H, W, levels, D.DT_F32)
+    out = []
+    for b in lay:
+        o, p = b.offset_bytes // 4, b.pitch_bytes // 4
+        if b.h == 0 or b.w == 0:
+            out.append(c[..., :0].reshape(*c.shape[:-1], b.h, b.w))
+            continue
+        out.append(c[..., o:o + b.h * p].reshape(*c.shape[:-1], b.h, p)[..., :b.w])
+    return out
+
+
+def _images(t: torch.Tensor):
+    return t.reshape(-1, t.shape[-2], t.shape[-1])
+
+
+def _check(x: torch.Tensor):
+    if not x.is_cuda or x.dtype != torch.float32:
+        raise ValueError("DWT2Fn / IDWT2Fn need float32 CUDA tensors")
+
+
+class DWT2Fn(torch.autograd.Function):
+    """c = W x for every image of x (..., H, W); c has shape (..., coeff_floats)."""
+
+    @staticmethod
+    def forward(ctx, x: torch.Tensor, wavelet: str, levels: int):
+        _check(x)
+        H, W = x.shape[-2:]
+        xs = _images(x.contiguous())
+        n = coeff_floats(H, W, levels)
+        out = torch.zeros((xs.shape[0], n), dtype=torch.float32, device=x.device)
+        ws = D.new_workspace(D.workspace_bytes(H, W, levels, wavelet, D.DT_F32), x.device)
+        lay, nbytes = D.layout(H, W, levels, D.DT_F32)
+        for i in range(xs.shape[0]):
+            c = D.Coeffs(out[i].view(torch.uint8), H, W, D._wid(wavelet), levels, D.DT_F32, lay)
+            D.forward(xs[i], wavelet, levels, out=c, workspace=ws)
+        ctx.meta = (H, W, wavelet, levels, x.shape)
+        return out.reshape(*x.shape[:-2], n)
+
+    @staticmethod
+    def backward(ctx, g: torch.Tensor):
+        H, W, wavelet, levels, xshape = ctx.meta
+        gs = g.reshape(-1, g.shape[-1]).contiguous()
+        gx = torch.empty((gs.shape[0], H, W), dtype=torch.float32, device=g.device)
+        ws = D.new_workspace(D.workspace_bytes(H, W, levels, wavelet, D.DT_F32), g.device)
+        lay, _ = D.layout(H, W, levels, D.DT_F32)
+        for i in range(gs.shape[0]):
+            c = D.Coeffs(gs[i].view(torch.uint8), H, W, D._wid(wavelet), levels, D.DT_F32, lay)
+            D.forward_adjoint(c, out=gx[i], workspace=ws)
+        return gx.reshape(xshape), None, None
+
+
+class IDWT2Fn(torch.autograd.Function):
+    """x = W^-1 c for every coefficient row of c (..., coeff_floats); x has shape (..., H, W)."""
+
+    @staticmethod
+    def forward(ctx, c: torch.Tensor, H: int, W: int, wavelet: str, levels: int):
+        _check(c)
+        cs = c.reshape(-1, c.shape[-1]).contiguous()
+        x = torch.empty((cs.shape[0], H, W), dtype=torch.float32, device=c.device)
+        ws = D.new_workspace(D.workspace_bytes(H, W, levels, wavelet, D.DT_F32), c.device)
+        lay, _ = D.layout(H, W, levels, D.DT_F32)
+        for i in range(cs.shape[0]):
+            cc = D.Coeffs(cs[i].view(torch.uint8), H, W, D._wid(wavelet), levels, D.DT_F32, lay)
+            D.inverse(cc, out=x[i], workspace=ws)
+        ctx.meta = (H, W, wavelet, levels, c.shape)
+        return x.reshape(*c.shape[:-1], H, W)
+
+    @staticmethod
+    def backward(ctx, gx: torch.Tensor):
+        H, W, wavelet, levels, cshape = ctx.meta
+        gxs = _images(gx.contiguous())
+        n = cshape[-1]
+        gc = torch.zeros((gxs.shape[0], n), dtype=torch.float32, device=gx.device)
+        ws = D.new_workspace(D.workspace_bytes(H, W, levels, wavelet, D.DT_F32), gx.device)
+        lay, _ = D.layout(H, W, levels, D.DT_F32)
+        for i in range(gxs.shape[0]):
+            out = D.Coeffs(gc[i].view(torch.uint8), H, W, D._wid(wavelet), levels, D.DT_F32, lay)
+            D.inverse_adjoint(gxs[i], wavelet, levels, out=out, workspace=ws)
+        return gc.reshape(cshape), None, None, None, None
+
+
+def dwt2(x: torch.Tensor, wavelet: str = "cdf97", levels: int = 1) -> torch.Tensor:
+    return DWT2Fn.apply(x, wavelet, levels)
+
+
+def idwt2(c: torch.Tensor, H: int, W: int, wavelet: str = "cdf97", levels: int = 1) -> torch.Tensor:
+    return IDWT2Fn.apply(c, H, W, wavelet, levels)

@@ -225,11 +225,27 @@ static cudaError_t launch_fwd(int wavelet, int mode, int ti, int tb, bool tma,
     }
 }
 
+// Per-level band scales of the CDF 9/7 normalisation (1 for CDF 5/3): per axis low 1/K, high
+// K/2, and 1 on an axis of length 1 (that axis passes through).
+static Scale4 level_scale(int wavelet, int h, int w) {
+    const double K = 1.230174104914001;
+    const bool s97 = wavelet == WV_CDF97;
+    const double vl = (s97 && h > 1) ? 1.0 / K : 1.0, vh = (s97 && h > 1) ? K / 2 : 1.0;
+    const double hl = (s97 && w > 1) ? 1.0 / K : 1.0, hh = (s97 && w > 1) ? K / 2 : 1.0;
+    return Scale4{float(vl * hl), float(vl * hh), float(vh * hl), float(vh * hh)};
+}
+
+static Scale4 reciprocal(Scale4 s) { return Scale4{1.f / s.ll, 1.f / s.hl, 1.f / s.lh, 1.f / s.hh}; }
+
+// adjoint = true: W^-T, the transpose of the inverse (image-shaped gradient in, band gradients
+// out), level by level 1..J with the forward kernel's data flow.
 static int forward_impl(const void* img, int64_t img_pitch, int H, int W, int img_dtype,
                         void* coeffs, void* ws, size_t ws_bytes, int wavelet, int J,
-                        int band_dtype, int scheme, cudaStream_t st) {
+                        int band_dtype, int scheme, cudaStream_t st, bool adjoint = false) {
     int rc = check_types(wavelet, img_dtype, band_dtype);
     if (rc) return rc;
+    if (adjoint && (wavelet == WV_CDF53_INT || img_dtype != DT_F32 || band_dtype != DT_F32))
+        return DWT2_EUNSUPPORTED;
     if (scheme < DWT2_SCHEME_NONSEP || scheme > DWT2_SCHEME_SEP_TWOPASS) return DWT2_EINVAL;
     if (scheme != DWT2_SCHEME_NONSEP && (img_dtype != band_dtype)) return DWT2_EUNSUPPORTED;
     Layout L;
@@ -284,7 +300,12 @@ static int forward_impl(const void* img, int64_t img_pitch, int H, int W, int im
             if (mr == MAP_ERROR) return DWT2_EINTERNAL;
             const bool tma = mr == MAP_OK;
             const int mode = scheme == DWT2_SCHEME_NONSEP ? MODE_NONSEP : MODE_SEP;
-            e = launch_fwd(wavelet, mode, in_dt, band_dtype, tma, tm, a, st);
+            if (adjoint) {
+                a.scale = reciprocal(level_scale(wavelet, h, w));
+                e = launch_adj_inv(wavelet, tma, tm, a, st);
+            } else {
+                e = launch_fwd(wavelet, mode, in_dt, band_dtype, tma, tm, a, st);
+            }
             if (e == cudaErrorNotSupported) return DWT2_EUNSUPPORTED;
             if (e != cudaSuccess) return cuda_fail(e, "forward level");
         }
@@ -295,11 +316,15 @@ static int forward_impl(const void* img, int64_t img_pitch, int H, int W, int im
     return DWT2_OK;
 }
 
+// adjoint = true: W^T, the transpose of the forward (band gradients in, image-shaped gradient
+// out), level by level J..1 with the inverse kernel's data flow.
 static int inverse_impl(const void* coeffs, void* img, int64_t img_pitch, int H, int W,
                         int img_dtype, void* ws, size_t ws_bytes, int wavelet, int J,
-                        int band_dtype, cudaStream_t st) {
+                        int band_dtype, cudaStream_t st, bool adjoint = false) {
     int rc = check_types(wavelet, img_dtype, band_dtype);
     if (rc) return rc;
+    if (adjoint && (wavelet == WV_CDF53_INT || img_dtype != DT_F32 || band_dtype != DT_F32))
+        return DWT2_EUNSUPPORTED;
     Layout L;
     if ((rc = make_layout(H, W, J, band_dtype, &L))) return rc;
     if ((rc = check_image(img, img_pitch, W, img_dtype))) return rc;
@@ -368,7 +393,13 @@ static int inverse_impl(const void* coeffs, void* img, int64_t img_pitch, int H,
             }
         }
         if (!tma) std::memset(tm, 0, sizeof(tm));
-        cudaError_t e = launch_inv(wavelet, band_dtype, out_dt, tma, tm, a, st);
+        cudaError_t e;
+        if (adjoint) {
+            a.scale = level_scale(wavelet, h, w);
+            e = launch_adj_fwd(wavelet, tma, tm, a, st);
+        } else {
+            e = launch_inv(wavelet, band_dtype, out_dt, tma, tm, a, st);
+        }
         if (e == cudaErrorNotSupported) return DWT2_EUNSUPPORTED;
         if (e != cudaSuccess) return cuda_fail(e, "inverse level");
     }
@@ -462,4 +493,20 @@ DWT2_EXPORT int dwt2_inverse(const void* coeffs, void* img, int64_t img_pitch_by
                              int levels, int band_dtype, void* stream) {
     return inverse_impl(coeffs, img, img_pitch_bytes, H, W, img_dtype, workspace, ws_bytes,
                         wavelet, levels, band_dtype, static_cast<cudaStream_t>(stream));
+}
+
+DWT2_EXPORT int dwt2_forward_adjoint(const void* g_coeffs, void* g_img, int64_t g_img_pitch_bytes,
+                                     int H, int W, int img_dtype, void* workspace, size_t ws_bytes,
+                                     int wavelet, int levels, int band_dtype, void* stream) {
+    return inverse_impl(g_coeffs, g_img, g_img_pitch_bytes, H, W, img_dtype, workspace, ws_bytes,
+                        wavelet, levels, band_dtype, static_cast<cudaStream_t>(stream), true);
+}
+
+DWT2_EXPORT int dwt2_inverse_adjoint(const void* g_img, int64_t g_img_pitch_bytes, int H, int W,
+                                     int img_dtype, void* g_coeffs, void* workspace,
+                                     size_t ws_bytes, int wavelet, int levels, int band_dtype,
+                                     void* stream) {
+    return forward_impl(g_img, g_img_pitch_bytes, H, W, img_dtype, g_coeffs, workspace, ws_bytes,
+                        wavelet, levels, band_dtype, DWT2_SCHEME_NONSEP,
+                        static_cast<cudaStream_t>(stream), true);
 }

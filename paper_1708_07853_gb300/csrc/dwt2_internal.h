@@ -24,4 +24,11 @@ cudaError_t launch_fwd_f97(int mode, int ti, int tb, bool tma, const CUtensorMap
 cudaError_t launch_inv(int wavelet, int tb, int to, bool tma, const CUtensorMap* tm,
                        const InvArgs& a, cudaStream_t s);
 
+// Adjoint levels (float wavelets, fp32): W_j^T with the inverse kernel's data flow, W_j^-T with
+// the forward kernel's.
+cudaError_t launch_adj_fwd(int wavelet, bool tma, const CUtensorMap* tm, const InvArgs& a,
+                           cudaStream_t s);
+cudaError_t launch_adj_inv(int wavelet, bool tma, const CUtensorMap& tm, const FwdArgs& a,
+                           cudaStream_t s);
+
 }  // namespace dwt2

@@ -23,7 +23,7 @@ namespace dwt2 {
 constexpr int kQ = 2;  // polyphase quads per lane (adjacent along a row)
 
 enum Wavelet { WV_CDF53_INT = 0, WV_CDF53 = 1, WV_CDF97 = 2 };
-enum Mode { MODE_NONSEP = 0, MODE_SEP = 1, MODE_ROWS = 2, MODE_COLS = 3 };
+enum Mode { MODE_NONSEP = 0, MODE_SEP = 1, MODE_ROWS = 2, MODE_COLS = 3, MODE_ADJ_INV = 4 };
 
 // CDF 9/7 lifting constants and the per-axis normalisation (low * 1/K, high * K/2).
 constexpr float k97Alpha = -1.586134342059924f;
@@ -353,6 +353,198 @@ struct UpdateCol {
             r.b[q] += step_u(pe[q], r.e[q], u);
             pc[q] = r.c[q];
             pe[q] = r.e[q];
+        }
+    }
+};
+
+// =============================================================================================
+// Adjoints (transposes) of the fused steps, for gradients.  The forward level is
+// W = S . U_K P_K ... U_1 P_1 (P = P* after P along rows, U = U* after U), so
+//   W^T    = P_1^T U_1^T ... P_K^T U_K^T S           (applied right to left),
+//   W^-T   = S^-1 U_K^-T P_K^-T ... U_1^-T P_1^-T,   with P^-1 = P(-p), U^-1 = U(-u).
+// The transpose of a step with the in-step symmetric reflection is not a reflected step: a
+// mirrored tap that read a sample twice now adds twice into it, and nothing is read from beyond
+// the edge.  In gather form on one axis of length N (ne even, nd odd samples):
+//   transposed predict, into even sample k:  p (w_own g_d[k] + w_left g_d[k-1])
+//       w_own  = [0 <= k < nd] (1 + [nd == ne and k == ne - 1]),  w_left = [1 <= k <= nd]
+//   transposed update, into odd sample k:    u (w_own g_s[k] + w_right g_s[k+1])
+//       w_own  = [0 <= k < nd] (1 + [k == 0]),
+//       w_right = [0 <= k < nd] ([k + 1 < ne] + [nd < ne and k == nd - 1])
+// Values outside the plane enter only with weight 0 (the loaders supply zeros there).
+// =============================================================================================
+struct AxisLen {
+    int ne, nd;
+};
+__device__ __forceinline__ float tp_own(int k, AxisLen a) {
+    return (k >= 0 && k < a.nd) ? ((a.nd == a.ne && k == a.ne - 1) ? 2.f : 1.f) : 0.f;
+}
+__device__ __forceinline__ float tp_left(int k, AxisLen a) { return (k >= 1 && k <= a.nd) ? 1.f : 0.f; }
+__device__ __forceinline__ float tu_own(int k, AxisLen a) {
+    return (k >= 0 && k < a.nd) ? (k == 0 ? 2.f : 1.f) : 0.f;
+}
+__device__ __forceinline__ float tu_right(int k, AxisLen a) {
+    return (k >= 0 && k < a.nd)
+               ? float(k + 1 < a.ne ? 1 : 0) + float(a.nd < a.ne && k == a.nd - 1 ? 1 : 0)
+               : 0.f;
+}
+
+// Per-lane horizontal weights of the lane's kQ quads (quad columns m0 .. m0 + kQ - 1).
+struct LaneW {
+    float p_own[kQ], p_left[kQ], u_own[kQ], u_right[kQ];
+    __device__ __forceinline__ void init(int m0, AxisLen cols) {
+#pragma unroll
+        for (int q = 0; q < kQ; ++q) {
+            p_own[q] = tp_own(m0 + q, cols);
+            p_left[q] = tp_left(m0 + q, cols);
+            u_own[q] = tu_own(m0 + q, cols);
+            u_right[q] = tu_right(m0 + q, cols);
+        }
+    }
+};
+
+// Transpose of the fused update: U*^T (into g_c from g_a, into g_e from g_b; reads row n + 1),
+// then U^T (into g_b from g_a, into g_e from the new g_c; reads quad m + 1).  Predict-shaped,
+// lag 1: push(row n + 1) returns row n.
+struct AdjUpdate {
+    float u;
+    QRow<float> x;
+    int xn;
+    float xar[kQ];
+    __device__ __forceinline__ void init(float u_) {
+        u = u_;
+        zero_row(x);
+        xn = -1 << 20;
+#pragma unroll
+        for (int q = 0; q < kQ; ++q) xar[q] = 0.f;
+    }
+    __device__ __forceinline__ void push(const QRow<float>& y, int yn, QRow<float>& o,
+                                         const LaneW& hw, AxisLen rows) {
+        const float wo = tu_own(xn, rows), wr = tu_right(xn, rows);
+        float gc[kQ], gcr[kQ];
+#pragma unroll
+        for (int q = 0; q < kQ; ++q) gc[q] = x.c[q] + u * (wo * x.a[q] + wr * y.a[q]);
+        right_of(gc, gcr);
+#pragma unroll
+        for (int q = 0; q < kQ; ++q) {
+            const float ge = x.e[q] + u * (wo * x.b[q] + wr * y.b[q]);
+            o.a[q] = x.a[q];
+            o.b[q] = x.b[q] + u * (hw.u_own[q] * x.a[q] + hw.u_right[q] * xar[q]);
+            o.c[q] = gc[q];
+            o.e[q] = ge + u * (hw.u_own[q] * gc[q] + hw.u_right[q] * gcr[q]);
+        }
+        x = y;
+        xn = yn;
+        right_of(y.a, xar);
+    }
+};
+
+// Transpose of the fused predict: P*^T (into g_a from g_c, into g_b from g_e; reads row n - 1),
+// then P^T (into g_a from the new g_b, into g_c from g_e; reads quad m - 1).  Update-shaped,
+// lag 0, in place.
+struct AdjPredict {
+    float p;
+    float pc[kQ], pe[kQ];  // row n - 1: g_c, g_e entering this step
+    __device__ __forceinline__ void init(float p_) {
+        p = p_;
+#pragma unroll
+        for (int q = 0; q < kQ; ++q) pc[q] = pe[q] = 0.f;
+    }
+    __device__ __forceinline__ void push(QRow<float>& r, int n, const LaneW& hw, AxisLen rows) {
+        const float wo = tp_own(n, rows), wl = tp_left(n, rows);
+        float ga[kQ], gb[kQ], gbl[kQ], gel[kQ];
+#pragma unroll
+        for (int q = 0; q < kQ; ++q) {
+            ga[q] = r.a[q] + p * (wo * r.c[q] + wl * pc[q]);
+            gb[q] = r.b[q] + p * (wo * r.e[q] + wl * pe[q]);
+        }
+        left_of(gb, gbl);
+        left_of(r.e, gel);
+#pragma unroll
+        for (int q = 0; q < kQ; ++q) {
+            const float gc = r.c[q] + p * (hw.p_own[q] * r.e[q] + hw.p_left[q] * gel[q]);
+            pc[q] = r.c[q];
+            pe[q] = r.e[q];
+            r.a[q] = ga[q] + p * (hw.p_own[q] * gb[q] + hw.p_left[q] * gbl[q]);
+            r.b[q] = gb[q];
+            r.c[q] = gc;
+        }
+    }
+};
+
+// Adjoint pipelines.  AdjFwdPipe = W^T (band gradients in, plane gradient out; the data flow of
+// the inverse kernel).  AdjInvPipe = W^-T (plane gradient in, band gradients out; the data flow
+// of the forward kernel).  Both lag kPairs rows.  The scale factors come from the host (an axis
+// of length 1 is not scaled).
+struct Scale4 {
+    float ll, hl, lh, hh;
+};
+
+template <int WV>
+struct AdjFwdPipe {
+    static constexpr int kPairs = WV == WV_CDF97 ? 2 : 1;
+    static constexpr int kLag = kPairs;
+    using C = float;
+    AdjUpdate tu[kPairs];
+    AdjPredict tp[kPairs];
+    __device__ __forceinline__ void init() {
+        const float P[2] = {WV == WV_CDF97 ? k97Alpha : -0.5f, k97Gamma};
+        const float U[2] = {WV == WV_CDF97 ? k97Beta : 0.25f, k97Delta};
+#pragma unroll
+        for (int k = 0; k < kPairs; ++k) {  // pairs in reverse order
+            tu[k].init(U[kPairs - 1 - k]);
+            tp[k].init(P[kPairs - 1 - k]);
+        }
+    }
+    __device__ __forceinline__ void push(QRow<float>& r, int n, const LaneW& hw, AxisLen rows,
+                                         const Scale4& s) {
+#pragma unroll
+        for (int q = 0; q < kQ; ++q) {
+            r.a[q] *= s.ll;
+            r.b[q] *= s.hl;
+            r.c[q] *= s.lh;
+            r.e[q] *= s.hh;
+        }
+#pragma unroll
+        for (int k = 0; k < kPairs; ++k) {
+            QRow<float> t;
+            tu[k].push(r, n - k, t, hw, rows);
+            tp[k].push(t, n - k - 1, hw, rows);
+            r = t;
+        }
+    }
+};
+
+template <int WV>
+struct AdjInvPipe {
+    static constexpr int kPairs = WV == WV_CDF97 ? 2 : 1;
+    static constexpr int kLag = kPairs;
+    using C = float;
+    AdjPredict tp[kPairs];
+    AdjUpdate tu[kPairs];
+    __device__ __forceinline__ void init() {
+        const float P[2] = {WV == WV_CDF97 ? k97Alpha : -0.5f, k97Gamma};
+        const float U[2] = {WV == WV_CDF97 ? k97Beta : 0.25f, k97Delta};
+#pragma unroll
+        for (int k = 0; k < kPairs; ++k) {  // pairs in forward order, negated coefficients
+            tp[k].init(-P[k]);
+            tu[k].init(-U[k]);
+        }
+    }
+    __device__ __forceinline__ void push(QRow<float>& r, int n, const LaneW& hw, AxisLen rows,
+                                         const Scale4& inv_s) {
+#pragma unroll
+        for (int k = 0; k < kPairs; ++k) {
+            QRow<float> t;
+            tp[k].push(r, n - k, hw, rows);
+            tu[k].push(r, n - k, t, hw, rows);
+            r = t;
+        }
+#pragma unroll
+        for (int q = 0; q < kQ; ++q) {
+            r.a[q] *= inv_s.ll;
+            r.b[q] *= inv_s.hl;
+            r.c[q] *= inv_s.lh;
+            r.e[q] *= inv_s.hh;
         }
     }
 };

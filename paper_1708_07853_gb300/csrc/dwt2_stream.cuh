@@ -52,6 +52,7 @@ struct FwdArgs {
     PlaneOut ll, hl, lh, hh;  // band planes (ll is the interleaved output plane in MODE_ROWS)
     int rpc;            // output quad rows per CTA
     int* status;        // workspace status word
+    Scale4 scale;       // MODE_ADJ_INV: the reciprocal band scales applied last
 };
 
 struct InvArgs {
@@ -63,6 +64,7 @@ struct InvArgs {
     int out_vec;          // output rows may use 4-element vector stores
     int rpc;
     int* status;
+    Scale4 scale;         // adjoint: the band scales applied first
 };
 
 template <typename T>
@@ -105,7 +107,10 @@ __device__ __forceinline__ uint8_t* align128(uint8_t* p) {
 template <int WV, int MODE, typename TI, typename TB, typename TL, bool TMA>
 __global__ void __launch_bounds__(kThreads)
     k_forward(const __grid_constant__ CUtensorMap tmap, const FwdArgs args) {
-    using Pipe = FwdPipe<WV, MODE>;
+    // MODE_ADJ_INV runs the transpose of the inverse level (gradient of an inverse transform):
+    // same data flow, no mirroring (zeros outside the plane), boundary weights in the steps.
+    constexpr bool kAdj = MODE == MODE_ADJ_INV;
+    using Pipe = std::conditional_t<kAdj, AdjInvPipe<WV>, FwdPipe<WV, kAdj ? MODE_NONSEP : MODE>>;
     using C = typename Pipe::C;
     constexpr int kVH = MODE == MODE_ROWS ? 0 : kVHalo;
     extern __shared__ __align__(128) uint8_t smem_raw[];
@@ -147,7 +152,8 @@ __global__ void __launch_bounds__(kThreads)
                 if (!__all_sync(kFull, ok)) break;
             }
             const int q = qfirst + i;
-            const int r0 = refl(2 * q, args.H), r1 = refl(2 * q + 1, args.H);
+            const int r0 = kAdj ? 2 * q : refl(2 * q, args.H);
+            const int r1 = kAdj ? 2 * q + 1 : refl(2 * q + 1, args.H);
             TI* dst = stages + size_t(s) * 2 * kSRow;
             if constexpr (TMA) {
                 if (lane == 0) {
@@ -159,15 +165,16 @@ __global__ void __launch_bounds__(kThreads)
                     }
                 }
             } else {
+                const bool ok0 = r0 >= 0 && r0 < args.H, ok1 = r1 >= 0 && r1 < args.H;
                 const TI* row0 = reinterpret_cast<const TI*>(static_cast<const char*>(args.in) +
-                                                             int64_t(r0) * args.in_pitch);
+                                                             int64_t(ok0 ? r0 : 0) * args.in_pitch);
                 const TI* row1 = reinterpret_cast<const TI*>(static_cast<const char*>(args.in) +
-                                                             int64_t(r1) * args.in_pitch);
+                                                             int64_t(ok1 ? r1 : 0) * args.in_pitch);
                 for (int k = lane; k < kSRow; k += 32) {
                     const int c = xs + k;
                     const bool in = c >= 0 && c < args.W;
-                    dst[k] = in ? row0[c] : zero_of<TI>();
-                    dst[kSRow + k] = in ? row1[c] : zero_of<TI>();
+                    dst[k] = (in && ok0) ? row0[c] : zero_of<TI>();
+                    dst[kSRow + k] = (in && ok1) ? row1[c] : zero_of<TI>();
                 }
                 mbar_arrive(&full[s]);
             }
@@ -186,9 +193,12 @@ __global__ void __launch_bounds__(kThreads)
     const int wq = qx0 - kHQ + warp * kWarpOut;  // first quad of the warp window
     const int m0 = wq + kQ * lane;               // first quad of this lane
     const int col0 = 2 * m0;                     // first pixel column of this lane
-    const bool edge = (2 * wq < 0) || (2 * wq + 2 * kWarpQ > args.W);
+    const bool edge = !kAdj && ((2 * wq < 0) || (2 * wq + 2 * kWarpQ > args.W));
     const int sc = col0 - xs;
     const bool store_lane = lane >= 1 && lane <= 30;
+    LaneW hw;
+    if constexpr (kAdj) hw.init(m0, AxisLen{args.nec, args.ndc});
+    const AxisLen rows{args.ner, args.ndr};
 
     Pipe pipe;
     pipe.init();
@@ -221,7 +231,10 @@ __global__ void __launch_bounds__(kThreads)
             row.c[q] = v1[2 * q];
             row.e[q] = v1[2 * q + 1];
         }
-        pipe.push(row);
+        if constexpr (kAdj)
+            pipe.push(row, qfirst + i, hw, rows, args.scale);
+        else
+            pipe.push(row);
 
         const int qo = qfirst + i - Pipe::kLag;
         if (qo < n0 || qo >= n1 || !store_lane) continue;
@@ -252,12 +265,14 @@ __global__ void __launch_bounds__(kThreads)
 // =============================================================================================
 // Inverse level: four band planes in, the interleaved plane out.
 // =============================================================================================
-template <int WV, typename TB, typename TL, typename TO, bool TMA>
+template <int WV, typename TB, typename TL, typename TO, bool TMA, bool ADJ>
 __global__ void __launch_bounds__(kThreads)
     k_inverse(const __grid_constant__ CUtensorMap tm_ll, const __grid_constant__ CUtensorMap tm_hl,
               const __grid_constant__ CUtensorMap tm_lh, const __grid_constant__ CUtensorMap tm_hh,
               const InvArgs args) {
-    using Pipe = InvPipe<WV>;
+    // ADJ runs the transpose of the forward level (gradient of a forward transform): same data
+    // flow, no mirroring (zeros outside the bands), boundary weights in the steps.
+    using Pipe = std::conditional_t<ADJ, AdjFwdPipe<WV>, InvPipe<WV>>;
     using C = typename Pipe::C;
     constexpr size_t kStageBytes = size_t(kBRow) * (sizeof(TL) + 3 * sizeof(TB));
     extern __shared__ __align__(128) uint8_t smem_raw[];
@@ -308,8 +323,8 @@ __global__ void __launch_bounds__(kThreads)
             }
             const int q = qfirst + i;
             // even pixel row 2q -> LL / HL row; odd pixel row 2q + 1 -> LH / HH row
-            const int re = refl(2 * q, args.H) >> 1;
-            const int ro = args.H > 1 ? (refl(2 * q + 1, args.H) - 1) >> 1 : -1;
+            const int re = ADJ ? q : refl(2 * q, args.H) >> 1;
+            const int ro = ADJ ? q : (args.H > 1 ? (refl(2 * q + 1, args.H) - 1) >> 1 : -1);
             if constexpr (TMA) {
                 if (lane == 0) {
                     mbar_arrive_expect_tx(&full[s], uint32_t(kStageBytes));
@@ -357,10 +372,13 @@ __global__ void __launch_bounds__(kThreads)
     // ------------------------------------------------------------------------- consumers
     const int wq = qx0 - kHQ + warp * kWarpOut;
     const int m0 = wq + kQ * lane;
-    const bool edge = (2 * wq < 0) || (2 * wq + 2 * kWarpQ > args.W);
+    const bool edge = !ADJ && ((2 * wq < 0) || (2 * wq + 2 * kWarpQ > args.W));
     const int sidx = m0 - xb;  // smem index of the lane's first quad (fast path)
     const bool odd_zero = args.W <= 1;
     const bool store_lane = lane >= 1 && lane <= 30;
+    LaneW hw;
+    if constexpr (ADJ) hw.init(m0, AxisLen{args.nec, args.ndc});
+    const AxisLen rows{args.ner, args.ndr};
 
     Pipe pipe;
     pipe.init();
@@ -395,7 +413,10 @@ __global__ void __launch_bounds__(kThreads)
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty[s]);
 
-        pipe.push(row);
+        if constexpr (ADJ)
+            pipe.push(row, qfirst + i, hw, rows, args.scale);
+        else
+            pipe.push(row);
         const int qo = qfirst + i - Pipe::kLag;
         if (qo < n0 || qo >= n1 || !store_lane) continue;
         const int c0 = 2 * m0;
@@ -483,9 +504,9 @@ cudaError_t launch_forward_t(const CUtensorMap& tm, FwdArgs a, cudaStream_t st) 
     return launch_pdl(k, g.grid, smem, st, tm, a);
 }
 
-template <int WV, typename TB, typename TL, typename TO, bool TMA>
+template <int WV, typename TB, typename TL, typename TO, bool TMA, bool ADJ = false>
 cudaError_t launch_inverse_t(const CUtensorMap* tm, InvArgs a, cudaStream_t st) {
-    auto k = k_inverse<WV, TB, TL, TO, TMA>;
+    auto k = k_inverse<WV, TB, TL, TO, TMA, ADJ>;
     constexpr size_t smem = inv_smem_bytes<TL, TB>();
     static const int occ = [&] {
         cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));

@@ -29,7 +29,7 @@ STATUS = {0: "ok", 1: "EINVAL", 2: "EUNSUPPORTED", 3: "ENOMEM", 4: "ECUDA", 5: "
 EXPORTS = ["dwt2_status_string", "dwt2_last_error", "dwt2_max_levels", "dwt2_layout",
            "dwt2_workspace_bytes", "dwt2_workspace_bytes_scheme", "dwt2_workspace_init",
            "dwt2_check_status", "dwt2_forward", "dwt2_forward_scheme", "dwt2_inverse",
-           "dwt2_forward_static"]
+           "dwt2_forward_static", "dwt2_forward_adjoint", "dwt2_inverse_adjoint"]
 
 
 class Dwt2Error(RuntimeError):
@@ -73,8 +73,11 @@ def _lib():
         lib.dwt2_forward_scheme.argtypes = [vp, i64, i, i, i, vp, vp, sz, i, i, i, i, vp]
         lib.dwt2_inverse.argtypes = [vp, vp, i64, i, i, i, vp, sz, i, i, i, vp]
         lib.dwt2_forward_static.argtypes = [vp, i64, i, i, i, vp, i, i, i, vp]
+        lib.dwt2_forward_adjoint.argtypes = [vp, vp, i64, i, i, i, vp, sz, i, i, i, vp]
+        lib.dwt2_inverse_adjoint.argtypes = [vp, i64, i, i, i, vp, vp, sz, i, i, i, vp]
         for f in ("dwt2_max_levels", "dwt2_layout", "dwt2_workspace_init", "dwt2_check_status",
-                  "dwt2_forward", "dwt2_forward_scheme", "dwt2_inverse", "dwt2_forward_static"):
+                  "dwt2_forward", "dwt2_forward_scheme", "dwt2_inverse", "dwt2_forward_static",
+                  "dwt2_forward_adjoint", "dwt2_inverse_adjoint"):
             getattr(lib, f).restype = i
         _LIB = lib
     return _LIB
@@ -218,4 +221,42 @@ def inverse(c: Coeffs, out: torch.Tensor | None = None, img_dtype=None,
         c.band_dtype, _stream_ptr(stream))
     if rc:
         raise Dwt2Error(rc, "dwt2_inverse")
+    return out
+
+
+def forward_adjoint(g: Coeffs, out: torch.Tensor | None = None,
+                    workspace: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """dwt2_forward_adjoint: W^T applied to a band-gradient buffer; returns the H x W gradient."""
+    if out is None:
+        out = torch.empty((g.H, g.W), dtype=torch.float32, device=g.buffer.device)
+    _check_img(out)
+    nws = workspace_bytes(g.H, g.W, g.levels, g.wavelet, g.band_dtype)
+    if workspace is None:
+        workspace = new_workspace(nws, out.device)
+    rc = _lib().dwt2_forward_adjoint(
+        g.buffer.data_ptr(), out.data_ptr(), out.stride(0) * out.element_size(), g.H, g.W,
+        TORCH_DT[out.dtype], workspace.data_ptr(), workspace.numel(), g.wavelet, g.levels,
+        g.band_dtype, _stream_ptr(stream))
+    if rc:
+        raise Dwt2Error(rc, "dwt2_forward_adjoint")
+    return out
+
+
+def inverse_adjoint(x: torch.Tensor, wavelet="cdf97", levels: int = 1, out: Coeffs | None = None,
+                    workspace: torch.Tensor | None = None, stream=None) -> Coeffs:
+    """dwt2_inverse_adjoint: W^-T applied to an image-shaped gradient; returns band gradients."""
+    _check_img(x)
+    H, W = x.shape
+    wid = _wid(wavelet)
+    if out is None:
+        out = alloc_coeffs(H, W, levels, wid, DT_F32, x.device)
+    nws = workspace_bytes(H, W, levels, wid, DT_F32)
+    if workspace is None:
+        workspace = new_workspace(nws, x.device)
+    rc = _lib().dwt2_inverse_adjoint(
+        x.data_ptr(), x.stride(0) * x.element_size(), H, W, TORCH_DT[x.dtype],
+        out.buffer.data_ptr(), workspace.data_ptr(), workspace.numel(), wid, levels, DT_F32,
+        _stream_ptr(stream))
+    if rc:
+        raise Dwt2Error(rc, "dwt2_inverse_adjoint")
     return out
