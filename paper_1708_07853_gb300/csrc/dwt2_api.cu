@@ -217,11 +217,12 @@ static FwdArgs level_args(const void* in, int64_t in_pitch, int h, int w, int* s
 }
 
 static cudaError_t launch_fwd(int wavelet, int mode, int ti, int tb, bool tma,
-                              const CUtensorMap& tm, const FwdArgs& a, cudaStream_t s) {
+                              const CUtensorMap& tm, FwdArgs a, cudaStream_t s) {
+    a.tma = tma ? 1 : 0;
     switch (wavelet) {
-    case WV_CDF53_INT: return launch_fwd_i53(mode, tma, tm, a, s);
-    case WV_CDF53: return launch_fwd_f53(mode, ti, tb, tma, tm, a, s);
-    default: return launch_fwd_f97(mode, ti, tb, tma, tm, a, s);
+    case WV_CDF53_INT: return launch_fwd_i53(mode, tm, a, s);
+    case WV_CDF53: return launch_fwd_f53(mode, ti, tb, tm, a, s);
+    default: return launch_fwd_f97(mode, ti, tb, tm, a, s);
     }
 }
 
@@ -302,7 +303,8 @@ static int forward_impl(const void* img, int64_t img_pitch, int H, int W, int im
             const int mode = scheme == DWT2_SCHEME_NONSEP ? MODE_NONSEP : MODE_SEP;
             if (adjoint) {
                 a.scale = reciprocal(level_scale(wavelet, h, w));
-                e = launch_adj_inv(wavelet, tma, tm, a, st);
+                a.tma = tma ? 1 : 0;
+                e = launch_adj_inv(wavelet, tm, a, st);
             } else {
                 e = launch_fwd(wavelet, mode, in_dt, band_dtype, tma, tm, a, st);
             }
@@ -393,12 +395,13 @@ static int inverse_impl(const void* coeffs, void* img, int64_t img_pitch, int H,
             }
         }
         if (!tma) std::memset(tm, 0, sizeof(tm));
+        a.tma = tma ? 1 : 0;
         cudaError_t e;
         if (adjoint) {
             a.scale = level_scale(wavelet, h, w);
-            e = launch_adj_fwd(wavelet, tma, tm, a, st);
+            e = launch_adj_fwd(wavelet, tm, a, st);
         } else {
-            e = launch_inv(wavelet, band_dtype, out_dt, tma, tm, a, st);
+            e = launch_inv(wavelet, band_dtype, out_dt, tm, a, st);
         }
         if (e == cudaErrorNotSupported) return DWT2_EUNSUPPORTED;
         if (e != cudaSuccess) return cuda_fail(e, "inverse level");

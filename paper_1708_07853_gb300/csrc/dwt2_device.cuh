@@ -46,14 +46,18 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t by
                  : "memory");
 }
 
+// One bounded wait on a phase: the thread may be suspended in hardware until the phase
+// completes or kSuspendNs elapses (so a waiting warp does not spin on issue slots).
+constexpr uint32_t kSuspendNs = 1000000;
+
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
     uint32_t ok;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}"
         : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
+        : "r"(smem_u32(bar)), "r"(parity), "r"(kSuspendNs)
         : "memory");
     return ok != 0;
 }
@@ -66,9 +70,7 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volati
     if (mbar_try_wait(bar, parity)) return true;
     const unsigned long long t0 = globaltimer_ns();
     for (;;) {
-#pragma unroll 1
-        for (int k = 0; k < 32; ++k)
-            if (mbar_try_wait(bar, parity)) return true;
+        if (mbar_try_wait(bar, parity)) return true;
         if (*abort_flag) return false;
         if (globaltimer_ns() - t0 > kWaitTimeoutNs) {
             *abort_flag = 1;
@@ -137,6 +139,12 @@ template <> __device__ __forceinline__ __nv_bfloat16 zero_of<__nv_bfloat16>() {
     return __float2bfloat16_rn(0.f);
 }
 template <> __device__ __forceinline__ __half zero_of<__half>() { return __float2half_rn(0.f); }
+
+// Global load that bypasses L1 (.cg): for planes another SM may have written during this kernel.
+template <typename T>
+__device__ __forceinline__ T ldcg(const T* p) {
+    return __ldcg(p);
+}
 
 // --------------------------------------------------------------- vector shared / global access
 // Four consecutive elements (16 B for 32-bit types, 8 B for 16-bit types); p is aligned to that.

@@ -3,11 +3,8 @@
 
 namespace dwt2 {
 
-cudaError_t launch_fwd_i53(int mode, bool tma, const CUtensorMap& tm, const FwdArgs& a,
-                           cudaStream_t s) {
-#define I53(M)                                                                                 \
-    return tma ? launch_forward_t<WV_CDF53_INT, M, int32_t, int32_t, int32_t, true>(tm, a, s)  \
-               : launch_forward_t<WV_CDF53_INT, M, int32_t, int32_t, int32_t, false>(tm, a, s)
+cudaError_t launch_fwd_i53(int mode, const CUtensorMap& tm, const FwdArgs& a, cudaStream_t s) {
+#define I53(M) return launch_forward_t<WV_CDF53_INT, M, int32_t, int32_t, int32_t>(tm, a, s)
     switch (mode) {
     case MODE_NONSEP: I53(MODE_NONSEP);
     case MODE_SEP: I53(MODE_SEP);

@@ -14,21 +14,19 @@ enum { DT_I32 = 0, DT_F32 = 1, DT_BF16 = 2, DT_F16 = 3 };
 
 // Forward level launch.  ti = input-plane dtype, tb = band dtype (LL output is int32 / fp32).
 // Returns cudaErrorNotSupported for a combination that has no kernel.
-cudaError_t launch_fwd_i53(int mode, bool tma, const CUtensorMap& tm, const FwdArgs& a,
+// a.tma selects TMA loads (tm valid) or plain loads.
+cudaError_t launch_fwd_i53(int mode, const CUtensorMap& tm, const FwdArgs& a, cudaStream_t s);
+cudaError_t launch_fwd_f53(int mode, int ti, int tb, const CUtensorMap& tm, const FwdArgs& a,
                            cudaStream_t s);
-cudaError_t launch_fwd_f53(int mode, int ti, int tb, bool tma, const CUtensorMap& tm,
-                           const FwdArgs& a, cudaStream_t s);
-cudaError_t launch_fwd_f97(int mode, int ti, int tb, bool tma, const CUtensorMap& tm,
-                           const FwdArgs& a, cudaStream_t s);
+cudaError_t launch_fwd_f97(int mode, int ti, int tb, const CUtensorMap& tm, const FwdArgs& a,
+                           cudaStream_t s);
 // Inverse level launch.  tb = band dtype, to = output-plane dtype; tm = LL, HL, LH, HH maps.
-cudaError_t launch_inv(int wavelet, int tb, int to, bool tma, const CUtensorMap* tm,
-                       const InvArgs& a, cudaStream_t s);
+cudaError_t launch_inv(int wavelet, int tb, int to, const CUtensorMap* tm, const InvArgs& a,
+                       cudaStream_t s);
 
 // Adjoint levels (float wavelets, fp32): W_j^T with the inverse kernel's data flow, W_j^-T with
 // the forward kernel's.
-cudaError_t launch_adj_fwd(int wavelet, bool tma, const CUtensorMap* tm, const InvArgs& a,
-                           cudaStream_t s);
-cudaError_t launch_adj_inv(int wavelet, bool tma, const CUtensorMap& tm, const FwdArgs& a,
-                           cudaStream_t s);
+cudaError_t launch_adj_fwd(int wavelet, const CUtensorMap* tm, const InvArgs& a, cudaStream_t s);
+cudaError_t launch_adj_inv(int wavelet, const CUtensorMap& tm, const FwdArgs& a, cudaStream_t s);
 
 }  // namespace dwt2

@@ -23,6 +23,13 @@ constexpr int kWarpQ = 32 * kQ;          // quads in a warp window
 constexpr int kWarpOut = kWarpQ - 2 * kHQ;  // output quads per warp (30 lanes)
 constexpr int kCtaQ = kNW * kWarpOut;    // output quads per CTA strip
 constexpr int kThreads = 32 * (kNW + 1);
+// Resident CTAs per SM the kernels are compiled for.  Measured on GB300: holding the cheap
+// wavelets (integer and float CDF 5/3) to 64 registers for 6 CTAs per SM is 7% faster; the CDF
+// 9/7 forward is 6% faster when the compiler is left free (it lands at 64 registers either way).
+template <int WV>
+constexpr int min_ctas() {
+    return WV == 2 ? 1 : 6;
+}
 constexpr int kStages = 8;               // quad rows in flight per CTA
 constexpr int kVHalo = 2;                // halo quad rows above and below a CTA's rows
 
@@ -53,6 +60,7 @@ struct FwdArgs {
     int rpc;            // output quad rows per CTA
     int* status;        // workspace status word
     Scale4 scale;       // MODE_ADJ_INV: the reciprocal band scales applied last
+    int tma;            // 1: load the input plane with TMA (16-byte aligned base and pitch)
 };
 
 struct InvArgs {
@@ -65,6 +73,7 @@ struct InvArgs {
     int rpc;
     int* status;
     Scale4 scale;         // adjoint: the band scales applied first
+    int tma;              // 1: load the band planes with TMA
 };
 
 template <typename T>
@@ -88,12 +97,13 @@ __device__ __forceinline__ void putN(T* p, const C (&v)[N], int c0, int width, b
 // Bytes of dynamic shared memory of the kernels (+128 to align the base to 128 bytes).
 template <typename TI>
 constexpr size_t fwd_smem_bytes() {
-    return size_t(kStages) * 2 * kSRow * sizeof(TI) + 2 * kStages * sizeof(uint64_t) + 16 + 128;
+    return size_t(kStages) * 2 * kSRow * sizeof(TI) + 2 * kStages * sizeof(uint64_t) +
+           4 * (kStages + 4) + 128;
 }
 template <typename TL, typename TB>
 constexpr size_t inv_smem_bytes() {
     return size_t(kStages) * kBRow * (sizeof(TL) + 3 * sizeof(TB)) +
-           2 * kStages * sizeof(uint64_t) + 16 + 128;
+           2 * kStages * sizeof(uint64_t) + 4 * (kStages + 4) + 128;
 }
 
 __device__ __forceinline__ uint8_t* align128(uint8_t* p) {
@@ -101,24 +111,284 @@ __device__ __forceinline__ uint8_t* align128(uint8_t* p) {
 }
 
 // =============================================================================================
-// Forward level.  MODE_ROWS writes the interleaved plane (the row pass of the two-pass
-// separable comparator); every other mode writes the four band planes.
+// Per-row machinery shared by the single-image kernels (one CTA = one tile) and the persistent
+// batched kernels (one CTA = many tiles).
+//
+// Stage protocol: the full barrier of a stage takes one arrival (the producer's lane 0, with the
+// TMA transaction count when the stage is filled by TMA); the empty barrier takes one arrival
+// per consumer warp.
 // =============================================================================================
-template <int WV, int MODE, typename TI, typename TB, typename TL, bool TMA>
-__global__ void __launch_bounds__(kThreads)
+
+// Forward data flow: loads of extended quad row q (pixel rows 2q, 2q + 1) of the input plane.
+// Mirrored (whole-sample symmetric) rows for the transform; plain rows, zeros outside, for the
+// adjoint of the inverse.
+template <typename TI>
+__device__ __forceinline__ void fwd_produce_row(const FwdArgs& a, const CUtensorMap* tm, bool adj,
+                                                int q, int xs, TI* dst, uint64_t* full, int lane) {
+    const int r0 = adj ? 2 * q : refl(2 * q, a.H);
+    const int r1 = adj ? 2 * q + 1 : refl(2 * q + 1, a.H);
+    if (a.tma) {
+        if (lane == 0) {
+            mbar_arrive_expect_tx(full, 2 * kSRow * sizeof(TI));
+#pragma unroll
+            for (int b = 0; b < kBoxes; ++b) {
+                tma_load_2d(dst + b * kBoxW, tm, full, xs + b * kBoxW, r0);
+                tma_load_2d(dst + kSRow + b * kBoxW, tm, full, xs + b * kBoxW, r1);
+            }
+        }
+    } else {
+        // plain loads (unaligned planes); .cg: the plane may have been written by other SMs
+        const bool ok0 = r0 >= 0 && r0 < a.H, ok1 = r1 >= 0 && r1 < a.H;
+        const TI* row0 = reinterpret_cast<const TI*>(static_cast<const char*>(a.in) +
+                                                     int64_t(ok0 ? r0 : 0) * a.in_pitch);
+        const TI* row1 = reinterpret_cast<const TI*>(static_cast<const char*>(a.in) +
+                                                     int64_t(ok1 ? r1 : 0) * a.in_pitch);
+        for (int k = lane; k < kSRow; k += 32) {
+            const int c = xs + k;
+            const bool in = c >= 0 && c < a.W;
+            dst[k] = (in && ok0) ? ldcg(row0 + c) : zero_of<TI>();
+            dst[kSRow + k] = (in && ok1) ? ldcg(row1 + c) : zero_of<TI>();
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(full);
+    }
+}
+
+// Stage offsets of a lane's 2*kQ pixel columns: consecutive (col0 - xs ...) inside the plane;
+// at the left / right edge each column's whole-sample-symmetric source, clamped to the stage.
+// Computed once per tile (the reflection needs a modulo).
+struct FwdCols {
+    bool edge;
+    int base;          // col0 - xs (fast path)
+    int ec[2 * kQ];    // edge path
+    __device__ __forceinline__ void init(int col0, int xs, int W, bool mirror, bool at_edge) {
+        edge = mirror && at_edge;
+        base = col0 - xs;
+#pragma unroll
+        for (int k = 0; k < 2 * kQ; ++k)
+            ec[k] = edge ? min(max(refl(col0 + k, W) - xs, 0), kSRow - 1) : base + k;
+    }
+};
+
+// A lane's kQ quads of one stage (pixel rows 2q, 2q + 1).
+template <typename TI, typename C>
+__device__ __forceinline__ void fwd_lane_row(const TI* stage, const FwdCols& cols, QRow<C>& row) {
+    const TI* r0 = stage;
+    const TI* r1 = stage + kSRow;
+    C v0[2 * kQ], v1[2 * kQ];
+    if (!cols.edge) {
+        ldN<2 * kQ>(r0 + cols.base, v0);
+        ldN<2 * kQ>(r1 + cols.base, v1);
+    } else {
+#pragma unroll
+        for (int k = 0; k < 2 * kQ; ++k) {
+            v0[k] = to_c(r0[cols.ec[k]]);
+            v1[k] = to_c(r1[cols.ec[k]]);
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < kQ; ++q) {
+        row.a[q] = v0[2 * q];
+        row.b[q] = v0[2 * q + 1];
+        row.c[q] = v1[2 * q];
+        row.e[q] = v1[2 * q + 1];
+    }
+}
+
+// Stores a finished quad row qo: the four band rows, or (MODE_ROWS) two interleaved pixel rows.
+template <int MODE, typename TB, typename TL, typename C>
+__device__ __forceinline__ void fwd_store_row(const FwdArgs& a, const QRow<C>& row, int qo, int m0) {
+    const int col0 = 2 * m0;
+    if constexpr (MODE == MODE_ROWS) {
+        C va[2 * kQ], vc[2 * kQ];
+#pragma unroll
+        for (int q = 0; q < kQ; ++q) {
+            va[2 * q] = row.a[q];
+            va[2 * q + 1] = row.b[q];
+            vc[2 * q] = row.c[q];
+            vc[2 * q + 1] = row.e[q];
+        }
+        putN<2 * kQ>(row_ptr<TL>(a.ll, 2 * qo) + col0, va, col0, a.W, true);
+        if (2 * qo + 1 < a.H)
+            putN<2 * kQ>(row_ptr<TL>(a.ll, 2 * qo + 1) + col0, vc, col0, a.W, true);
+    } else {
+        putN<kQ>(row_ptr<TL>(a.ll, qo) + m0, row.a, m0, a.nec, true);
+        putN<kQ>(row_ptr<TB>(a.hl, qo) + m0, row.b, m0, a.ndc, true);
+        if (qo < a.ndr) {
+            putN<kQ>(row_ptr<TB>(a.lh, qo) + m0, row.c, m0, a.nec, true);
+            putN<kQ>(row_ptr<TB>(a.hh, qo) + m0, row.e, m0, a.ndc, true);
+        }
+    }
+}
+
+// Inverse data flow: band rows of extended quad row q.  Even pixel row 2q -> LL / HL row, odd
+// pixel row 2q + 1 -> LH / HH row (mirrored; plain rows with zeros outside for the adjoint).
+// tm[k] points to the tensor map of band k (LL, HL, LH, HH) in parameter or global memory.
+template <typename TL, typename TB>
+__device__ __forceinline__ void inv_produce_row(const InvArgs& a, const CUtensorMap* const* tm,
+                                                bool adj, int q, int xb, uint8_t* stage,
+                                                uint64_t* full, int lane) {
+    constexpr size_t kStageBytes = size_t(kBRow) * (sizeof(TL) + 3 * sizeof(TB));
+    TL* sll = reinterpret_cast<TL*>(stage);
+    TB* sb = reinterpret_cast<TB*>(stage + kBRow * sizeof(TL));
+    const int re = adj ? q : refl(2 * q, a.H) >> 1;
+    const int ro = adj ? q : (a.H > 1 ? (refl(2 * q + 1, a.H) - 1) >> 1 : -1);
+    if (a.tma) {
+        if (lane == 0) {
+            mbar_arrive_expect_tx(full, uint32_t(kStageBytes));
+#pragma unroll
+            for (int b = 0; b < kBBoxes; ++b) {
+                const int x = xb + b * kBoxW;
+                tma_load_2d(sll + b * kBoxW, tm[0], full, x, re);
+                tma_load_2d(sb + b * kBoxW, tm[1], full, x, re);
+                tma_load_2d(sb + kBRow + b * kBoxW, tm[2], full, x, ro);
+                tma_load_2d(sb + 2 * kBRow + b * kBoxW, tm[3], full, x, ro);
+            }
+        }
+    } else {
+        const int rows[4] = {re, re, ro, ro};
+        const int widths[4] = {a.nec, a.ndc, a.nec, a.ndc};
+        const int heights[4] = {a.ner, a.ner, a.ndr, a.ndr};
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            const bool row_ok = rows[b] >= 0 && rows[b] < heights[b];
+            const char* src = static_cast<const char*>(a.band[b]) +
+                              int64_t(row_ok ? rows[b] : 0) * a.band_pitch[b];
+            for (int k = lane; k < kBRow; k += 32) {
+                const int c = xb + k;
+                const bool in = row_ok && c >= 0 && c < widths[b];
+                if (b == 0)
+                    sll[k] = in ? ldcg(reinterpret_cast<const TL*>(src) + c) : zero_of<TL>();
+                else
+                    sb[(b - 1) * kBRow + k] =
+                        in ? ldcg(reinterpret_cast<const TB*>(src) + c) : zero_of<TB>();
+            }
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(full);
+    }
+}
+
+// Stage offsets of a lane's kQ quads in the band rows: the quad itself inside the plane; at the
+// edges the band column of each pixel column's symmetric source (even pixel column 2m -> LL / LH,
+// odd 2m + 1 -> HL / HH; no odd columns in a 1-column plane).  Computed once per tile.
+struct InvCols {
+    bool edge, odd_zero;
+    int base;
+    int ie[kQ], io[kQ];
+    __device__ __forceinline__ void init(int m0, int xb, int W, bool mirror, bool at_edge) {
+        edge = mirror && at_edge;
+        odd_zero = W <= 1;
+        base = m0 - xb;
+#pragma unroll
+        for (int j = 0; j < kQ; ++j) {
+            const int m = m0 + j;
+            ie[j] = edge ? min(max((refl(2 * m, W) >> 1) - xb, 0), kBRow - 1) : base + j;
+            io[j] = (edge && !odd_zero)
+                        ? min(max(((refl(2 * m + 1, W) - 1) >> 1) - xb, 0), kBRow - 1)
+                        : base + j;
+        }
+    }
+};
+
+// A lane's kQ quads of the four band rows of one stage.
+template <typename TL, typename TB, typename C>
+__device__ __forceinline__ void inv_lane_row(const uint8_t* stage, const InvCols& cols,
+                                             QRow<C>& row) {
+    const TL* sll = reinterpret_cast<const TL*>(stage);
+    const TB* shl = reinterpret_cast<const TB*>(stage + kBRow * sizeof(TL));
+    const TB* slh = shl + kBRow;
+    const TB* shh = shl + 2 * kBRow;
+    if (!cols.edge) {
+        ldN<kQ>(sll + cols.base, row.a);
+        ldN<kQ>(shl + cols.base, row.b);
+        ldN<kQ>(slh + cols.base, row.c);
+        ldN<kQ>(shh + cols.base, row.e);
+    } else {
+#pragma unroll
+        for (int j = 0; j < kQ; ++j) {
+            row.a[j] = to_c(sll[cols.ie[j]]);
+            row.c[j] = to_c(slh[cols.ie[j]]);
+            row.b[j] = cols.odd_zero ? C(0) : C(to_c(shl[cols.io[j]]));
+            row.e[j] = cols.odd_zero ? C(0) : C(to_c(shh[cols.io[j]]));
+        }
+    }
+}
+
+// Stores a reconstructed quad row qo as pixel rows 2qo and 2qo + 1 of the output plane.
+template <typename TO, typename C>
+__device__ __forceinline__ void inv_store_row(const InvArgs& a, const QRow<C>& row, int qo, int m0) {
+    const int c0 = 2 * m0;
+    C va[2 * kQ], vc[2 * kQ];
+#pragma unroll
+    for (int q = 0; q < kQ; ++q) {
+        va[2 * q] = row.a[q];
+        va[2 * q + 1] = row.b[q];
+        vc[2 * q] = row.c[q];
+        vc[2 * q + 1] = row.e[q];
+    }
+    putN<2 * kQ>(row_ptr<TO>(a.out, 2 * qo) + c0, va, c0, a.W, a.out_vec != 0);
+    if (2 * qo + 1 < a.H)
+        putN<2 * kQ>(row_ptr<TO>(a.out, 2 * qo + 1) + c0, vc, c0, a.W, a.out_vec != 0);
+}
+
+// Shared-memory ring: kStages stages, then the full / empty barriers, the abort flag and the
+// per-stage tile ids (persistent kernels).
+struct Ring {
+    uint8_t* stage0;
+    size_t stage_bytes;
+    uint64_t* full;
+    uint64_t* empty;
+    volatile int* abort;
+    volatile int* meta;
+    __device__ __forceinline__ uint8_t* stage(int s) const { return stage0 + size_t(s) * stage_bytes; }
+};
+
+__device__ __forceinline__ Ring make_ring(uint8_t* smem_raw, size_t stage_bytes) {
+    Ring r;
+    r.stage0 = align128(smem_raw);
+    r.stage_bytes = stage_bytes;
+    r.full = reinterpret_cast<uint64_t*>(r.stage0 + kStages * stage_bytes);
+    r.empty = r.full + kStages;
+    r.abort = reinterpret_cast<volatile int*>(r.empty + kStages);
+    r.meta = r.abort + 1;
+    return r;
+}
+
+// Thread 0 initialises the barriers; every thread must call __syncthreads() afterwards.
+__device__ __forceinline__ void init_ring(const Ring& r) {
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kStages; ++s) {
+            mbar_init(&r.full[s], 1);
+            mbar_init(&r.empty[s], kNW);
+        }
+        *r.abort = 0;
+        fence_barrier_init();
+    }
+}
+
+// Lets the last TMA copies of a producer land before its CTA exits (bounded).
+__device__ __forceinline__ void drain_ring(const Ring& r, int issued, int* status) {
+    volatile int no_abort = 0;
+    for (int i = max(0, issued - kStages); i < issued; ++i)
+        if (!mbar_wait(&r.full[i % kStages], (i / kStages) & 1, &no_abort, status)) break;
+}
+
+// =============================================================================================
+// Single-image kernels: one CTA = one tile (kCtaQ quad columns x rpc quad rows + halo) of one
+// level.  MODE_ROWS writes the interleaved plane (the row pass of the two-pass separable
+// comparator); MODE_ADJ_INV is the transpose of the inverse level; every other mode is the
+// forward level.
+// =============================================================================================
+template <int WV, int MODE, typename TI, typename TB, typename TL>
+__global__ void __launch_bounds__(kThreads, min_ctas<WV>())
     k_forward(const __grid_constant__ CUtensorMap tmap, const FwdArgs args) {
-    // MODE_ADJ_INV runs the transpose of the inverse level (gradient of an inverse transform):
-    // same data flow, no mirroring (zeros outside the plane), boundary weights in the steps.
     constexpr bool kAdj = MODE == MODE_ADJ_INV;
     using Pipe = std::conditional_t<kAdj, AdjInvPipe<WV>, FwdPipe<WV, kAdj ? MODE_NONSEP : MODE>>;
     using C = typename Pipe::C;
     constexpr int kVH = MODE == MODE_ROWS ? 0 : kVHalo;
     extern __shared__ __align__(128) uint8_t smem_raw[];
-    uint8_t* smem = align128(smem_raw);
-    TI* stages = reinterpret_cast<TI*>(smem);
-    uint64_t* full = reinterpret_cast<uint64_t*>(smem + size_t(kStages) * 2 * kSRow * sizeof(TI));
-    uint64_t* empty = full + kStages;
-    volatile int* abort_flag = reinterpret_cast<volatile int*>(empty + kStages);
+    const Ring ring = make_ring(smem_raw, size_t(2) * kSRow * sizeof(TI));
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int qx0 = blockIdx.x * kCtaQ;
@@ -128,15 +398,8 @@ __global__ void __launch_bounds__(kThreads)
     const int qfirst = n0 - kVH;
     const int xs = 2 * qx0 - kXL;
 
-    if (threadIdx.x == 0) {
-        for (int s = 0; s < kStages; ++s) {
-            mbar_init(&full[s], TMA ? 1 : 32);
-            mbar_init(&empty[s], kNW);
-        }
-        *abort_flag = 0;
-        fence_barrier_init();
-    }
-    if (TMA && warp == kNW && lane == 0) prefetch_tensormap(&tmap);
+    init_ring(ring);
+    if (args.tma && warp == kNW && lane == 0) prefetch_tensormap(&tmap);
     __syncthreads();
     // Everything above overlaps the previous level's tail; nothing below may touch global memory
     // before that level has finished writing this level's input (and reading what we overwrite).
@@ -148,54 +411,25 @@ __global__ void __launch_bounds__(kThreads)
         for (int i = 0; i < nrows; ++i) {
             const int s = i % kStages;
             if (i >= kStages) {
-                bool ok = mbar_wait(&empty[s], ((i / kStages) - 1) & 1, abort_flag, args.status);
+                bool ok = mbar_wait(&ring.empty[s], ((i / kStages) - 1) & 1, ring.abort, args.status);
                 if (!__all_sync(kFull, ok)) break;
             }
-            const int q = qfirst + i;
-            const int r0 = kAdj ? 2 * q : refl(2 * q, args.H);
-            const int r1 = kAdj ? 2 * q + 1 : refl(2 * q + 1, args.H);
-            TI* dst = stages + size_t(s) * 2 * kSRow;
-            if constexpr (TMA) {
-                if (lane == 0) {
-                    mbar_arrive_expect_tx(&full[s], 2 * kSRow * sizeof(TI));
-#pragma unroll
-                    for (int b = 0; b < kBoxes; ++b) {
-                        tma_load_2d(dst + b * kBoxW, &tmap, &full[s], xs + b * kBoxW, r0);
-                        tma_load_2d(dst + kSRow + b * kBoxW, &tmap, &full[s], xs + b * kBoxW, r1);
-                    }
-                }
-            } else {
-                const bool ok0 = r0 >= 0 && r0 < args.H, ok1 = r1 >= 0 && r1 < args.H;
-                const TI* row0 = reinterpret_cast<const TI*>(static_cast<const char*>(args.in) +
-                                                             int64_t(ok0 ? r0 : 0) * args.in_pitch);
-                const TI* row1 = reinterpret_cast<const TI*>(static_cast<const char*>(args.in) +
-                                                             int64_t(ok1 ? r1 : 0) * args.in_pitch);
-                for (int k = lane; k < kSRow; k += 32) {
-                    const int c = xs + k;
-                    const bool in = c >= 0 && c < args.W;
-                    dst[k] = (in && ok0) ? row0[c] : zero_of<TI>();
-                    dst[kSRow + k] = (in && ok1) ? row1[c] : zero_of<TI>();
-                }
-                mbar_arrive(&full[s]);
-            }
+            fwd_produce_row<TI>(args, &tmap, kAdj, qfirst + i, xs,
+                                reinterpret_cast<TI*>(ring.stage(s)), &ring.full[s], lane);
             issued = i + 1;
         }
-        if (TMA && lane == 0) {  // let the last copies land before the CTA can exit
-            volatile int no_abort = 0;
-            for (int i = max(0, issued - kStages); i < issued; ++i)
-                if (!mbar_wait(&full[i % kStages], (i / kStages) & 1, &no_abort, args.status))
-                    break;
-        }
+        if (args.tma && lane == 0) drain_ring(ring, issued, args.status);
         return;
     }
 
     // ------------------------------------------------------------------------- consumers
     const int wq = qx0 - kHQ + warp * kWarpOut;  // first quad of the warp window
     const int m0 = wq + kQ * lane;               // first quad of this lane
-    const int col0 = 2 * m0;                     // first pixel column of this lane
-    const bool edge = !kAdj && ((2 * wq < 0) || (2 * wq + 2 * kWarpQ > args.W));
-    const int sc = col0 - xs;
     const bool store_lane = lane >= 1 && lane <= 30;
+    FwdCols cols;
+    cols.init(2 * m0, xs, args.W, !kAdj, (2 * wq < 0) || (2 * wq + 2 * kWarpQ > args.W));
+    // a warp whose output quads all lie beyond the plane only cycles the barriers
+    const bool idle = wq + kHQ >= args.nec;
     LaneW hw;
     if constexpr (kAdj) hw.init(m0, AxisLen{args.nec, args.ndc});
     const AxisLen rows{args.ner, args.ndr};
@@ -204,82 +438,37 @@ __global__ void __launch_bounds__(kThreads)
     pipe.init();
     for (int i = 0; i < nrows; ++i) {
         const int s = i % kStages;
-        bool ok = mbar_wait(&full[s], (i / kStages) & 1, abort_flag, args.status);
+        bool ok = mbar_wait(&ring.full[s], (i / kStages) & 1, ring.abort, args.status);
         if (!__all_sync(kFull, ok)) break;
-        const TI* r0 = stages + size_t(s) * 2 * kSRow;
-        const TI* r1 = r0 + kSRow;
-        C v0[2 * kQ], v1[2 * kQ];
-        if (!edge) {
-            ldN<2 * kQ>(r0 + sc, v0);
-            ldN<2 * kQ>(r1 + sc, v1);
-        } else {
-#pragma unroll
-            for (int k = 0; k < 2 * kQ; ++k) {
-                const int c = min(max(refl(col0 + k, args.W) - xs, 0), kSRow - 1);
-                v0[k] = to_c(r0[c]);
-                v1[k] = to_c(r1[c]);
-            }
+        if (idle) {
+            if (lane == 0) mbar_arrive(&ring.empty[s]);
+            continue;
         }
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&empty[s]);
-
         QRow<C> row;
-#pragma unroll
-        for (int q = 0; q < kQ; ++q) {
-            row.a[q] = v0[2 * q];
-            row.b[q] = v0[2 * q + 1];
-            row.c[q] = v1[2 * q];
-            row.e[q] = v1[2 * q + 1];
-        }
+        fwd_lane_row<TI, C>(reinterpret_cast<const TI*>(ring.stage(s)), cols, row);
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&ring.empty[s]);
         if constexpr (kAdj)
             pipe.push(row, qfirst + i, hw, rows, args.scale);
         else
             pipe.push(row);
-
         const int qo = qfirst + i - Pipe::kLag;
-        if (qo < n0 || qo >= n1 || !store_lane) continue;
-        if constexpr (MODE == MODE_ROWS) {
-            // interleaved output plane: pixel rows 2qo (a b a b ...) and 2qo + 1 (c e c e ...)
-            C va[2 * kQ], vc[2 * kQ];
-#pragma unroll
-            for (int q = 0; q < kQ; ++q) {
-                va[2 * q] = row.a[q];
-                va[2 * q + 1] = row.b[q];
-                vc[2 * q] = row.c[q];
-                vc[2 * q + 1] = row.e[q];
-            }
-            putN<2 * kQ>(row_ptr<TL>(args.ll, 2 * qo) + col0, va, col0, args.W, true);
-            if (2 * qo + 1 < args.H)
-                putN<2 * kQ>(row_ptr<TL>(args.ll, 2 * qo + 1) + col0, vc, col0, args.W, true);
-        } else {
-            putN<kQ>(row_ptr<TL>(args.ll, qo) + m0, row.a, m0, args.nec, true);
-            putN<kQ>(row_ptr<TB>(args.hl, qo) + m0, row.b, m0, args.ndc, true);
-            if (qo < args.ndr) {
-                putN<kQ>(row_ptr<TB>(args.lh, qo) + m0, row.c, m0, args.nec, true);
-                putN<kQ>(row_ptr<TB>(args.hh, qo) + m0, row.e, m0, args.ndc, true);
-            }
-        }
+        if (qo >= n0 && qo < n1 && store_lane) fwd_store_row<MODE, TB, TL>(args, row, qo, m0);
     }
 }
 
-// =============================================================================================
-// Inverse level: four band planes in, the interleaved plane out.
-// =============================================================================================
-template <int WV, typename TB, typename TL, typename TO, bool TMA, bool ADJ>
-__global__ void __launch_bounds__(kThreads)
+// Inverse level (ADJ = false) or the transpose of the forward level (ADJ = true): four band
+// planes in, the interleaved plane out.
+template <int WV, typename TB, typename TL, typename TO, bool ADJ>
+__global__ void __launch_bounds__(kThreads, min_ctas<WV>())
     k_inverse(const __grid_constant__ CUtensorMap tm_ll, const __grid_constant__ CUtensorMap tm_hl,
               const __grid_constant__ CUtensorMap tm_lh, const __grid_constant__ CUtensorMap tm_hh,
               const InvArgs args) {
-    // ADJ runs the transpose of the forward level (gradient of a forward transform): same data
-    // flow, no mirroring (zeros outside the bands), boundary weights in the steps.
     using Pipe = std::conditional_t<ADJ, AdjFwdPipe<WV>, InvPipe<WV>>;
     using C = typename Pipe::C;
     constexpr size_t kStageBytes = size_t(kBRow) * (sizeof(TL) + 3 * sizeof(TB));
     extern __shared__ __align__(128) uint8_t smem_raw[];
-    uint8_t* smem = align128(smem_raw);
-    uint64_t* full = reinterpret_cast<uint64_t*>(smem + kStages * kStageBytes);
-    uint64_t* empty = full + kStages;
-    volatile int* abort_flag = reinterpret_cast<volatile int*>(empty + kStages);
+    const Ring ring = make_ring(smem_raw, kStageBytes);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int qx0 = blockIdx.x * kCtaQ;
@@ -289,15 +478,8 @@ __global__ void __launch_bounds__(kThreads)
     const int qfirst = n0 - kVHalo;
     const int xb = qx0 - kXLB;
 
-    if (threadIdx.x == 0) {
-        for (int s = 0; s < kStages; ++s) {
-            mbar_init(&full[s], TMA ? 1 : 32);
-            mbar_init(&empty[s], kNW);
-        }
-        *abort_flag = 0;
-        fence_barrier_init();
-    }
-    if (TMA && warp == kNW && lane == 0) {
+    init_ring(ring);
+    if (args.tma && warp == kNW && lane == 0) {
         prefetch_tensormap(&tm_ll);
         prefetch_tensormap(&tm_hl);
         prefetch_tensormap(&tm_lh);
@@ -307,75 +489,31 @@ __global__ void __launch_bounds__(kThreads)
     grid_dependency_wait();
     allow_dependent_launch();
 
-    auto stage_ll = [&](int s) { return reinterpret_cast<TL*>(smem + s * kStageBytes); };
-    auto stage_b = [&](int s, int k) {  // k = 0 HL, 1 LH, 2 HH
-        return reinterpret_cast<TB*>(smem + s * kStageBytes + kBRow * sizeof(TL) +
-                                     size_t(k) * kBRow * sizeof(TB));
-    };
-
     if (warp == kNW) {  // ------------------------------------------------------ producer
+        // pointers to the __grid_constant__ parameters (TMA reads the maps where they live)
+        const CUtensorMap* maps[4] = {&tm_ll, &tm_hl, &tm_lh, &tm_hh};
         int issued = 0;
         for (int i = 0; i < nrows; ++i) {
             const int s = i % kStages;
             if (i >= kStages) {
-                bool ok = mbar_wait(&empty[s], ((i / kStages) - 1) & 1, abort_flag, args.status);
+                bool ok = mbar_wait(&ring.empty[s], ((i / kStages) - 1) & 1, ring.abort, args.status);
                 if (!__all_sync(kFull, ok)) break;
             }
-            const int q = qfirst + i;
-            // even pixel row 2q -> LL / HL row; odd pixel row 2q + 1 -> LH / HH row
-            const int re = ADJ ? q : refl(2 * q, args.H) >> 1;
-            const int ro = ADJ ? q : (args.H > 1 ? (refl(2 * q + 1, args.H) - 1) >> 1 : -1);
-            if constexpr (TMA) {
-                if (lane == 0) {
-                    mbar_arrive_expect_tx(&full[s], uint32_t(kStageBytes));
-#pragma unroll
-                    for (int b = 0; b < kBBoxes; ++b) {
-                        const int x = xb + b * kBoxW;
-                        tma_load_2d(stage_ll(s) + b * kBoxW, &tm_ll, &full[s], x, re);
-                        tma_load_2d(stage_b(s, 0) + b * kBoxW, &tm_hl, &full[s], x, re);
-                        tma_load_2d(stage_b(s, 1) + b * kBoxW, &tm_lh, &full[s], x, ro);
-                        tma_load_2d(stage_b(s, 2) + b * kBoxW, &tm_hh, &full[s], x, ro);
-                    }
-                }
-            } else {
-                const int rows[4] = {re, re, ro, ro};
-                const int widths[4] = {args.nec, args.ndc, args.nec, args.ndc};
-                const int heights[4] = {args.ner, args.ner, args.ndr, args.ndr};
-#pragma unroll
-                for (int b = 0; b < 4; ++b) {
-                    const bool row_ok = rows[b] >= 0 && rows[b] < heights[b];
-                    const char* src = static_cast<const char*>(args.band[b]) +
-                                      int64_t(row_ok ? rows[b] : 0) * args.band_pitch[b];
-                    for (int k = lane; k < kBRow; k += 32) {
-                        const int c = xb + k;
-                        const bool in = row_ok && c >= 0 && c < widths[b];
-                        if (b == 0)
-                            stage_ll(s)[k] = in ? reinterpret_cast<const TL*>(src)[c] : zero_of<TL>();
-                        else
-                            stage_b(s, b - 1)[k] =
-                                in ? reinterpret_cast<const TB*>(src)[c] : zero_of<TB>();
-                    }
-                }
-                mbar_arrive(&full[s]);
-            }
+            inv_produce_row<TL, TB>(args, maps, ADJ, qfirst + i, xb, ring.stage(s), &ring.full[s],
+                                    lane);
             issued = i + 1;
         }
-        if (TMA && lane == 0) {
-            volatile int no_abort = 0;
-            for (int i = max(0, issued - kStages); i < issued; ++i)
-                if (!mbar_wait(&full[i % kStages], (i / kStages) & 1, &no_abort, args.status))
-                    break;
-        }
+        if (args.tma && lane == 0) drain_ring(ring, issued, args.status);
         return;
     }
 
     // ------------------------------------------------------------------------- consumers
     const int wq = qx0 - kHQ + warp * kWarpOut;
     const int m0 = wq + kQ * lane;
-    const bool edge = !ADJ && ((2 * wq < 0) || (2 * wq + 2 * kWarpQ > args.W));
-    const int sidx = m0 - xb;  // smem index of the lane's first quad (fast path)
-    const bool odd_zero = args.W <= 1;
     const bool store_lane = lane >= 1 && lane <= 30;
+    InvCols cols;
+    cols.init(m0, xb, args.W, !ADJ, (2 * wq < 0) || (2 * wq + 2 * kWarpQ > args.W));
+    const bool idle = wq + kHQ >= args.nec;
     LaneW hw;
     if constexpr (ADJ) hw.init(m0, AxisLen{args.nec, args.ndc});
     const AxisLen rows{args.ner, args.ndr};
@@ -384,53 +522,22 @@ __global__ void __launch_bounds__(kThreads)
     pipe.init();
     for (int i = 0; i < nrows; ++i) {
         const int s = i % kStages;
-        bool ok = mbar_wait(&full[s], (i / kStages) & 1, abort_flag, args.status);
+        bool ok = mbar_wait(&ring.full[s], (i / kStages) & 1, ring.abort, args.status);
         if (!__all_sync(kFull, ok)) break;
-        QRow<C> row;
-        const TL* sll = stage_ll(s);
-        const TB* shl = stage_b(s, 0);
-        const TB* slh = stage_b(s, 1);
-        const TB* shh = stage_b(s, 2);
-        if (!edge) {
-            ldN<kQ>(sll + sidx, row.a);
-            ldN<kQ>(shl + sidx, row.b);
-            ldN<kQ>(slh + sidx, row.c);
-            ldN<kQ>(shh + sidx, row.e);
-        } else {
-            // even pixel column 2m -> LL / LH column; odd 2m + 1 -> HL / HH column (reflected)
-#pragma unroll
-            for (int j = 0; j < kQ; ++j) {
-                const int m = m0 + j;
-                const int ie = min(max((refl(2 * m, args.W) >> 1) - xb, 0), kBRow - 1);
-                const int io =
-                    odd_zero ? 0 : min(max(((refl(2 * m + 1, args.W) - 1) >> 1) - xb, 0), kBRow - 1);
-                row.a[j] = to_c(sll[ie]);
-                row.c[j] = to_c(slh[ie]);
-                row.b[j] = odd_zero ? C(0) : C(to_c(shl[io]));
-                row.e[j] = odd_zero ? C(0) : C(to_c(shh[io]));
-            }
+        if (idle) {
+            if (lane == 0) mbar_arrive(&ring.empty[s]);
+            continue;
         }
+        QRow<C> row;
+        inv_lane_row<TL, TB, C>(ring.stage(s), cols, row);
         __syncwarp();
-        if (lane == 0) mbar_arrive(&empty[s]);
-
+        if (lane == 0) mbar_arrive(&ring.empty[s]);
         if constexpr (ADJ)
             pipe.push(row, qfirst + i, hw, rows, args.scale);
         else
             pipe.push(row);
         const int qo = qfirst + i - Pipe::kLag;
-        if (qo < n0 || qo >= n1 || !store_lane) continue;
-        const int c0 = 2 * m0;
-        C va[2 * kQ], vc[2 * kQ];
-#pragma unroll
-        for (int q = 0; q < kQ; ++q) {
-            va[2 * q] = row.a[q];
-            va[2 * q + 1] = row.b[q];
-            vc[2 * q] = row.c[q];
-            vc[2 * q + 1] = row.e[q];
-        }
-        putN<2 * kQ>(row_ptr<TO>(args.out, 2 * qo) + c0, va, c0, args.W, args.out_vec != 0);
-        if (2 * qo + 1 < args.H)
-            putN<2 * kQ>(row_ptr<TO>(args.out, 2 * qo + 1) + c0, vc, c0, args.W, args.out_vec != 0);
+        if (qo >= n0 && qo < n1 && store_lane) inv_store_row<TO>(args, row, qo, m0);
     }
 }
 
@@ -482,36 +589,36 @@ cudaError_t launch_pdl(K kernel, dim3 grid, size_t smem, cudaStream_t st, Args..
 
 int device_sm_count();
 
+// Sets the kernel's dynamic shared memory limit and asks for the largest shared-memory carveout
+// (the kernels need no L1 beyond the default; without this the driver may pick a smaller carveout
+// and fit fewer CTAs per SM), then returns the resident CTAs per SM.
 template <typename K>
-int occupancy_of(K kernel, size_t smem) {
+int configure(K kernel, size_t smem) {
+    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                         int(cudaSharedmemCarveoutMaxShared));
     int n = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, kThreads, smem) != cudaSuccess)
         n = 1;
     return n;
 }
 
-template <int WV, int MODE, typename TI, typename TB, typename TL, bool TMA>
+template <int WV, int MODE, typename TI, typename TB, typename TL>
 cudaError_t launch_forward_t(const CUtensorMap& tm, FwdArgs a, cudaStream_t st) {
-    auto k = k_forward<WV, MODE, TI, TB, TL, TMA>;
+    auto k = k_forward<WV, MODE, TI, TB, TL>;
     constexpr size_t smem = fwd_smem_bytes<TI>();
-    static const int occ = [&] {
-        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-        return occupancy_of(k, smem);
-    }();
+    static const int occ = configure(k, smem);
     const LaunchGeom g = pick_geometry(a.ner, a.nec, int64_t(a.H) * a.W * int64_t(sizeof(TI)),
                                        device_sm_count(), occ);
     a.rpc = g.rpc;
     return launch_pdl(k, g.grid, smem, st, tm, a);
 }
 
-template <int WV, typename TB, typename TL, typename TO, bool TMA, bool ADJ = false>
+template <int WV, typename TB, typename TL, typename TO, bool ADJ = false>
 cudaError_t launch_inverse_t(const CUtensorMap* tm, InvArgs a, cudaStream_t st) {
-    auto k = k_inverse<WV, TB, TL, TO, TMA, ADJ>;
+    auto k = k_inverse<WV, TB, TL, TO, ADJ>;
     constexpr size_t smem = inv_smem_bytes<TL, TB>();
-    static const int occ = [&] {
-        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-        return occupancy_of(k, smem);
-    }();
+    static const int occ = configure(k, smem);
     const LaunchGeom g = pick_geometry(a.ner, a.nec, int64_t(a.H) * a.W * int64_t(sizeof(TL)),
                                        device_sm_count(), occ);
     a.rpc = g.rpc;
