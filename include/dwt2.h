@@ -188,6 +188,55 @@ int dwt2_inverse_adjoint(const void* g_img, int64_t g_img_pitch_bytes, int H, in
                          int band_dtype, void* stream);
 
 /* ---------------------------------------------------------------------------------------------
+ * Batched plans: many images of any sizes, every level, ONE persistent kernel launch replayed
+ * from a CUDA graph.  The work is a list of tiles (image, level, strip of 240 quad columns,
+ * block of rows) in level-major order; CTAs claim tiles from a counter, and a tile of level j of
+ * an image waits (bounded in time) until the same image's level j-1 (forward flow) or j+1
+ * (inverse flow) has completed.
+ *   imgs[i].img     image (forward, inverse adjoint: input; inverse, forward adjoint: output),
+ *                   H x W of img_dtype with row pitch img_pitch_bytes (multiple of 4 bytes);
+ *   imgs[i].coeffs  coefficient buffer laid out by dwt2_layout(H, W, levels, band_dtype),
+ *                   16-byte aligned (output of forward, input of inverse).
+ *   img_dtype       DWT2_I32 (integer wavelet) or DWT2_F32; band_dtype as for dwt2_forward
+ *                   (adjoint directions: DWT2_F32 only).
+ *   workspace       device buffer of dwt2_plan_workspace_bytes(...), 256-byte aligned, header
+ *                   zeroed (dwt2_workspace_init); it holds every image's intermediate LL planes.
+ *   tune_cache      path of a text file of tuned schedules, or NULL.  With a path, the first
+ *                   plan of a kind (GPU, direction, wavelet, storage, levels, image count, size
+ *                   class) times candidate tile heights and CTAs per SM on itself -- running the
+ *                   transform several times -- and appends the winner; later plans read it.
+ *                   Without a path a default schedule is used.
+ * The plan allocates its own small device buffers (descriptors, tensor maps, counters) at
+ * creation and captures [counter reset, kernel] in a graph; buffers are bound at creation.
+ * Results are identical to the single-image entry points (bit for bit for the integer wavelet). */
+typedef struct {
+    void* img;
+    int64_t img_pitch_bytes;
+    int H, W;
+    void* coeffs;
+} dwt2_image_desc;
+
+typedef enum {
+    DWT2_DIR_FORWARD = 0,
+    DWT2_DIR_INVERSE = 1,
+    DWT2_DIR_FORWARD_ADJOINT = 2, /* W^T: band gradients (coeffs) -> image gradient (img) */
+    DWT2_DIR_INVERSE_ADJOINT = 3  /* W^-T: image gradient (img) -> band gradients (coeffs) */
+} dwt2_direction;
+
+typedef struct dwt2_plan dwt2_plan;
+
+size_t dwt2_plan_workspace_bytes(const dwt2_image_desc* imgs, int n, int wavelet, int levels,
+                                 int band_dtype);
+int dwt2_plan_create(const dwt2_image_desc* imgs, int n, int wavelet, int levels, int img_dtype,
+                     int band_dtype, int direction, void* workspace, size_t ws_bytes,
+                     const char* tune_cache, dwt2_plan** plan);
+/* Enqueue the plan's graph on stream (asynchronous). */
+int dwt2_plan_execute(dwt2_plan* plan, void* stream);
+/* The schedule in use: quad rows per tile, CTAs per SM, number of tiles. */
+int dwt2_plan_info(const dwt2_plan* plan, int* rows_per_tile, int* ctas_per_sm, int* n_tiles);
+int dwt2_plan_destroy(dwt2_plan* plan);
+
+/* ---------------------------------------------------------------------------------------------
  * Forward transform without a caller-provided workspace.  The paper has no counterpart: this
  * entry point exists for callers that cannot allocate device memory (for example code whose host
  * application owns all device memory and passes in only the input and output buffers, or a

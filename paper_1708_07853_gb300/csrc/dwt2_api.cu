@@ -409,6 +409,71 @@ static int inverse_impl(const void* coeffs, void* img, int64_t img_pitch, int H,
     return DWT2_OK;
 }
 
+// ------------------------------------------------------------------ helpers for batched plans
+Scale4 plan_level_scale(int wavelet, int h, int w) { return level_scale(wavelet, h, w); }
+
+// Bytes of one image's LL ping-pong planes and their offsets / pitches within that region.
+int64_t plan_image_scratch(int H, int W, int J, int wavelet, int64_t offs[2], int64_t pitch[2]) {
+    const WsPlan wp = plan_workspace(H, W, J, wavelet, DWT2_SCHEME_NONSEP);
+    for (int k = 0; k < 2; ++k) {
+        offs[k] = wp.off[k] - kHeader;
+        pitch[k] = wp.pitch[k];
+    }
+    return wp.bytes - kHeader;
+}
+
+int plan_layout(int H, int W, int J, int band_dtype, dwt2_band* bands, size_t* bytes) {
+    Layout L;
+    const int rc = make_layout(H, W, J, band_dtype, &L);
+    if (rc) return rc;
+    std::memcpy(bands, L.band, sizeof(dwt2_band) * (1 + 3 * J));
+    *bytes = size_t(L.bytes);
+    return DWT2_OK;
+}
+
+int plan_prepare_fwd_unit(FwdUnit* u, const void* in, int64_t in_pitch, int h, int w, int in_dt,
+                          int tb, int* status) {
+    (void)tb;
+    u->a = level_args(in, in_pitch, h, w, status);
+    const MapResult mr = make_map(&u->tm, in, in_pitch, h, w, in_dt, kBoxW);
+    if (mr == MAP_ERROR) return DWT2_EINTERNAL;
+    u->a.tma = mr == MAP_OK ? 1 : 0;
+    return DWT2_OK;
+}
+
+int plan_prepare_inv_unit(InvUnit* u, const void* const bands[4], const int64_t pitches[4], int h,
+                          int w, int tl, int tb, void* out, int64_t out_pitch, int out_dt,
+                          int* status) {
+    InvArgs& a = u->a;
+    std::memset(&a, 0, sizeof(a));
+    a.H = h;
+    a.W = w;
+    a.ner = (h + 1) / 2;
+    a.ndr = h / 2;
+    a.nec = (w + 1) / 2;
+    a.ndc = w / 2;
+    a.status = status;
+    for (int k = 0; k < 4; ++k) {
+        a.band[k] = bands[k];
+        a.band_pitch[k] = pitches[k];
+    }
+    a.out = {out, out_pitch};
+    const size_t vbytes = 4 * esize(out_dt);
+    a.out_vec = aligned(out, vbytes) && out_pitch % int64_t(vbytes) == 0;
+    bool tma = h >= 2 && w >= 2;
+    if (tma) {
+        const int dims[4][2] = {{a.ner, a.nec}, {a.ner, a.ndc}, {a.ndr, a.nec}, {a.ndr, a.ndc}};
+        for (int k = 0; k < 4; ++k) {
+            const MapResult r = make_map(&u->tm[k], bands[k], pitches[k], dims[k][0], dims[k][1],
+                                         k == 0 ? tl : tb, kBoxW);
+            if (r == MAP_ERROR) return DWT2_EINTERNAL;
+            if (r != MAP_OK) tma = false;
+        }
+    }
+    a.tma = tma ? 1 : 0;
+    return DWT2_OK;
+}
+
 }  // namespace dwt2
 
 using namespace dwt2;

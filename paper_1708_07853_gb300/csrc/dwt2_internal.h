@@ -5,7 +5,7 @@
 #include <cuda.h>
 #include <cuda_runtime.h>
 
-#include "dwt2_stream.cuh"
+#include "dwt2_persist.cuh"
 
 namespace dwt2 {
 
@@ -28,5 +28,14 @@ cudaError_t launch_inv(int wavelet, int tb, int to, const CUtensorMap* tm, const
 // the forward kernel's.
 cudaError_t launch_adj_fwd(int wavelet, const CUtensorMap* tm, const InvArgs& a, cudaStream_t s);
 cudaError_t launch_adj_inv(int wavelet, const CUtensorMap& tm, const FwdArgs& a, cudaStream_t s);
+
+// Persistent batched kernels (one launch for every level of every image of a plan).
+// ctas_per_sm <= 0 uses the occupancy limit; *occ (if non-null) receives that limit and nothing
+// is launched.  Forward data flow: mode MODE_NONSEP or MODE_ADJ_INV; inverse data flow: adj
+// selects the transpose of the forward.
+cudaError_t launch_fwd_persistent(int wavelet, int mode, int tb, const PersistArgs<FwdUnit>& p,
+                                  int ctas_per_sm, cudaStream_t st, int* occ);
+cudaError_t launch_inv_persistent(int wavelet, bool adj, int tb, const PersistArgs<InvUnit>& p,
+                                  int ctas_per_sm, cudaStream_t st, int* occ);
 
 }  // namespace dwt2

@@ -1,0 +1,335 @@
+// dwt2_persist.cuh -- persistent kernels for batches: one launch runs every level of every image.
+//
+// Work list: tiles (image, level, strip, row block) in level-major ticket order (forward: level 1
+// of all images, then level 2, ...; inverse: the coarsest level first).  Each CTA of a grid sized
+// to the resident capacity claims tickets with an atomic counter.  Its producer warp resolves a
+// ticket to its unit (one image at one level), waits until the unit it depends on (the same
+// image's previous level) has completed, and streams the tile's rows into the stage ring, tagging
+// each stage with the ticket; the consumer warps follow the tags, re-initialise their pipeline at
+// each new tile and count completion per warp.
+//
+// Deadlock freedom: a tile waits only for tiles with smaller tickets, which were claimed by CTAs
+// that are running (claims happen only in running CTAs) and never wait for larger tickets.
+// Every wait is bounded in time; a wait that gives up records DWT2_ETIMEOUT and the CTA winds down.
+#pragma once
+
+#include "dwt2_stream.cuh"
+
+namespace dwt2 {
+
+// One image at one level of a batched plan (64-byte aligned: the tensor maps live here).
+struct alignas(64) FwdUnit {
+    CUtensorMap tm;  // input plane (when a.tma)
+    FwdArgs a;
+    int item_begin;  // first ticket of the unit
+    int n_items;     // tiles: strips x row blocks
+    int strips;
+    int dep;         // unit that must complete first (-1: none)
+};
+
+struct alignas(64) InvUnit {
+    CUtensorMap tm[4];  // LL, HL, LH, HH (when a.tma)
+    InvArgs a;
+    int item_begin;
+    int n_items;
+    int strips;
+    int dep;
+};
+
+template <typename Unit>
+struct PersistArgs {
+    const Unit* units;
+    const int* item_unit;  // ticket -> unit
+    int n_items;
+    int* ticket;           // claimed tickets (zero before the launch)
+    int* done;             // per unit: consumer warps that finished one of its tiles (zeroed)
+    int* status;
+};
+
+__device__ __forceinline__ int ld_acquire_gpu(const int* p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Makes data that other CTAs wrote with ordinary stores (and published with a release) visible
+// to this thread's subsequent TMA (async proxy) reads.
+__device__ __forceinline__ void fence_proxy_async_global() {
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+}
+
+// Waits (bounded) until *counter >= need.  On timeout raises the CTA abort flag and records
+// DWT2_ETIMEOUT.
+__device__ __forceinline__ bool wait_count(const int* counter, int need, volatile int* abort_flag,
+                                           int* status) {
+    if (ld_acquire_gpu(counter) >= need) return true;
+    const unsigned long long t0 = globaltimer_ns();
+    for (;;) {
+        __nanosleep(256);
+        if (ld_acquire_gpu(counter) >= need) return true;
+        if (*abort_flag) return false;
+        if (globaltimer_ns() - t0 > kWaitTimeoutNs) {
+            *abort_flag = 1;
+            if (status) atomicExch(status, kStatusTimeout);
+            return false;
+        }
+    }
+}
+
+// Marks one consumer warp's share of a tile done: every lane's stores are made visible at GPU
+// scope before lane 0 counts the warp.
+__device__ __forceinline__ void warp_done(int* counter, int lane) {
+    __threadfence();
+    __syncwarp();
+    if (lane == 0) atomicAdd(counter, 1);
+}
+
+// Geometry of one tile.
+struct Tile {
+    int qx0, n0, n1, nrows, qfirst;
+};
+
+template <typename Args>
+__device__ __forceinline__ Tile tile_of(const Args& a, int local, int strips) {
+    Tile t;
+    const int rb = local / strips, strip = local - rb * strips;
+    t.qx0 = strip * kCtaQ;
+    t.n0 = rb * a.rpc;
+    t.n1 = min(t.n0 + a.rpc, a.ner);
+    t.nrows = t.n1 - t.n0 + 2 * kVHalo;
+    t.qfirst = t.n0 - kVHalo;
+    return t;
+}
+
+// Producer side shared by both kernel shapes: claim the next ticket; returns -1 when the work is
+// exhausted.  Waits for the ticket's dependency.
+template <typename Unit>
+__device__ __forceinline__ int claim(const PersistArgs<Unit>& p, volatile int* abort_flag,
+                                     int lane, bool& ok) {
+    int t = 0;
+    if (lane == 0) t = atomicAdd(p.ticket, 1);
+    t = __shfl_sync(kFull, t, 0);
+    ok = true;
+    if (t >= p.n_items) return -1;
+    const int u = __ldg(&p.item_unit[t]);
+    const int dep = p.units[u].dep;
+    if (dep >= 0) {
+        int good = 1;
+        if (lane == 0) good = wait_count(&p.done[dep], kNW * p.units[dep].n_items, abort_flag, p.status);
+        good = __shfl_sync(kFull, good, 0);
+        if (!good) {
+            ok = false;
+            return -1;
+        }
+        fence_proxy_async_global();
+    }
+    return t;
+}
+
+// Producer: after the last tile (or on abort) a sentinel stage tells the consumers to stop.
+__device__ __forceinline__ void post_sentinel(const Ring& ring, int g, int lane, int* status) {
+    const int s = g % kStages;
+    if (g >= kStages) {
+        bool ok = mbar_wait(&ring.empty[s], ((g / kStages) - 1) & 1, ring.abort, status);
+        if (!__all_sync(kFull, ok)) return;  // consumers are aborting anyway
+    }
+    if (lane == 0) {
+        ring.meta[s] = -1;
+        mbar_arrive(&ring.full[s]);
+    }
+}
+
+template <int WV, int MODE, typename TI, typename TB, typename TL>
+__global__ void __launch_bounds__(kThreads, min_ctas<WV>())
+    k_forward_persistent(const PersistArgs<FwdUnit> p) {
+    constexpr bool kAdj = MODE == MODE_ADJ_INV;
+    using Pipe = std::conditional_t<kAdj, AdjInvPipe<WV>, FwdPipe<WV, MODE_NONSEP>>;
+    using C = typename Pipe::C;
+    extern __shared__ __align__(128) uint8_t smem_raw[];
+    const Ring ring = make_ring(smem_raw, size_t(2) * kSRow * sizeof(TI));
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    init_ring(ring);
+    __syncthreads();
+
+    if (warp == kNW) {  // ------------------------------------------------------ producer
+        int g = 0;
+        bool tma_used = false;
+        for (;;) {
+            bool ok;
+            const int t = claim(p, ring.abort, lane, ok);
+            if (t < 0) {
+                if (ok) post_sentinel(ring, g, lane, p.status);
+                break;
+            }
+            const FwdUnit& U = p.units[__ldg(&p.item_unit[t])];
+            const Tile tl = tile_of(U.a, t - U.item_begin, U.strips);
+            const int xs = 2 * tl.qx0 - kXL;
+            tma_used |= U.a.tma != 0;
+            bool alive = true;
+            for (int i = 0; i < tl.nrows; ++i, ++g) {
+                const int s = g % kStages;
+                if (g >= kStages) {
+                    bool w = mbar_wait(&ring.empty[s], ((g / kStages) - 1) & 1, ring.abort, p.status);
+                    if (!__all_sync(kFull, w)) {
+                        alive = false;
+                        break;
+                    }
+                }
+                if (lane == 0) ring.meta[s] = t;
+                fwd_produce_row<TI>(U.a, &U.tm, kAdj, tl.qfirst + i, xs,
+                                    reinterpret_cast<TI*>(ring.stage(s)), &ring.full[s], lane);
+            }
+            if (!alive) break;
+        }
+        // Normally the consumers take every stage (the sentinel last) before the CTA can exit, so
+        // all copies have landed.  After an abort, let the copies still in flight land first.  (No
+        // drain otherwise: the sentinel's stage has moved one phase past its last copy.)
+        if (tma_used && lane == 0 && *ring.abort) drain_ring(ring, g, p.status);
+        return;
+    }
+
+    // ------------------------------------------------------------------------- consumers
+    const bool store_lane = lane >= 1 && lane <= 30;
+    int cur = -1, i = 0, unit = 0;
+    Tile tl{};
+    FwdCols cols;
+    LaneW hw;
+    bool idle = false;
+    int m0 = 0;
+    Pipe pipe;
+    for (int g = 0;; ++g) {
+        const int s = g % kStages;
+        bool ok = mbar_wait(&ring.full[s], (g / kStages) & 1, ring.abort, p.status);
+        if (!__all_sync(kFull, ok)) break;
+        const int t = ring.meta[s];
+        if (t < 0) break;
+        const FwdUnit* U = &p.units[__ldg(&p.item_unit[t])];
+        if (t != cur) {  // first row of a new tile
+            cur = t;
+            unit = __ldg(&p.item_unit[t]);
+            tl = tile_of(U->a, t - U->item_begin, U->strips);
+            const int wq = tl.qx0 - kHQ + warp * kWarpOut;
+            m0 = wq + kQ * lane;
+            const int xs = 2 * tl.qx0 - kXL;
+            cols.init(2 * m0, xs, U->a.W, !kAdj, (2 * wq < 0) || (2 * wq + 2 * kWarpQ > U->a.W));
+            idle = wq + kHQ >= U->a.nec;
+            if constexpr (kAdj) hw.init(m0, AxisLen{U->a.nec, U->a.ndc});
+            pipe.init();
+            i = 0;
+        }
+        if (!idle) {
+            QRow<C> row;
+            fwd_lane_row<TI, C>(reinterpret_cast<const TI*>(ring.stage(s)), cols, row);
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&ring.empty[s]);
+            if constexpr (kAdj)
+                pipe.push(row, tl.qfirst + i, hw, AxisLen{U->a.ner, U->a.ndr}, U->a.scale);
+            else
+                pipe.push(row);
+            const int qo = tl.qfirst + i - Pipe::kLag;
+            if (qo >= tl.n0 && qo < tl.n1 && store_lane)
+                fwd_store_row<MODE_NONSEP, TB, TL>(U->a, row, qo, m0);
+        } else if (lane == 0) {
+            mbar_arrive(&ring.empty[s]);
+        }
+        if (++i == tl.nrows) warp_done(&p.done[unit], lane);
+    }
+}
+
+template <int WV, typename TB, typename TL, typename TO, bool ADJ>
+__global__ void __launch_bounds__(kThreads, min_ctas<WV>())
+    k_inverse_persistent(const PersistArgs<InvUnit> p) {
+    using Pipe = std::conditional_t<ADJ, AdjFwdPipe<WV>, InvPipe<WV>>;
+    using C = typename Pipe::C;
+    constexpr size_t kStageBytes = size_t(kBRow) * (sizeof(TL) + 3 * sizeof(TB));
+    extern __shared__ __align__(128) uint8_t smem_raw[];
+    const Ring ring = make_ring(smem_raw, kStageBytes);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    init_ring(ring);
+    __syncthreads();
+
+    if (warp == kNW) {  // ------------------------------------------------------ producer
+        int g = 0;
+        bool tma_used = false;
+        for (;;) {
+            bool ok;
+            const int t = claim(p, ring.abort, lane, ok);
+            if (t < 0) {
+                if (ok) post_sentinel(ring, g, lane, p.status);
+                break;
+            }
+            const InvUnit& U = p.units[__ldg(&p.item_unit[t])];
+            const Tile tl = tile_of(U.a, t - U.item_begin, U.strips);
+            const int xb = tl.qx0 - kXLB;
+            const CUtensorMap* maps[4] = {&U.tm[0], &U.tm[1], &U.tm[2], &U.tm[3]};
+            tma_used |= U.a.tma != 0;
+            bool alive = true;
+            for (int i = 0; i < tl.nrows; ++i, ++g) {
+                const int s = g % kStages;
+                if (g >= kStages) {
+                    bool w = mbar_wait(&ring.empty[s], ((g / kStages) - 1) & 1, ring.abort, p.status);
+                    if (!__all_sync(kFull, w)) {
+                        alive = false;
+                        break;
+                    }
+                }
+                if (lane == 0) ring.meta[s] = t;
+                inv_produce_row<TL, TB>(U.a, maps, ADJ, tl.qfirst + i, xb, ring.stage(s),
+                                        &ring.full[s], lane);
+            }
+            if (!alive) break;
+        }
+        // Normally the consumers take every stage (the sentinel last) before the CTA can exit, so
+        // all copies have landed.  After an abort, let the copies still in flight land first.  (No
+        // drain otherwise: the sentinel's stage has moved one phase past its last copy.)
+        if (tma_used && lane == 0 && *ring.abort) drain_ring(ring, g, p.status);
+        return;
+    }
+
+    // ------------------------------------------------------------------------- consumers
+    const bool store_lane = lane >= 1 && lane <= 30;
+    int cur = -1, i = 0, unit = 0;
+    Tile tl{};
+    InvCols cols;
+    LaneW hw;
+    bool idle = false;
+    int m0 = 0;
+    Pipe pipe;
+    for (int g = 0;; ++g) {
+        const int s = g % kStages;
+        bool ok = mbar_wait(&ring.full[s], (g / kStages) & 1, ring.abort, p.status);
+        if (!__all_sync(kFull, ok)) break;
+        const int t = ring.meta[s];
+        if (t < 0) break;
+        const InvUnit* U = &p.units[__ldg(&p.item_unit[t])];
+        if (t != cur) {
+            cur = t;
+            unit = __ldg(&p.item_unit[t]);
+            tl = tile_of(U->a, t - U->item_begin, U->strips);
+            const int wq = tl.qx0 - kHQ + warp * kWarpOut;
+            m0 = wq + kQ * lane;
+            cols.init(m0, tl.qx0 - kXLB, U->a.W, !ADJ, (2 * wq < 0) || (2 * wq + 2 * kWarpQ > U->a.W));
+            idle = wq + kHQ >= U->a.nec;
+            if constexpr (ADJ) hw.init(m0, AxisLen{U->a.nec, U->a.ndc});
+            pipe.init();
+            i = 0;
+        }
+        if (!idle) {
+            QRow<C> row;
+            inv_lane_row<TL, TB, C>(ring.stage(s), cols, row);
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&ring.empty[s]);
+            if constexpr (ADJ)
+                pipe.push(row, tl.qfirst + i, hw, AxisLen{U->a.ner, U->a.ndr}, U->a.scale);
+            else
+                pipe.push(row);
+            const int qo = tl.qfirst + i - Pipe::kLag;
+            if (qo >= tl.n0 && qo < tl.n1 && store_lane) inv_store_row<TO>(U->a, row, qo, m0);
+        } else if (lane == 0) {
+            mbar_arrive(&ring.empty[s]);
+        }
+        if (++i == tl.nrows) warp_done(&p.done[unit], lane);
+    }
+}
+
+}  // namespace dwt2

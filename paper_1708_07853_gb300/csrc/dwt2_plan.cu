@@ -1,0 +1,489 @@
+// dwt2_plan.cu -- batched plans: many images (any sizes), all levels, one persistent launch.
+//
+// dwt2_plan_create builds the work list (one unit per image and level, tiles of kCtaQ quad columns
+// x rows_per_tile quad rows), the TMA tensor maps and argument blocks of every unit in plan-owned
+// device memory, and captures [memset of the tile counters, persistent kernel] into a CUDA graph;
+// dwt2_plan_execute replays it.  rows_per_tile (and the CTAs per SM) come from an autotuner that
+// times candidates on the plan itself and keeps the winner in a text cache file, or from a
+// default when no cache file is given.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <fstream>
+#include <sstream>
+#include <string>
+#include <vector>
+
+#include "../../include/dwt2.h"
+#include "dwt2_internal.h"
+
+#define DWT2_EXPORT extern "C" __attribute__((visibility("default")))
+
+namespace dwt2 {
+void set_last_error(const char* msg);
+int plan_prepare_fwd_unit(FwdUnit* u, const void* in, int64_t in_pitch, int h, int w, int in_dt,
+                          int tb, int* status);
+int plan_prepare_inv_unit(InvUnit* u, const void* const bands[4], const int64_t pitches[4], int h,
+                          int w, int tl, int tb, void* out, int64_t out_pitch, int out_dt,
+                          int* status);
+Scale4 plan_level_scale(int wavelet, int h, int w);
+int64_t plan_image_scratch(int H, int W, int J, int wavelet, int64_t offs[2], int64_t pitch[2]);
+int plan_layout(int H, int W, int J, int band_dtype, dwt2_band* bands, size_t* bytes);
+int device_sm_count();
+}  // namespace dwt2
+
+using namespace dwt2;
+
+struct dwt2_plan {
+    int n = 0, wavelet = 0, levels = 0, img_dtype = 0, band_dtype = 0, direction = 0;
+    std::vector<dwt2_image_desc> imgs;
+    char* ws = nullptr;
+    size_t ws_bytes = 0;
+    void* dmem = nullptr;
+    int n_units = 0, n_items = 0;
+    int rows_per_tile = 0, ctas_per_sm = 0;
+    bool fwd_flow = true;  // forward data flow (forward, inverse adjoint) or inverse data flow
+    PersistArgs<FwdUnit> pf{};
+    PersistArgs<InvUnit> pi{};
+    size_t counter_bytes = 0;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
+namespace {
+
+constexpr int64_t kHeaderBytes = 256;
+
+int64_t align256(int64_t v) { return (v + 255) / 256 * 256; }
+
+bool valid_direction(int d) { return d >= DWT2_DIR_FORWARD && d <= DWT2_DIR_INVERSE_ADJOINT; }
+
+// Scratch of every image, after the shared 256-byte status header.
+int64_t scratch_offsets(const dwt2_image_desc* imgs, int n, int J, int wavelet,
+                        std::vector<int64_t>* base) {
+    int64_t off = kHeaderBytes;
+    for (int i = 0; i < n; ++i) {
+        int64_t o[2], p[2];
+        const int64_t bytes = plan_image_scratch(imgs[i].H, imgs[i].W, J, wavelet, o, p);
+        if (base) base->push_back(off);
+        off = align256(off + bytes);
+    }
+    return off;
+}
+
+int check_plan_args(const dwt2_image_desc* imgs, int n, int wavelet, int J, int img_dtype,
+                    int band_dtype, int direction) {
+    if (!imgs || n < 1 || !valid_direction(direction)) return DWT2_EINVAL;
+    if (wavelet < WV_CDF53_INT || wavelet > WV_CDF97) return DWT2_EINVAL;
+    const bool adj = direction == DWT2_DIR_FORWARD_ADJOINT || direction == DWT2_DIR_INVERSE_ADJOINT;
+    if (wavelet == WV_CDF53_INT) {
+        if (img_dtype != DT_I32 || band_dtype != DT_I32 || adj) return DWT2_EUNSUPPORTED;
+    } else {
+        if (img_dtype != DT_F32) return DWT2_EUNSUPPORTED;
+        if (band_dtype != DT_F32 && band_dtype != DT_BF16 && band_dtype != DT_F16)
+            return DWT2_EUNSUPPORTED;
+        if (adj && band_dtype != DT_F32) return DWT2_EUNSUPPORTED;
+    }
+    for (int i = 0; i < n; ++i) {
+        const dwt2_image_desc& d = imgs[i];
+        if (!d.img || !d.coeffs || d.H < 1 || d.W < 1) return DWT2_EINVAL;
+        if (J < 1 || J > dwt2_max_levels(d.H, d.W)) return DWT2_EINVAL;
+        if (d.img_pitch_bytes < int64_t(d.W) * 4 || d.img_pitch_bytes % 4 != 0) return DWT2_EINVAL;
+        if (reinterpret_cast<uintptr_t>(d.img) % 4 != 0 ||
+            reinterpret_cast<uintptr_t>(d.coeffs) % 16 != 0)
+            return DWT2_EINVAL;
+    }
+    return DWT2_OK;
+}
+
+// Default rows per tile: about four tiles per resident CTA over the whole batch, so that the
+// tail of the ticket queue is short, within [4, 128] quad rows.
+int default_rows(const dwt2_image_desc* imgs, int n, int J, int resident) {
+    double quad_rows_x_strips = 0;
+    for (int i = 0; i < n; ++i) {
+        int h = imgs[i].H, w = imgs[i].W;
+        for (int j = 0; j < J; ++j) {
+            const int ner = (h + 1) / 2, nec = (w + 1) / 2;
+            quad_rows_x_strips += double(ner) * ((nec + kCtaQ - 1) / kCtaQ);
+            h = ner;
+            w = nec;
+        }
+    }
+    const double want_tiles = 4.0 * std::max(1, resident);
+    const int r = int(std::ceil(quad_rows_x_strips / want_tiles));
+    return std::min(128, std::max(4, r));
+}
+
+// Builds the units and the ticket table for rows_per_tile; returns DWT2_OK or an error.
+int build_work(dwt2_plan* P, int rows, std::vector<FwdUnit>& fu, std::vector<InvUnit>& iu,
+               std::vector<int>& item_unit) {
+    const int n = P->n, J = P->levels;
+    std::vector<int64_t> wsbase;
+    scratch_offsets(P->imgs.data(), n, J, P->wavelet, &wsbase);
+    int* status = reinterpret_cast<int*>(P->ws);
+    const int ll_dt = P->wavelet == WV_CDF53_INT ? DT_I32 : DT_F32;
+    // images in descending size within a level: long tiles first, short ones fill the tail
+    std::vector<int> order(n);
+    for (int i = 0; i < n; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+        return int64_t(P->imgs[a].H) * P->imgs[a].W > int64_t(P->imgs[b].H) * P->imgs[b].W;
+    });
+    std::vector<int> unit_of(size_t(n) * (J + 1), -1);  // (image, level) -> unit
+    fu.clear();
+    iu.clear();
+    item_unit.clear();
+    for (int step = 0; step < J; ++step) {
+        const int j = P->fwd_flow ? step + 1 : J - step;  // level of this step
+        for (int i : order) {
+            const dwt2_image_desc& d = P->imgs[i];
+            std::vector<dwt2_band> bands(1 + 3 * J);
+            size_t cbytes = 0;
+            plan_layout(d.H, d.W, J, P->band_dtype, bands.data(), &cbytes);
+            int hh = d.H, ww = d.W;
+            for (int k = 1; k < j; ++k) {
+                hh = (hh + 1) / 2;
+                ww = (ww + 1) / 2;
+            }
+            int64_t o[2], pitch[2];
+            plan_image_scratch(d.H, d.W, J, P->wavelet, o, pitch);
+            char* sbase = P->ws + wsbase[i];
+            char* cb = static_cast<char*>(d.coeffs);
+            const dwt2_band& bhl = bands[1 + 3 * (J - j) + 0];
+            const dwt2_band& blh = bands[1 + 3 * (J - j) + 1];
+            const dwt2_band& bhh = bands[1 + 3 * (J - j) + 2];
+            const int ner = (hh + 1) / 2, nec = (ww + 1) / 2;
+            const int rpc = std::max(1, std::min(rows, ner));
+            const int strips = (nec + kCtaQ - 1) / kCtaQ;
+            const int n_items = strips * ((ner + rpc - 1) / rpc);
+            const int dep_level = P->fwd_flow ? j - 1 : j + 1;
+            const int dep = (dep_level >= 1 && dep_level <= J) ? unit_of[size_t(i) * (J + 1) + dep_level]
+                                                              : -1;
+            const int begin = int(item_unit.size());
+            if (P->fwd_flow) {
+                FwdUnit u;
+                std::memset(&u, 0, sizeof(u));
+                const void* in = j == 1 ? d.img : sbase + o[(j - 2) % 2];
+                const int64_t in_pitch = j == 1 ? d.img_pitch_bytes : pitch[(j - 2) % 2];
+                const int in_dt = j == 1 ? P->img_dtype : ll_dt;
+                int rc = plan_prepare_fwd_unit(&u, in, in_pitch, hh, ww, in_dt, P->band_dtype, status);
+                if (rc) return rc;
+                u.a.hl = {cb + bhl.offset_bytes, bhl.pitch_bytes};
+                u.a.lh = {cb + blh.offset_bytes, blh.pitch_bytes};
+                u.a.hh = {cb + bhh.offset_bytes, bhh.pitch_bytes};
+                if (j == J) u.a.ll = {cb + bands[0].offset_bytes, bands[0].pitch_bytes};
+                else u.a.ll = {sbase + o[(j - 1) % 2], pitch[(j - 1) % 2]};
+                if (P->direction == DWT2_DIR_INVERSE_ADJOINT) {
+                    const Scale4 s = plan_level_scale(P->wavelet, hh, ww);
+                    u.a.scale = Scale4{1.f / s.ll, 1.f / s.hl, 1.f / s.lh, 1.f / s.hh};
+                }
+                u.a.rpc = rpc;
+                u.item_begin = begin;
+                u.n_items = n_items;
+                u.strips = strips;
+                u.dep = dep;
+                unit_of[size_t(i) * (J + 1) + j] = int(fu.size());
+                fu.push_back(u);
+            } else {
+                InvUnit u;
+                std::memset(&u, 0, sizeof(u));
+                const void* bp[4];
+                int64_t pp[4];
+                if (j == J) {
+                    bp[0] = cb + bands[0].offset_bytes;
+                    pp[0] = bands[0].pitch_bytes;
+                } else {
+                    bp[0] = sbase + o[(j - 1) % 2];
+                    pp[0] = pitch[(j - 1) % 2];
+                }
+                bp[1] = cb + bhl.offset_bytes;
+                pp[1] = bhl.pitch_bytes;
+                bp[2] = cb + blh.offset_bytes;
+                pp[2] = blh.pitch_bytes;
+                bp[3] = cb + bhh.offset_bytes;
+                pp[3] = bhh.pitch_bytes;
+                void* out = j == 1 ? d.img : sbase + o[(j - 2) % 2];
+                const int64_t opitch = j == 1 ? d.img_pitch_bytes : pitch[(j - 2) % 2];
+                const int out_dt = j == 1 ? P->img_dtype : ll_dt;
+                int rc = plan_prepare_inv_unit(&u, bp, pp, hh, ww, ll_dt, P->band_dtype, out, opitch,
+                                               out_dt, status);
+                if (rc) return rc;
+                if (P->direction == DWT2_DIR_FORWARD_ADJOINT)
+                    u.a.scale = plan_level_scale(P->wavelet, hh, ww);
+                u.a.rpc = rpc;
+                u.item_begin = begin;
+                u.n_items = n_items;
+                u.strips = strips;
+                u.dep = dep;
+                unit_of[size_t(i) * (J + 1) + j] = int(iu.size());
+                iu.push_back(u);
+            }
+            const int uidx = P->fwd_flow ? int(fu.size()) - 1 : int(iu.size()) - 1;
+            for (int k = 0; k < n_items; ++k) item_unit.push_back(uidx);
+        }
+    }
+    return DWT2_OK;
+}
+
+cudaError_t launch(dwt2_plan* P, cudaStream_t st, int* occ) {
+    if (P->fwd_flow) {
+        const int mode = P->direction == DWT2_DIR_INVERSE_ADJOINT ? MODE_ADJ_INV : MODE_NONSEP;
+        return launch_fwd_persistent(P->wavelet, mode, P->band_dtype, P->pf, P->ctas_per_sm, st, occ);
+    }
+    return launch_inv_persistent(P->wavelet, P->direction == DWT2_DIR_FORWARD_ADJOINT,
+                                 P->band_dtype, P->pi, P->ctas_per_sm, st, occ);
+}
+
+void free_graph(dwt2_plan* P) {
+    if (P->exec) cudaGraphExecDestroy(P->exec);
+    if (P->graph) cudaGraphDestroy(P->graph);
+    P->exec = nullptr;
+    P->graph = nullptr;
+}
+
+// (Re)builds units, uploads them and captures the graph for the plan's rows_per_tile.
+int materialise(dwt2_plan* P) {
+    std::vector<FwdUnit> fu;
+    std::vector<InvUnit> iu;
+    std::vector<int> item_unit;
+    int rc = build_work(P, P->rows_per_tile, fu, iu, item_unit);
+    if (rc) return rc;
+    P->n_units = int(P->fwd_flow ? fu.size() : iu.size());
+    P->n_items = int(item_unit.size());
+    const size_t unit_bytes = P->fwd_flow ? fu.size() * sizeof(FwdUnit) : iu.size() * sizeof(InvUnit);
+    const size_t table_off = align256(int64_t(unit_bytes));
+    const size_t counter_off = align256(int64_t(table_off + item_unit.size() * sizeof(int)));
+    P->counter_bytes = sizeof(int) * (1 + size_t(P->n_units));
+    const size_t total = counter_off + P->counter_bytes;
+    if (P->dmem) cudaFree(P->dmem);
+    P->dmem = nullptr;
+    cudaError_t e = cudaMalloc(&P->dmem, total);
+    if (e != cudaSuccess) {
+        set_last_error(cudaGetErrorString(e));
+        return DWT2_ENOMEM;
+    }
+    char* base = static_cast<char*>(P->dmem);
+    e = cudaMemcpy(base, P->fwd_flow ? static_cast<const void*>(fu.data()) : iu.data(), unit_bytes,
+                   cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(base + table_off, item_unit.data(), item_unit.size() * sizeof(int),
+                       cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        set_last_error(cudaGetErrorString(e));
+        return DWT2_ECUDA;
+    }
+    int* counters = reinterpret_cast<int*>(base + counter_off);
+    int* status = reinterpret_cast<int*>(P->ws);
+    if (P->fwd_flow)
+        P->pf = PersistArgs<FwdUnit>{reinterpret_cast<const FwdUnit*>(base),
+                                     reinterpret_cast<const int*>(base + table_off), P->n_items,
+                                     counters, counters + 1, status};
+    else
+        P->pi = PersistArgs<InvUnit>{reinterpret_cast<const InvUnit*>(base),
+                                     reinterpret_cast<const int*>(base + table_off), P->n_items,
+                                     counters, counters + 1, status};
+    // capture [memset counters, persistent kernel]
+    free_graph(P);
+    cudaStream_t cs;
+    e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        set_last_error(cudaGetErrorString(e));
+        return DWT2_ECUDA;
+    }
+    int occ = 0;
+    launch(P, cs, &occ);  // configures the kernel (attributes) before capture
+    e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) e = cudaMemsetAsync(counters, 0, P->counter_bytes, cs);
+    if (e == cudaSuccess) e = launch(P, cs, nullptr);
+    cudaGraph_t g = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(cs, &g);
+    if (e == cudaSuccess) e = e2;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&P->exec, g, 0);
+    P->graph = g;
+    cudaStreamDestroy(cs);
+    if (e != cudaSuccess) {
+        set_last_error(cudaGetErrorString(e));
+        return DWT2_ECUDA;
+    }
+    return DWT2_OK;
+}
+
+std::string tune_key(const dwt2_plan* P) {
+    cudaDeviceProp prop;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaGetDeviceProperties(&prop, dev);
+    int64_t px = 0;
+    for (const auto& d : P->imgs) px += int64_t(d.H) * d.W;
+    std::ostringstream k;
+    std::string name(prop.name);
+    std::replace(name.begin(), name.end(), ' ', '_');
+    k << name << "|dir" << P->direction << "|wv" << P->wavelet << "|bt" << P->band_dtype << "|L"
+      << P->levels << "|n" << P->n << "|px2^" << int(std::lround(std::log2(double(std::max<int64_t>(px, 1)))));
+    return k.str();
+}
+
+bool cache_lookup(const char* path, const std::string& key, int* rows, int* ctas) {
+    std::ifstream f(path);
+    std::string line;
+    bool found = false;
+    while (std::getline(f, line)) {
+        std::istringstream ls(line);
+        std::string k;
+        int r = 0, c = 0;
+        if (ls >> k >> r >> c && k == key) {  // the last entry for a key wins
+            *rows = r;
+            *ctas = c;
+            found = true;
+        }
+    }
+    return found;
+}
+
+// Times each candidate (rows per tile x CTAs per SM) on the plan itself: 2 warm-up and 5 timed
+// graph replays, median; keeps the fastest.
+int autotune(dwt2_plan* P, int occ) {
+    const int rows_c[] = {4, 8, 16, 32, 64, 128};
+    std::vector<int> ctas_c = {occ};
+    if (occ > 1) ctas_c.push_back(occ - 1);
+    cudaStream_t st;
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) return DWT2_ECUDA;
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    float best = 1e30f;
+    int best_r = P->rows_per_tile, best_c = P->ctas_per_sm;
+    for (int r : rows_c) {
+        for (int c : ctas_c) {
+            P->rows_per_tile = r;
+            P->ctas_per_sm = c;
+            if (materialise(P)) continue;
+            std::vector<float> ts;
+            for (int it = 0; it < 7; ++it) {
+                cudaEventRecord(a, st);
+                cudaGraphLaunch(P->exec, st);
+                cudaEventRecord(b, st);
+                cudaEventSynchronize(b);
+                float ms = 0;
+                cudaEventElapsedTime(&ms, a, b);
+                if (it >= 2) ts.push_back(ms);
+            }
+            std::sort(ts.begin(), ts.end());
+            if (!ts.empty() && ts[ts.size() / 2] < best) {
+                best = ts[ts.size() / 2];
+                best_r = r;
+                best_c = c;
+            }
+        }
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    cudaStreamDestroy(st);
+    P->rows_per_tile = best_r;
+    P->ctas_per_sm = best_c;
+    return DWT2_OK;
+}
+
+}  // namespace
+
+// ==================================================================================== C ABI
+DWT2_EXPORT size_t dwt2_plan_workspace_bytes(const dwt2_image_desc* imgs, int n, int wavelet,
+                                             int levels, int band_dtype) {
+    if (!imgs || n < 1 || wavelet < 0 || wavelet > 2 || band_dtype < 0 || band_dtype > 3) return 0;
+    for (int i = 0; i < n; ++i)
+        if (imgs[i].H < 1 || imgs[i].W < 1 || levels < 1 || levels > dwt2_max_levels(imgs[i].H, imgs[i].W))
+            return 0;
+    return size_t(scratch_offsets(imgs, n, levels, wavelet, nullptr));
+}
+
+DWT2_EXPORT int dwt2_plan_create(const dwt2_image_desc* imgs, int n, int wavelet, int levels,
+                                 int img_dtype, int band_dtype, int direction, void* workspace,
+                                 size_t ws_bytes, const char* tune_cache, dwt2_plan** out) {
+    if (!out) return DWT2_EINVAL;
+    *out = nullptr;
+    int rc = check_plan_args(imgs, n, wavelet, levels, img_dtype, band_dtype, direction);
+    if (rc) return rc;
+    const size_t need = dwt2_plan_workspace_bytes(imgs, n, wavelet, levels, band_dtype);
+    if (!workspace || reinterpret_cast<uintptr_t>(workspace) % 256 != 0) return DWT2_EINVAL;
+    if (ws_bytes < need) return DWT2_ENOMEM;
+    dwt2_plan* P = new dwt2_plan;
+    P->n = n;
+    P->wavelet = wavelet;
+    P->levels = levels;
+    P->img_dtype = img_dtype;
+    P->band_dtype = band_dtype;
+    P->direction = direction;
+    P->imgs.assign(imgs, imgs + n);
+    P->ws = static_cast<char*>(workspace);
+    P->ws_bytes = ws_bytes;
+    P->fwd_flow = direction == DWT2_DIR_FORWARD || direction == DWT2_DIR_INVERSE_ADJOINT;
+    // occupancy of the kernel this plan launches
+    P->rows_per_tile = 16;
+    int occ = 0;
+    {
+        P->pf = PersistArgs<FwdUnit>{};
+        P->pi = PersistArgs<InvUnit>{};
+        cudaError_t e = launch(P, nullptr, &occ);
+        if (e == cudaErrorNotSupported) {
+            delete P;
+            return DWT2_EUNSUPPORTED;
+        }
+    }
+    P->ctas_per_sm = occ;
+    P->rows_per_tile = default_rows(imgs, n, levels, occ * device_sm_count());
+    bool tuned = false;
+    std::string key;
+    if (tune_cache && *tune_cache) {
+        key = tune_key(P);
+        int r = 0, c = 0;
+        if (cache_lookup(tune_cache, key, &r, &c) && r > 0 && c > 0) {
+            P->rows_per_tile = r;
+            P->ctas_per_sm = std::min(c, occ);
+        } else {
+            rc = autotune(P, occ);
+            if (rc) {
+                dwt2_plan_destroy(P);
+                return rc;
+            }
+            tuned = true;
+        }
+    }
+    rc = materialise(P);
+    if (rc) {
+        dwt2_plan_destroy(P);
+        return rc;
+    }
+    if (tuned) {
+        std::ofstream f(tune_cache, std::ios::app);
+        if (f) f << key << " " << P->rows_per_tile << " " << P->ctas_per_sm << "\n";
+    }
+    *out = P;
+    return DWT2_OK;
+}
+
+DWT2_EXPORT int dwt2_plan_execute(dwt2_plan* plan, void* stream) {
+    if (!plan || !plan->exec) return DWT2_EINVAL;
+    cudaError_t e = cudaGraphLaunch(plan->exec, static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) {
+        set_last_error(cudaGetErrorString(e));
+        return DWT2_ECUDA;
+    }
+    return DWT2_OK;
+}
+
+DWT2_EXPORT int dwt2_plan_info(const dwt2_plan* plan, int* rows_per_tile, int* ctas_per_sm,
+                               int* n_tiles) {
+    if (!plan) return DWT2_EINVAL;
+    if (rows_per_tile) *rows_per_tile = plan->rows_per_tile;
+    if (ctas_per_sm) *ctas_per_sm = plan->ctas_per_sm;
+    if (n_tiles) *n_tiles = plan->n_items;
+    return DWT2_OK;
+}
+
+DWT2_EXPORT int dwt2_plan_destroy(dwt2_plan* plan) {
+    if (!plan) return DWT2_EINVAL;
+    free_graph(plan);
+    if (plan->dmem) cudaFree(plan->dmem);
+    delete plan;
+    return DWT2_OK;
+}

@@ -29,7 +29,10 @@ STATUS = {0: "ok", 1: "EINVAL", 2: "EUNSUPPORTED", 3: "ENOMEM", 4: "ECUDA", 5: "
 EXPORTS = ["dwt2_status_string", "dwt2_last_error", "dwt2_max_levels", "dwt2_layout",
            "dwt2_workspace_bytes", "dwt2_workspace_bytes_scheme", "dwt2_workspace_init",
            "dwt2_check_status", "dwt2_forward", "dwt2_forward_scheme", "dwt2_inverse",
-           "dwt2_forward_static", "dwt2_forward_adjoint", "dwt2_inverse_adjoint"]
+           "dwt2_forward_static", "dwt2_forward_adjoint", "dwt2_inverse_adjoint",
+           "dwt2_plan_workspace_bytes", "dwt2_plan_create", "dwt2_plan_execute", "dwt2_plan_info",
+           "dwt2_plan_destroy"]
+DIRECTIONS = {"forward": 0, "inverse": 1, "forward_adjoint": 2, "inverse_adjoint": 3}
 
 
 class Dwt2Error(RuntimeError):
@@ -38,6 +41,11 @@ class Dwt2Error(RuntimeError):
         msg = f"{what}: {STATUS.get(status, status)}"
         err = _lib().dwt2_last_error().decode()
         super().__init__(msg + (f" ({err})" if err and status in (3, 4, 6) else ""))
+
+
+class ImageDesc(ctypes.Structure):
+    _fields_ = [("img", ctypes.c_void_p), ("img_pitch_bytes", ctypes.c_int64),
+                ("H", ctypes.c_int), ("W", ctypes.c_int), ("coeffs", ctypes.c_void_p)]
 
 
 class Band(ctypes.Structure):
@@ -74,10 +82,19 @@ def _lib():
         lib.dwt2_inverse.argtypes = [vp, vp, i64, i, i, i, vp, sz, i, i, i, vp]
         lib.dwt2_forward_static.argtypes = [vp, i64, i, i, i, vp, i, i, i, vp]
         lib.dwt2_forward_adjoint.argtypes = [vp, vp, i64, i, i, i, vp, sz, i, i, i, vp]
+        pd = ctypes.POINTER(ImageDesc)
+        lib.dwt2_plan_workspace_bytes.restype = sz
+        lib.dwt2_plan_workspace_bytes.argtypes = [pd, i, i, i, i]
+        lib.dwt2_plan_create.argtypes = [pd, i, i, i, i, i, i, vp, sz, ctypes.c_char_p,
+                                         ctypes.POINTER(vp)]
+        lib.dwt2_plan_execute.argtypes = [vp, vp]
+        lib.dwt2_plan_info.argtypes = [vp, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i)]
+        lib.dwt2_plan_destroy.argtypes = [vp]
         lib.dwt2_inverse_adjoint.argtypes = [vp, i64, i, i, i, vp, vp, sz, i, i, i, vp]
         for f in ("dwt2_max_levels", "dwt2_layout", "dwt2_workspace_init", "dwt2_check_status",
                   "dwt2_forward", "dwt2_forward_scheme", "dwt2_inverse", "dwt2_forward_static",
-                  "dwt2_forward_adjoint", "dwt2_inverse_adjoint"):
+                  "dwt2_forward_adjoint", "dwt2_inverse_adjoint", "dwt2_plan_create",
+                  "dwt2_plan_execute", "dwt2_plan_info", "dwt2_plan_destroy"):
             getattr(lib, f).restype = i
         _LIB = lib
     return _LIB
@@ -260,3 +277,63 @@ def inverse_adjoint(x: torch.Tensor, wavelet="cdf97", levels: int = 1, out: Coef
     if rc:
         raise Dwt2Error(rc, "dwt2_inverse_adjoint")
     return out
+
+
+class Plan:
+    """A batched plan (dwt2_plan_create): every level of every image in one persistent launch,
+    replayed from a CUDA graph by run().  Keeps the tensors it was built on alive."""
+
+    def __init__(self, images, coeffs, wavelet, levels: int, direction: str = "forward",
+                 band_dtype: int | None = None, tune_cache: str | None = None):
+        self.images, self.coeffs = list(images), list(coeffs)
+        n = len(self.images)
+        wid = _wid(wavelet)
+        img_dt = TORCH_DT[self.images[0].dtype]
+        bdt = self.coeffs[0].band_dtype if band_dtype is None else band_dtype
+        descs = (ImageDesc * n)()
+        for k, (x, c) in enumerate(zip(self.images, self.coeffs)):
+            _check_img(x)
+            descs[k] = ImageDesc(x.data_ptr(), x.stride(0) * x.element_size(), x.shape[0],
+                                 x.shape[1], c.buffer.data_ptr())
+        nws = _lib().dwt2_plan_workspace_bytes(descs, n, wid, levels, bdt)
+        if nws == 0:
+            raise Dwt2Error(1, "dwt2_plan_workspace_bytes")
+        self.workspace = new_workspace(nws, self.images[0].device)
+        h = ctypes.c_void_p(0)
+        rc = _lib().dwt2_plan_create(descs, n, wid, levels, img_dt, bdt, DIRECTIONS[direction],
+                                     self.workspace.data_ptr(), nws,
+                                     tune_cache.encode() if tune_cache else None, ctypes.byref(h))
+        if rc:
+            raise Dwt2Error(rc, "dwt2_plan_create")
+        self.handle = h
+
+    def run(self, stream=None):
+        rc = _lib().dwt2_plan_execute(self.handle, _stream_ptr(stream))
+        if rc:
+            raise Dwt2Error(rc, "dwt2_plan_execute")
+
+    def info(self):
+        r, c, t = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_int(0)
+        _lib().dwt2_plan_info(self.handle, ctypes.byref(r), ctypes.byref(c), ctypes.byref(t))
+        return {"rows_per_tile": r.value, "ctas_per_sm": c.value, "tiles": t.value}
+
+    def close(self):
+        if getattr(self, "handle", None):
+            _lib().dwt2_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def plan_forward(images, wavelet="cdf97", levels: int = 1, band_dtype=None,
+                 tune_cache: str | None = None):
+    """A forward plan over CUDA images of any sizes; returns (plan, [Coeffs per image])."""
+    dev = images[0].device
+    bdt = TORCH_DT[band_dtype] if isinstance(band_dtype, torch.dtype) else (
+        band_dtype if band_dtype is not None else TORCH_DT[images[0].dtype])
+    coeffs = [alloc_coeffs(x.shape[0], x.shape[1], levels, wavelet, bdt, dev) for x in images]
+    return Plan(images, coeffs, wavelet, levels, "forward", bdt, tune_cache), coeffs
