@@ -188,6 +188,46 @@ int dwt2_inverse_adjoint(const void* g_img, int64_t g_img_pitch_bytes, int H, in
                          int band_dtype, void* stream);
 
 /* ---------------------------------------------------------------------------------------------
+ * Uniform batches: N images of the same H x W, wavelet, levels and types, transformed by the
+ * same per-level kernels as the single-image calls (one launch per level covers all N images; the
+ * image index is the third grid dimension).  Each image's result equals, bit for bit, what the
+ * single-image call gives for it.  The paper transforms one image at a time (Sec. 4); batching
+ * changes only how many images a launch covers, not the arithmetic.
+ *   img / g_img               image z at img + z * img_batch_bytes, rows img_pitch_bytes apart;
+ *                             img_batch_bytes >= H * img_pitch_bytes when N > 1.
+ *   coeffs / g_coeffs         image z's coefficients, laid out by dwt2_layout(H, W, levels,
+ *                             band_dtype), at coeffs + z * coeff_batch_bytes; coeff_batch_bytes
+ *                             >= that layout's total bytes and a multiple of 16 when N > 1
+ *                             (a contiguous (N, total/4) float32 tensor qualifies, since the
+ *                             layout's total is a multiple of 256 bytes).
+ *   N                         1..65535 (the batch strides are ignored when N == 1).
+ *   workspace, ws_bytes       at least dwt2_workspace_bytes_batch(N, H, W, levels, wavelet,
+ *                             band_dtype) bytes, 16-byte aligned, prepared by dwt2_workspace_init;
+ *                             images share the status word at its start and each has its own
+ *                             region for the intermediate LL planes.
+ * Errors as for the single-image calls (DWT2_EINVAL for a bad N or batch stride); the adjoint
+ * entries are float-only as above.  Tensor maps address the batch as a third dimension, so a
+ * batch stride that is not a multiple of 16 bytes selects the plain-load path. */
+size_t dwt2_workspace_bytes_batch(int N, int H, int W, int levels, int wavelet, int band_dtype);
+int dwt2_forward_batch(const void* img, int64_t img_pitch_bytes, int64_t img_batch_bytes, int N,
+                       int H, int W, int img_dtype, void* coeffs, int64_t coeff_batch_bytes,
+                       void* workspace, size_t ws_bytes, int wavelet, int levels, int band_dtype,
+                       void* stream);
+int dwt2_inverse_batch(const void* coeffs, int64_t coeff_batch_bytes, void* img,
+                       int64_t img_pitch_bytes, int64_t img_batch_bytes, int N, int H, int W,
+                       int img_dtype, void* workspace, size_t ws_bytes, int wavelet, int levels,
+                       int band_dtype, void* stream);
+int dwt2_forward_adjoint_batch(const void* g_coeffs, int64_t coeff_batch_bytes, void* g_img,
+                               int64_t g_img_pitch_bytes, int64_t g_img_batch_bytes, int N, int H,
+                               int W, int img_dtype, void* workspace, size_t ws_bytes, int wavelet,
+                               int levels, int band_dtype, void* stream);
+int dwt2_inverse_adjoint_batch(const void* g_img, int64_t g_img_pitch_bytes,
+                               int64_t g_img_batch_bytes, int N, int H, int W, int img_dtype,
+                               void* g_coeffs, int64_t coeff_batch_bytes, void* workspace,
+                               size_t ws_bytes, int wavelet, int levels, int band_dtype,
+                               void* stream);
+
+/* ---------------------------------------------------------------------------------------------
  * Batched plans: many images of any sizes, every level, ONE persistent kernel launch replayed
  * from a CUDA graph.  The work is a list of tiles (image, level, strip of 240 quad columns,
  * block of rows) in level-major order; CTAs claim tiles from a counter, and a tile of level j of

@@ -8,7 +8,8 @@ kernels, from the coarsest level down (W^T) or from the finest up (W^-T).
 Coefficients travel as one flat float32 tensor per image, laid out exactly as dwt2_layout
 describes (fp32 storage makes every band, and the padding between rows and bands, a whole
 number of floats).  `band_views` gives the LL / HL / LH / HH planes as views into it; the
-padding entries are zero in forward outputs and in gradients.
+padding entries are zero in forward outputs and in gradients.  All images of a call go through
+the uniform-batch entry points: one launch per level covers every image.
 """
 from __future__ import annotations
 
@@ -55,11 +56,7 @@ class DWT2Fn(torch.autograd.Function):
         xs = _images(x.contiguous())
         n = coeff_floats(H, W, levels)
         out = torch.zeros((xs.shape[0], n), dtype=torch.float32, device=x.device)
-        ws = D.new_workspace(D.workspace_bytes(H, W, levels, wavelet, D.DT_F32), x.device)
-        lay, nbytes = D.layout(H, W, levels, D.DT_F32)
-        for i in range(xs.shape[0]):
-            c = D.Coeffs(out[i].view(torch.uint8), H, W, D._wid(wavelet), levels, D.DT_F32, lay)
-            D.forward(xs[i], wavelet, levels, out=c, workspace=ws)
+        D.forward_batch(xs, wavelet, levels, D.DT_F32, out=out)
         ctx.meta = (H, W, wavelet, levels, x.shape)
         return out.reshape(*x.shape[:-2], n)
 
@@ -67,12 +64,7 @@ class DWT2Fn(torch.autograd.Function):
     def backward(ctx, g: torch.Tensor):
         H, W, wavelet, levels, xshape = ctx.meta
         gs = g.reshape(-1, g.shape[-1]).contiguous()
-        gx = torch.empty((gs.shape[0], H, W), dtype=torch.float32, device=g.device)
-        ws = D.new_workspace(D.workspace_bytes(H, W, levels, wavelet, D.DT_F32), g.device)
-        lay, _ = D.layout(H, W, levels, D.DT_F32)
-        for i in range(gs.shape[0]):
-            c = D.Coeffs(gs[i].view(torch.uint8), H, W, D._wid(wavelet), levels, D.DT_F32, lay)
-            D.forward_adjoint(c, out=gx[i], workspace=ws)
+        gx = D.forward_adjoint_batch(gs, H, W, wavelet, levels)
         return gx.reshape(xshape), None, None
 
 
@@ -83,12 +75,7 @@ class IDWT2Fn(torch.autograd.Function):
     def forward(ctx, c: torch.Tensor, H: int, W: int, wavelet: str, levels: int):
         _check(c)
         cs = c.reshape(-1, c.shape[-1]).contiguous()
-        x = torch.empty((cs.shape[0], H, W), dtype=torch.float32, device=c.device)
-        ws = D.new_workspace(D.workspace_bytes(H, W, levels, wavelet, D.DT_F32), c.device)
-        lay, _ = D.layout(H, W, levels, D.DT_F32)
-        for i in range(cs.shape[0]):
-            cc = D.Coeffs(cs[i].view(torch.uint8), H, W, D._wid(wavelet), levels, D.DT_F32, lay)
-            D.inverse(cc, out=x[i], workspace=ws)
+        x = D.inverse_batch(cs, H, W, wavelet, levels, D.DT_F32, img_dtype=torch.float32)
         ctx.meta = (H, W, wavelet, levels, c.shape)
         return x.reshape(*c.shape[:-1], H, W)
 
@@ -96,13 +83,8 @@ class IDWT2Fn(torch.autograd.Function):
     def backward(ctx, gx: torch.Tensor):
         H, W, wavelet, levels, cshape = ctx.meta
         gxs = _images(gx.contiguous())
-        n = cshape[-1]
-        gc = torch.zeros((gxs.shape[0], n), dtype=torch.float32, device=gx.device)
-        ws = D.new_workspace(D.workspace_bytes(H, W, levels, wavelet, D.DT_F32), gx.device)
-        lay, _ = D.layout(H, W, levels, D.DT_F32)
-        for i in range(gxs.shape[0]):
-            out = D.Coeffs(gc[i].view(torch.uint8), H, W, D._wid(wavelet), levels, D.DT_F32, lay)
-            D.inverse_adjoint(gxs[i], wavelet, levels, out=out, workspace=ws)
+        gc = torch.zeros((gxs.shape[0], cshape[-1]), dtype=torch.float32, device=gx.device)
+        D.inverse_adjoint_batch(gxs, wavelet, levels, out=gc)
         return gc.reshape(cshape), None, None, None, None
 
 

@@ -150,32 +150,36 @@ static CUtensorMapDataType tm_type(int dt) {
     }
 }
 
-// A 2-D map over an h x w plane with 1-row boxes of box_w elements.
-// MAP_OK: use TMA.  MAP_INELIGIBLE: the plane cannot be addressed by TMA (base or pitch not
-// 16-byte aligned, empty plane): use the plain-load path.  MAP_ERROR: an eligible plane was
-// rejected by the driver, which is a library bug and is reported, never silently worked around.
+// A 3-D map over n planes of h x w (image z at base + z * bstride) with 1-row boxes of box_w
+// elements; n = 1 for a single plane.
+// MAP_OK: use TMA.  MAP_INELIGIBLE: the planes cannot be addressed by TMA (base, pitch or batch
+// stride not 16-byte aligned, empty plane): use the plain-load path.  MAP_ERROR: an eligible
+// plane was rejected by the driver, which is a library bug and is reported, never silently
+// worked around.
 enum MapResult { MAP_OK = 0, MAP_INELIGIBLE = 1, MAP_ERROR = 2 };
 
-static MapResult make_map(CUtensorMap* m, const void* base, int64_t pitch, int h, int w, int dt,
-                          int box_w) {
+static MapResult make_map(CUtensorMap* m, const void* base, int64_t pitch, int64_t bstride, int h,
+                          int w, int n, int dt, int box_w) {
     std::memset(m, 0, sizeof(*m));
-    if (h < 1 || w < 1 || !aligned(base, 16) || pitch % 16 != 0) return MAP_INELIGIBLE;
+    if (n <= 1) bstride = int64_t(h) * pitch;
+    if (h < 1 || w < 1 || n < 1 || !aligned(base, 16) || pitch % 16 != 0 || bstride % 16 != 0)
+        return MAP_INELIGIBLE;
     auto fn = encode_fn();
     if (!fn) {
         g_last_error = "cuTensorMapEncodeTiled is not available from the driver";
         return MAP_ERROR;
     }
-    cuuint64_t dims[2] = {cuuint64_t(w), cuuint64_t(h)};
-    cuuint64_t strides[1] = {cuuint64_t(pitch)};
-    cuuint32_t box[2] = {cuuint32_t(box_w), 1};
-    cuuint32_t estr[2] = {1, 1};
-    CUresult r = fn(m, tm_type(dt), 2, const_cast<void*>(base), dims, strides, box, estr,
+    cuuint64_t dims[3] = {cuuint64_t(w), cuuint64_t(h), cuuint64_t(n)};
+    cuuint64_t strides[2] = {cuuint64_t(pitch), cuuint64_t(bstride)};
+    cuuint32_t box[3] = {cuuint32_t(box_w), 1, 1};
+    cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = fn(m, tm_type(dt), 3, const_cast<void*>(base), dims, strides, box, estr,
                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) {
         g_last_error = "cuTensorMapEncodeTiled failed (CUresult " + std::to_string(int(r)) +
-                       ") for a " + std::to_string(h) + "x" + std::to_string(w) + " plane, box " +
-                       std::to_string(box_w);
+                       ") for " + std::to_string(n) + " planes of " + std::to_string(h) + "x" +
+                       std::to_string(w) + ", box " + std::to_string(box_w);
         return MAP_ERROR;
     }
     return MAP_OK;
@@ -201,11 +205,13 @@ static int check_image(const void* img, int64_t pitch, int W, int dt) {
     return DWT2_OK;
 }
 
-static FwdArgs level_args(const void* in, int64_t in_pitch, int h, int w, int* status) {
+static FwdArgs level_args(const void* in, int64_t in_pitch, int64_t in_bstride, int h, int w,
+                          int n, int* status) {
     FwdArgs a;
     std::memset(&a, 0, sizeof(a));
     a.in = in;
     a.in_pitch = in_pitch;
+    a.in_bstride = in_bstride;
     a.H = h;
     a.W = w;
     a.ner = (h + 1) / 2;
@@ -213,6 +219,7 @@ static FwdArgs level_args(const void* in, int64_t in_pitch, int h, int w, int* s
     a.nec = (w + 1) / 2;
     a.ndc = w / 2;
     a.status = status;
+    a.nbatch = n;
     return a;
 }
 
@@ -238,23 +245,48 @@ static Scale4 level_scale(int wavelet, int h, int w) {
 
 static Scale4 reciprocal(Scale4 s) { return Scale4{1.f / s.ll, 1.f / s.hl, 1.f / s.lh, 1.f / s.hh}; }
 
+// A batch of N images (N = 1 for the single-image entry points): image z of the input at
+// img + z * img_bstride, its coefficients at coeffs + z * coeff_bstride, and its intermediate LL
+// planes in workspace region z (after the shared 256-byte status header).
+struct Batch {
+    int N;
+    int64_t img_bstride, coeff_bstride;
+};
+
+static int check_batch(const Batch& b, int H, int64_t img_pitch, int img_dtype, const Layout& L) {
+    if (b.N < 1 || b.N > 65535) return DWT2_EINVAL;
+    if (b.N == 1) return DWT2_OK;
+    if (b.img_bstride < int64_t(H) * img_pitch || b.img_bstride % int64_t(esize(img_dtype)) != 0 ||
+        b.coeff_bstride < L.bytes || b.coeff_bstride % 16 != 0)
+        return DWT2_EINVAL;
+    return DWT2_OK;
+}
+
+// Bytes between the workspace regions of consecutive images of a batch.
+static int64_t ws_region(const WsPlan& wp) { return align_up(wp.bytes - kHeader, 256); }
+
 // adjoint = true: W^-T, the transpose of the inverse (image-shaped gradient in, band gradients
 // out), level by level 1..J with the forward kernel's data flow.
 static int forward_impl(const void* img, int64_t img_pitch, int H, int W, int img_dtype,
                         void* coeffs, void* ws, size_t ws_bytes, int wavelet, int J,
-                        int band_dtype, int scheme, cudaStream_t st, bool adjoint = false) {
+                        int band_dtype, int scheme, cudaStream_t st, bool adjoint = false,
+                        Batch bt = Batch{1, 0, 0}) {
     int rc = check_types(wavelet, img_dtype, band_dtype);
     if (rc) return rc;
     if (adjoint && (wavelet == WV_CDF53_INT || img_dtype != DT_F32 || band_dtype != DT_F32))
         return DWT2_EUNSUPPORTED;
     if (scheme < DWT2_SCHEME_NONSEP || scheme > DWT2_SCHEME_SEP_TWOPASS) return DWT2_EINVAL;
-    if (scheme != DWT2_SCHEME_NONSEP && (img_dtype != band_dtype)) return DWT2_EUNSUPPORTED;
+    if (scheme != DWT2_SCHEME_NONSEP && (img_dtype != band_dtype || bt.N != 1))
+        return DWT2_EUNSUPPORTED;
     Layout L;
     if ((rc = make_layout(H, W, J, band_dtype, &L))) return rc;
     if ((rc = check_image(img, img_pitch, W, img_dtype))) return rc;
+    if ((rc = check_batch(bt, H, img_pitch, img_dtype, L))) return rc;
     if (!coeffs || !ws || !aligned(coeffs, 16) || !aligned(ws, 16)) return DWT2_EINVAL;
     const WsPlan wp = plan_workspace(H, W, J, wavelet, scheme);
-    if (int64_t(ws_bytes) < wp.bytes) return DWT2_ENOMEM;
+    const int64_t region = ws_region(wp);
+    if (int64_t(ws_bytes) < kHeader + bt.N * region) return DWT2_ENOMEM;
+    const int64_t cbs = bt.N > 1 ? bt.coeff_bstride : 0;
 
     char* cb = static_cast<char*>(coeffs);
     char* wb = static_cast<char*>(ws);
@@ -262,42 +294,42 @@ static int forward_impl(const void* img, int64_t img_pitch, int H, int W, int im
     const int ll_dt = wavelet == WV_CDF53_INT ? DT_I32 : DT_F32;
 
     const void* in = img;
-    int64_t in_pitch = img_pitch;
+    int64_t in_pitch = img_pitch, in_bstride = bt.N > 1 ? bt.img_bstride : 0;
     int in_dt = img_dtype;
     for (int j = 1; j <= J; ++j) {
         const int h = L.h[j - 1], w = L.w[j - 1];
-        FwdArgs a = level_args(in, in_pitch, h, w, status);
+        FwdArgs a = level_args(in, in_pitch, in_bstride, h, w, bt.N, status);
         const dwt2_band &bhl = band_of(L, j, 0), &blh = band_of(L, j, 1), &bhh = band_of(L, j, 2);
-        a.hl = {cb + bhl.offset_bytes, bhl.pitch_bytes};
-        a.lh = {cb + blh.offset_bytes, blh.pitch_bytes};
-        a.hh = {cb + bhh.offset_bytes, bhh.pitch_bytes};
-        if (j == J) a.ll = {cb + L.band[0].offset_bytes, L.band[0].pitch_bytes};
-        else a.ll = {wb + wp.off[(j - 1) % 2], wp.pitch[(j - 1) % 2]};
+        a.hl = {cb + bhl.offset_bytes, bhl.pitch_bytes, cbs};
+        a.lh = {cb + blh.offset_bytes, blh.pitch_bytes, cbs};
+        a.hh = {cb + bhh.offset_bytes, bhh.pitch_bytes, cbs};
+        if (j == J) a.ll = {cb + L.band[0].offset_bytes, L.band[0].pitch_bytes, cbs};
+        else a.ll = {wb + wp.off[(j - 1) % 2], wp.pitch[(j - 1) % 2], region};
 
         cudaError_t e;
         if (scheme == DWT2_SCHEME_SEP_TWOPASS) {
             // row pass into the full-size plane, then the column pass into the bands
             CUtensorMap tm;
-            MapResult mr = make_map(&tm, in, in_pitch, h, w, in_dt, kBoxW);
+            MapResult mr = make_map(&tm, in, in_pitch, 0, h, w, 1, in_dt, kBoxW);
             if (mr == MAP_ERROR) return DWT2_EINTERNAL;
             bool tma = mr == MAP_OK;
             FwdArgs r = a;
-            r.ll = {wb + wp.off[2], wp.pitch[2]};
+            r.ll = {wb + wp.off[2], wp.pitch[2], 0};
             e = launch_fwd(wavelet, MODE_ROWS, in_dt, band_dtype, tma, tm, r, st);
             if (e != cudaSuccess) return cuda_fail(e, "row pass");
-            FwdArgs c = level_args(wb + wp.off[2], wp.pitch[2], h, w, status);
+            FwdArgs c = level_args(wb + wp.off[2], wp.pitch[2], 0, h, w, 1, status);
             c.ll = a.ll;
             c.hl = a.hl;
             c.lh = a.lh;
             c.hh = a.hh;
-            mr = make_map(&tm, wb + wp.off[2], wp.pitch[2], h, w, ll_dt, kBoxW);
+            mr = make_map(&tm, wb + wp.off[2], wp.pitch[2], 0, h, w, 1, ll_dt, kBoxW);
             if (mr == MAP_ERROR) return DWT2_EINTERNAL;
             tma = mr == MAP_OK;
             e = launch_fwd(wavelet, MODE_COLS, ll_dt, band_dtype, tma, tm, c, st);
             if (e != cudaSuccess) return cuda_fail(e, "column pass");
         } else {
             CUtensorMap tm;
-            const MapResult mr = make_map(&tm, in, in_pitch, h, w, in_dt, kBoxW);
+            const MapResult mr = make_map(&tm, in, in_pitch, in_bstride, h, w, bt.N, in_dt, kBoxW);
             if (mr == MAP_ERROR) return DWT2_EINTERNAL;
             const bool tma = mr == MAP_OK;
             const int mode = scheme == DWT2_SCHEME_NONSEP ? MODE_NONSEP : MODE_SEP;
@@ -313,6 +345,7 @@ static int forward_impl(const void* img, int64_t img_pitch, int H, int W, int im
         }
         in = a.ll.ptr;
         in_pitch = a.ll.pitch;
+        in_bstride = a.ll.bstride;
         in_dt = ll_dt;
     }
     return DWT2_OK;
@@ -322,7 +355,8 @@ static int forward_impl(const void* img, int64_t img_pitch, int H, int W, int im
 // out), level by level J..1 with the inverse kernel's data flow.
 static int inverse_impl(const void* coeffs, void* img, int64_t img_pitch, int H, int W,
                         int img_dtype, void* ws, size_t ws_bytes, int wavelet, int J,
-                        int band_dtype, cudaStream_t st, bool adjoint = false) {
+                        int band_dtype, cudaStream_t st, bool adjoint = false,
+                        Batch bt = Batch{1, 0, 0}) {
     int rc = check_types(wavelet, img_dtype, band_dtype);
     if (rc) return rc;
     if (adjoint && (wavelet == WV_CDF53_INT || img_dtype != DT_F32 || band_dtype != DT_F32))
@@ -330,9 +364,13 @@ static int inverse_impl(const void* coeffs, void* img, int64_t img_pitch, int H,
     Layout L;
     if ((rc = make_layout(H, W, J, band_dtype, &L))) return rc;
     if ((rc = check_image(img, img_pitch, W, img_dtype))) return rc;
+    if ((rc = check_batch(bt, H, img_pitch, img_dtype, L))) return rc;
     if (!coeffs || !ws || !aligned(coeffs, 16) || !aligned(ws, 16)) return DWT2_EINVAL;
     const WsPlan wp = plan_workspace(H, W, J, wavelet, DWT2_SCHEME_NONSEP);
-    if (int64_t(ws_bytes) < wp.bytes) return DWT2_ENOMEM;
+    const int64_t region = ws_region(wp);
+    if (int64_t(ws_bytes) < kHeader + bt.N * region) return DWT2_ENOMEM;
+    const int64_t cbs = bt.N > 1 ? bt.coeff_bstride : 0;
+    const int64_t ibs = bt.N > 1 ? bt.img_bstride : 0;
 
     const char* cb = static_cast<const char*>(coeffs);
     char* wb = static_cast<char*>(ws);
@@ -350,48 +388,46 @@ static int inverse_impl(const void* coeffs, void* img, int64_t img_pitch, int H,
         a.nec = (w + 1) / 2;
         a.ndc = w / 2;
         a.status = status;
-        const void* llp;
-        int64_t llpitch;
+        a.nbatch = bt.N;
         if (j == J) {
-            llp = cb + L.band[0].offset_bytes;
-            llpitch = L.band[0].pitch_bytes;
+            a.band[0] = cb + L.band[0].offset_bytes;
+            a.band_pitch[0] = L.band[0].pitch_bytes;
+            a.band_bstride[0] = cbs;
         } else {
-            llp = wb + wp.off[(j - 1) % 2];
-            llpitch = wp.pitch[(j - 1) % 2];
+            a.band[0] = wb + wp.off[(j - 1) % 2];
+            a.band_pitch[0] = wp.pitch[(j - 1) % 2];
+            a.band_bstride[0] = region;
         }
-        const dwt2_band &bhl = band_of(L, j, 0), &blh = band_of(L, j, 1), &bhh = band_of(L, j, 2);
-        a.band[0] = llp;
-        a.band_pitch[0] = llpitch;
-        a.band[1] = cb + bhl.offset_bytes;
-        a.band_pitch[1] = bhl.pitch_bytes;
-        a.band[2] = cb + blh.offset_bytes;
-        a.band_pitch[2] = blh.pitch_bytes;
-        a.band[3] = cb + bhh.offset_bytes;
-        a.band_pitch[3] = bhh.pitch_bytes;
+        for (int k = 0; k < 3; ++k) {
+            const dwt2_band& b = band_of(L, j, k);
+            a.band[1 + k] = cb + b.offset_bytes;
+            a.band_pitch[1 + k] = b.pitch_bytes;
+            a.band_bstride[1 + k] = cbs;
+        }
         int out_dt;
         if (j == 1) {
-            a.out = {img, img_pitch};
+            a.out = {img, img_pitch, ibs};
             out_dt = img_dtype;
         } else {
-            a.out = {wb + wp.off[(j - 2) % 2], wp.pitch[(j - 2) % 2]};
+            a.out = {wb + wp.off[(j - 2) % 2], wp.pitch[(j - 2) % 2], region};
             out_dt = ll_dt;
         }
         const size_t vbytes = 4 * esize(out_dt);
-        a.out_vec = aligned(a.out.ptr, vbytes) && a.out.pitch % int64_t(vbytes) == 0;
+        a.out_vec = aligned(a.out.ptr, vbytes) && a.out.pitch % int64_t(vbytes) == 0 &&
+                    a.out.bstride % int64_t(vbytes) == 0;
 
         // TMA needs all four band planes non-empty (h, w >= 2); the plain-load path covers the
-        // rest (and planes whose base or pitch TMA cannot address).
+        // rest (and planes whose base, pitch or batch stride TMA cannot address).
         CUtensorMap tm[4];
         bool tma = h >= 2 && w >= 2;
         if (tma) {
-            const MapResult r[4] = {
-                make_map(&tm[0], a.band[0], a.band_pitch[0], a.ner, a.nec, ll_dt, kBoxW),
-                make_map(&tm[1], a.band[1], a.band_pitch[1], a.ner, a.ndc, band_dtype, kBoxW),
-                make_map(&tm[2], a.band[2], a.band_pitch[2], a.ndr, a.nec, band_dtype, kBoxW),
-                make_map(&tm[3], a.band[3], a.band_pitch[3], a.ndr, a.ndc, band_dtype, kBoxW)};
+            const int dims[4][2] = {{a.ner, a.nec}, {a.ner, a.ndc}, {a.ndr, a.nec}, {a.ndr, a.ndc}};
             for (int k = 0; k < 4; ++k) {
-                if (r[k] == MAP_ERROR) return DWT2_EINTERNAL;
-                if (r[k] != MAP_OK) tma = false;
+                const MapResult r = make_map(&tm[k], a.band[k], a.band_pitch[k], a.band_bstride[k],
+                                             dims[k][0], dims[k][1], bt.N, k == 0 ? ll_dt : band_dtype,
+                                             kBoxW);
+                if (r == MAP_ERROR) return DWT2_EINTERNAL;
+                if (r != MAP_OK) tma = false;
             }
         }
         if (!tma) std::memset(tm, 0, sizeof(tm));
@@ -434,8 +470,8 @@ int plan_layout(int H, int W, int J, int band_dtype, dwt2_band* bands, size_t* b
 int plan_prepare_fwd_unit(FwdUnit* u, const void* in, int64_t in_pitch, int h, int w, int in_dt,
                           int tb, int* status) {
     (void)tb;
-    u->a = level_args(in, in_pitch, h, w, status);
-    const MapResult mr = make_map(&u->tm, in, in_pitch, h, w, in_dt, kBoxW);
+    u->a = level_args(in, in_pitch, 0, h, w, 1, status);
+    const MapResult mr = make_map(&u->tm, in, in_pitch, 0, h, w, 1, in_dt, kBoxW);
     if (mr == MAP_ERROR) return DWT2_EINTERNAL;
     u->a.tma = mr == MAP_OK ? 1 : 0;
     return DWT2_OK;
@@ -453,19 +489,20 @@ int plan_prepare_inv_unit(InvUnit* u, const void* const bands[4], const int64_t 
     a.nec = (w + 1) / 2;
     a.ndc = w / 2;
     a.status = status;
+    a.nbatch = 1;
     for (int k = 0; k < 4; ++k) {
         a.band[k] = bands[k];
         a.band_pitch[k] = pitches[k];
     }
-    a.out = {out, out_pitch};
+    a.out = {out, out_pitch, 0};
     const size_t vbytes = 4 * esize(out_dt);
     a.out_vec = aligned(out, vbytes) && out_pitch % int64_t(vbytes) == 0;
     bool tma = h >= 2 && w >= 2;
     if (tma) {
         const int dims[4][2] = {{a.ner, a.nec}, {a.ner, a.ndc}, {a.ndr, a.nec}, {a.ndr, a.ndc}};
         for (int k = 0; k < 4; ++k) {
-            const MapResult r = make_map(&u->tm[k], bands[k], pitches[k], dims[k][0], dims[k][1],
-                                         k == 0 ? tl : tb, kBoxW);
+            const MapResult r = make_map(&u->tm[k], bands[k], pitches[k], 0, dims[k][0], dims[k][1],
+                                         1, k == 0 ? tl : tb, kBoxW);
             if (r == MAP_ERROR) return DWT2_EINTERNAL;
             if (r != MAP_OK) tma = false;
         }
@@ -577,4 +614,50 @@ DWT2_EXPORT int dwt2_inverse_adjoint(const void* g_img, int64_t g_img_pitch_byte
     return forward_impl(g_img, g_img_pitch_bytes, H, W, img_dtype, g_coeffs, workspace, ws_bytes,
                         wavelet, levels, band_dtype, DWT2_SCHEME_NONSEP,
                         static_cast<cudaStream_t>(stream), true);
+}
+
+DWT2_EXPORT size_t dwt2_workspace_bytes_batch(int N, int H, int W, int levels, int wavelet,
+                                              int band_dtype) {
+    Layout L;
+    if (N < 1 || make_layout(H, W, levels, band_dtype, &L) || wavelet < 0 || wavelet > 2) return 0;
+    return size_t(kHeader + N * ws_region(plan_workspace(H, W, levels, wavelet, DWT2_SCHEME_NONSEP)));
+}
+
+DWT2_EXPORT int dwt2_forward_batch(const void* img, int64_t img_pitch_bytes, int64_t img_batch_bytes,
+                                   int N, int H, int W, int img_dtype, void* coeffs,
+                                   int64_t coeff_batch_bytes, void* workspace, size_t ws_bytes,
+                                   int wavelet, int levels, int band_dtype, void* stream) {
+    return forward_impl(img, img_pitch_bytes, H, W, img_dtype, coeffs, workspace, ws_bytes, wavelet,
+                        levels, band_dtype, DWT2_SCHEME_NONSEP, static_cast<cudaStream_t>(stream),
+                        false, Batch{N, img_batch_bytes, coeff_batch_bytes});
+}
+
+DWT2_EXPORT int dwt2_inverse_batch(const void* coeffs, int64_t coeff_batch_bytes, void* img,
+                                   int64_t img_pitch_bytes, int64_t img_batch_bytes, int N, int H,
+                                   int W, int img_dtype, void* workspace, size_t ws_bytes,
+                                   int wavelet, int levels, int band_dtype, void* stream) {
+    return inverse_impl(coeffs, img, img_pitch_bytes, H, W, img_dtype, workspace, ws_bytes, wavelet,
+                        levels, band_dtype, static_cast<cudaStream_t>(stream), false,
+                        Batch{N, img_batch_bytes, coeff_batch_bytes});
+}
+
+DWT2_EXPORT int dwt2_forward_adjoint_batch(const void* g_coeffs, int64_t coeff_batch_bytes,
+                                           void* g_img, int64_t g_img_pitch_bytes,
+                                           int64_t g_img_batch_bytes, int N, int H, int W,
+                                           int img_dtype, void* workspace, size_t ws_bytes,
+                                           int wavelet, int levels, int band_dtype, void* stream) {
+    return inverse_impl(g_coeffs, g_img, g_img_pitch_bytes, H, W, img_dtype, workspace, ws_bytes,
+                        wavelet, levels, band_dtype, static_cast<cudaStream_t>(stream), true,
+                        Batch{N, g_img_batch_bytes, coeff_batch_bytes});
+}
+
+DWT2_EXPORT int dwt2_inverse_adjoint_batch(const void* g_img, int64_t g_img_pitch_bytes,
+                                           int64_t g_img_batch_bytes, int N, int H, int W,
+                                           int img_dtype, void* g_coeffs, int64_t coeff_batch_bytes,
+                                           void* workspace, size_t ws_bytes, int wavelet,
+                                           int levels, int band_dtype, void* stream) {
+    return forward_impl(g_img, g_img_pitch_bytes, H, W, img_dtype, g_coeffs, workspace, ws_bytes,
+                        wavelet, levels, band_dtype, DWT2_SCHEME_NONSEP,
+                        static_cast<cudaStream_t>(stream), true,
+                        Batch{N, g_img_batch_bytes, coeff_batch_bytes});
 }

@@ -177,7 +177,7 @@ __global__ void __launch_bounds__(kThreads, min_ctas<WV>())
                 }
                 if (lane == 0) ring.meta[s] = t;
                 fwd_produce_row<TI>(U.a, &U.tm, kAdj, tl.qfirst + i, xs,
-                                    reinterpret_cast<TI*>(ring.stage(s)), &ring.full[s], lane);
+                                    reinterpret_cast<TI*>(ring.stage(s)), &ring.full[s], lane, 0);
             }
             if (!alive) break;
         }
@@ -228,7 +228,7 @@ __global__ void __launch_bounds__(kThreads, min_ctas<WV>())
                 pipe.push(row);
             const int qo = tl.qfirst + i - Pipe::kLag;
             if (qo >= tl.n0 && qo < tl.n1 && store_lane)
-                fwd_store_row<MODE_NONSEP, TB, TL>(U->a, row, qo, m0);
+                fwd_store_row<MODE_NONSEP, TB, TL>(U->a, row, qo, m0, 0);
         } else if (lane == 0) {
             mbar_arrive(&ring.empty[s]);
         }
@@ -275,7 +275,7 @@ __global__ void __launch_bounds__(kThreads, min_ctas<WV>())
                 }
                 if (lane == 0) ring.meta[s] = t;
                 inv_produce_row<TL, TB>(U.a, maps, ADJ, tl.qfirst + i, xb, ring.stage(s),
-                                        &ring.full[s], lane);
+                                        &ring.full[s], lane, 0);
             }
             if (!alive) break;
         }
@@ -324,7 +324,7 @@ __global__ void __launch_bounds__(kThreads, min_ctas<WV>())
             else
                 pipe.push(row);
             const int qo = tl.qfirst + i - Pipe::kLag;
-            if (qo >= tl.n0 && qo < tl.n1 && store_lane) inv_store_row<TO>(U->a, row, qo, m0);
+            if (qo >= tl.n0 && qo < tl.n1 && store_lane) inv_store_row<TO>(U->a, row, qo, m0, 0);
         } else if (lane == 0) {
             mbar_arrive(&ring.empty[s]);
         }

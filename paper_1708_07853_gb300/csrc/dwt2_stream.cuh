@@ -13,6 +13,8 @@
 // source column.  The lifting then runs on the symmetric extension with no boundary rule.
 #pragma once
 
+#include <algorithm>
+
 #include "dwt2_lifting.cuh"
 
 namespace dwt2 {
@@ -46,14 +48,18 @@ constexpr int kBRow = kBBoxes * kBoxW;
 static_assert(kSRow >= kXL + 2 * kCtaQ + 2 * kHQ, "forward stage row too short");
 static_assert(kBRow >= kXLB + kCtaQ + kHQ, "inverse stage row too short");
 
+// A plane (or a batch of equally shaped planes): image z, row r starts at
+// ptr + z * bstride + r * pitch (bytes).
 struct PlaneOut {
     void* ptr;
-    int64_t pitch;  // bytes
+    int64_t pitch;
+    int64_t bstride;
 };
 
 struct FwdArgs {
     const void* in;     // input plane (used by the plain-load path)
     int64_t in_pitch;   // bytes
+    int64_t in_bstride; // bytes between the images of a batch
     int H, W;           // input plane size in pixels
     int ner, ndr, nec, ndc;  // even/odd row and column counts = band sizes
     PlaneOut ll, hl, lh, hh;  // band planes (ll is the interleaved output plane in MODE_ROWS)
@@ -61,11 +67,13 @@ struct FwdArgs {
     int* status;        // workspace status word
     Scale4 scale;       // MODE_ADJ_INV: the reciprocal band scales applied last
     int tma;            // 1: load the input plane with TMA (16-byte aligned base and pitch)
+    int nbatch;         // images in the batch (grid z)
 };
 
 struct InvArgs {
     const void* band[4];  // LL, HL, LH, HH (used by the plain-load path)
     int64_t band_pitch[4];
+    int64_t band_bstride[4];
     int H, W;             // output plane size in pixels
     int ner, ndr, nec, ndc;
     PlaneOut out;         // output plane
@@ -74,11 +82,13 @@ struct InvArgs {
     int* status;
     Scale4 scale;         // adjoint: the band scales applied first
     int tma;              // 1: load the band planes with TMA
+    int nbatch;           // images in the batch (grid z)
 };
 
 template <typename T>
-__device__ __forceinline__ T* row_ptr(const PlaneOut& p, int r) {
-    return reinterpret_cast<T*>(static_cast<char*>(p.ptr) + static_cast<int64_t>(r) * p.pitch);
+__device__ __forceinline__ T* row_ptr(const PlaneOut& p, int r, int z) {
+    return reinterpret_cast<T*>(static_cast<char*>(p.ptr) + int64_t(z) * p.bstride +
+                                static_cast<int64_t>(r) * p.pitch);
 }
 
 // Stores N consecutive values of an output row starting at column c0 (an aligned vector store
@@ -124,7 +134,8 @@ __device__ __forceinline__ uint8_t* align128(uint8_t* p) {
 // adjoint of the inverse.
 template <typename TI>
 __device__ __forceinline__ void fwd_produce_row(const FwdArgs& a, const CUtensorMap* tm, bool adj,
-                                                int q, int xs, TI* dst, uint64_t* full, int lane) {
+                                                int q, int xs, TI* dst, uint64_t* full, int lane,
+                                                int z) {
     const int r0 = adj ? 2 * q : refl(2 * q, a.H);
     const int r1 = adj ? 2 * q + 1 : refl(2 * q + 1, a.H);
     if (a.tma) {
@@ -132,17 +143,16 @@ __device__ __forceinline__ void fwd_produce_row(const FwdArgs& a, const CUtensor
             mbar_arrive_expect_tx(full, 2 * kSRow * sizeof(TI));
 #pragma unroll
             for (int b = 0; b < kBoxes; ++b) {
-                tma_load_2d(dst + b * kBoxW, tm, full, xs + b * kBoxW, r0);
-                tma_load_2d(dst + kSRow + b * kBoxW, tm, full, xs + b * kBoxW, r1);
+                tma_load_3d(dst + b * kBoxW, tm, full, xs + b * kBoxW, r0, z);
+                tma_load_3d(dst + kSRow + b * kBoxW, tm, full, xs + b * kBoxW, r1, z);
             }
         }
     } else {
         // plain loads (unaligned planes); .cg: the plane may have been written by other SMs
         const bool ok0 = r0 >= 0 && r0 < a.H, ok1 = r1 >= 0 && r1 < a.H;
-        const TI* row0 = reinterpret_cast<const TI*>(static_cast<const char*>(a.in) +
-                                                     int64_t(ok0 ? r0 : 0) * a.in_pitch);
-        const TI* row1 = reinterpret_cast<const TI*>(static_cast<const char*>(a.in) +
-                                                     int64_t(ok1 ? r1 : 0) * a.in_pitch);
+        const char* base = static_cast<const char*>(a.in) + int64_t(z) * a.in_bstride;
+        const TI* row0 = reinterpret_cast<const TI*>(base + int64_t(ok0 ? r0 : 0) * a.in_pitch);
+        const TI* row1 = reinterpret_cast<const TI*>(base + int64_t(ok1 ? r1 : 0) * a.in_pitch);
         for (int k = lane; k < kSRow; k += 32) {
             const int c = xs + k;
             const bool in = c >= 0 && c < a.W;
@@ -197,7 +207,8 @@ __device__ __forceinline__ void fwd_lane_row(const TI* stage, const FwdCols& col
 
 // Stores a finished quad row qo: the four band rows, or (MODE_ROWS) two interleaved pixel rows.
 template <int MODE, typename TB, typename TL, typename C>
-__device__ __forceinline__ void fwd_store_row(const FwdArgs& a, const QRow<C>& row, int qo, int m0) {
+__device__ __forceinline__ void fwd_store_row(const FwdArgs& a, const QRow<C>& row, int qo, int m0,
+                                              int z) {
     const int col0 = 2 * m0;
     if constexpr (MODE == MODE_ROWS) {
         C va[2 * kQ], vc[2 * kQ];
@@ -208,15 +219,15 @@ __device__ __forceinline__ void fwd_store_row(const FwdArgs& a, const QRow<C>& r
             vc[2 * q] = row.c[q];
             vc[2 * q + 1] = row.e[q];
         }
-        putN<2 * kQ>(row_ptr<TL>(a.ll, 2 * qo) + col0, va, col0, a.W, true);
+        putN<2 * kQ>(row_ptr<TL>(a.ll, 2 * qo, z) + col0, va, col0, a.W, true);
         if (2 * qo + 1 < a.H)
-            putN<2 * kQ>(row_ptr<TL>(a.ll, 2 * qo + 1) + col0, vc, col0, a.W, true);
+            putN<2 * kQ>(row_ptr<TL>(a.ll, 2 * qo + 1, z) + col0, vc, col0, a.W, true);
     } else {
-        putN<kQ>(row_ptr<TL>(a.ll, qo) + m0, row.a, m0, a.nec, true);
-        putN<kQ>(row_ptr<TB>(a.hl, qo) + m0, row.b, m0, a.ndc, true);
+        putN<kQ>(row_ptr<TL>(a.ll, qo, z) + m0, row.a, m0, a.nec, true);
+        putN<kQ>(row_ptr<TB>(a.hl, qo, z) + m0, row.b, m0, a.ndc, true);
         if (qo < a.ndr) {
-            putN<kQ>(row_ptr<TB>(a.lh, qo) + m0, row.c, m0, a.nec, true);
-            putN<kQ>(row_ptr<TB>(a.hh, qo) + m0, row.e, m0, a.ndc, true);
+            putN<kQ>(row_ptr<TB>(a.lh, qo, z) + m0, row.c, m0, a.nec, true);
+            putN<kQ>(row_ptr<TB>(a.hh, qo, z) + m0, row.e, m0, a.ndc, true);
         }
     }
 }
@@ -227,7 +238,7 @@ __device__ __forceinline__ void fwd_store_row(const FwdArgs& a, const QRow<C>& r
 template <typename TL, typename TB>
 __device__ __forceinline__ void inv_produce_row(const InvArgs& a, const CUtensorMap* const* tm,
                                                 bool adj, int q, int xb, uint8_t* stage,
-                                                uint64_t* full, int lane) {
+                                                uint64_t* full, int lane, int z) {
     constexpr size_t kStageBytes = size_t(kBRow) * (sizeof(TL) + 3 * sizeof(TB));
     TL* sll = reinterpret_cast<TL*>(stage);
     TB* sb = reinterpret_cast<TB*>(stage + kBRow * sizeof(TL));
@@ -239,10 +250,10 @@ __device__ __forceinline__ void inv_produce_row(const InvArgs& a, const CUtensor
 #pragma unroll
             for (int b = 0; b < kBBoxes; ++b) {
                 const int x = xb + b * kBoxW;
-                tma_load_2d(sll + b * kBoxW, tm[0], full, x, re);
-                tma_load_2d(sb + b * kBoxW, tm[1], full, x, re);
-                tma_load_2d(sb + kBRow + b * kBoxW, tm[2], full, x, ro);
-                tma_load_2d(sb + 2 * kBRow + b * kBoxW, tm[3], full, x, ro);
+                tma_load_3d(sll + b * kBoxW, tm[0], full, x, re, z);
+                tma_load_3d(sb + b * kBoxW, tm[1], full, x, re, z);
+                tma_load_3d(sb + kBRow + b * kBoxW, tm[2], full, x, ro, z);
+                tma_load_3d(sb + 2 * kBRow + b * kBoxW, tm[3], full, x, ro, z);
             }
         }
     } else {
@@ -252,7 +263,7 @@ __device__ __forceinline__ void inv_produce_row(const InvArgs& a, const CUtensor
 #pragma unroll
         for (int b = 0; b < 4; ++b) {
             const bool row_ok = rows[b] >= 0 && rows[b] < heights[b];
-            const char* src = static_cast<const char*>(a.band[b]) +
+            const char* src = static_cast<const char*>(a.band[b]) + int64_t(z) * a.band_bstride[b] +
                               int64_t(row_ok ? rows[b] : 0) * a.band_pitch[b];
             for (int k = lane; k < kBRow; k += 32) {
                 const int c = xb + k;
@@ -317,7 +328,8 @@ __device__ __forceinline__ void inv_lane_row(const uint8_t* stage, const InvCols
 
 // Stores a reconstructed quad row qo as pixel rows 2qo and 2qo + 1 of the output plane.
 template <typename TO, typename C>
-__device__ __forceinline__ void inv_store_row(const InvArgs& a, const QRow<C>& row, int qo, int m0) {
+__device__ __forceinline__ void inv_store_row(const InvArgs& a, const QRow<C>& row, int qo, int m0,
+                                              int z) {
     const int c0 = 2 * m0;
     C va[2 * kQ], vc[2 * kQ];
 #pragma unroll
@@ -327,9 +339,9 @@ __device__ __forceinline__ void inv_store_row(const InvArgs& a, const QRow<C>& r
         vc[2 * q] = row.c[q];
         vc[2 * q + 1] = row.e[q];
     }
-    putN<2 * kQ>(row_ptr<TO>(a.out, 2 * qo) + c0, va, c0, a.W, a.out_vec != 0);
+    putN<2 * kQ>(row_ptr<TO>(a.out, 2 * qo, z) + c0, va, c0, a.W, a.out_vec != 0);
     if (2 * qo + 1 < a.H)
-        putN<2 * kQ>(row_ptr<TO>(a.out, 2 * qo + 1) + c0, vc, c0, a.W, a.out_vec != 0);
+        putN<2 * kQ>(row_ptr<TO>(a.out, 2 * qo + 1, z) + c0, vc, c0, a.W, a.out_vec != 0);
 }
 
 // Shared-memory ring: kStages stages, then the full / empty barriers, the abort flag and the
@@ -391,6 +403,7 @@ __global__ void __launch_bounds__(kThreads, min_ctas<WV>())
     const Ring ring = make_ring(smem_raw, size_t(2) * kSRow * sizeof(TI));
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int z = blockIdx.z;  // image of a batch
     const int qx0 = blockIdx.x * kCtaQ;
     const int n0 = blockIdx.y * args.rpc;
     const int n1 = min(n0 + args.rpc, args.ner);
@@ -415,7 +428,7 @@ __global__ void __launch_bounds__(kThreads, min_ctas<WV>())
                 if (!__all_sync(kFull, ok)) break;
             }
             fwd_produce_row<TI>(args, &tmap, kAdj, qfirst + i, xs,
-                                reinterpret_cast<TI*>(ring.stage(s)), &ring.full[s], lane);
+                                reinterpret_cast<TI*>(ring.stage(s)), &ring.full[s], lane, z);
             issued = i + 1;
         }
         if (args.tma && lane == 0) drain_ring(ring, issued, args.status);
@@ -453,7 +466,7 @@ __global__ void __launch_bounds__(kThreads, min_ctas<WV>())
         else
             pipe.push(row);
         const int qo = qfirst + i - Pipe::kLag;
-        if (qo >= n0 && qo < n1 && store_lane) fwd_store_row<MODE, TB, TL>(args, row, qo, m0);
+        if (qo >= n0 && qo < n1 && store_lane) fwd_store_row<MODE, TB, TL>(args, row, qo, m0, z);
     }
 }
 
@@ -471,6 +484,7 @@ __global__ void __launch_bounds__(kThreads, min_ctas<WV>())
     const Ring ring = make_ring(smem_raw, kStageBytes);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int z = blockIdx.z;  // image of a batch
     const int qx0 = blockIdx.x * kCtaQ;
     const int n0 = blockIdx.y * args.rpc;
     const int n1 = min(n0 + args.rpc, args.ner);
@@ -500,7 +514,7 @@ __global__ void __launch_bounds__(kThreads, min_ctas<WV>())
                 if (!__all_sync(kFull, ok)) break;
             }
             inv_produce_row<TL, TB>(args, maps, ADJ, qfirst + i, xb, ring.stage(s), &ring.full[s],
-                                    lane);
+                                    lane, z);
             issued = i + 1;
         }
         if (args.tma && lane == 0) drain_ring(ring, issued, args.status);
@@ -537,7 +551,7 @@ __global__ void __launch_bounds__(kThreads, min_ctas<WV>())
         else
             pipe.push(row);
         const int qo = qfirst + i - Pipe::kLag;
-        if (qo >= n0 && qo < n1 && store_lane) inv_store_row<TO>(args, row, qo, m0);
+        if (qo >= n0 && qo < n1 && store_lane) inv_store_row<TO>(args, row, qo, m0, z);
     }
 }
 
@@ -553,9 +567,10 @@ struct LaunchGeom {
 // least 16 quad rows each, so the 4 halo rows of a CTA stay a small overhead on HBM reads.
 // Small planes (a few MB, served from L2 after the previous level wrote them): as many CTAs as
 // fit, down to 4 rows each, because there the per-row latency of a CTA, not bytes, sets the time.
-inline LaunchGeom pick_geometry(int ner, int nec, int64_t plane_bytes, int sms, int ctas_per_sm) {
+inline LaunchGeom pick_geometry(int ner, int nec, int64_t plane_bytes, int sms, int ctas_per_sm,
+                                int nbatch) {
     const int strips = (nec + kCtaQ - 1) / kCtaQ;
-    const int target = sms * (ctas_per_sm > 0 ? ctas_per_sm : 1);
+    const int target = std::max(1, sms * (ctas_per_sm > 0 ? ctas_per_sm : 1) / std::max(1, nbatch));
     const int min_rows = plane_bytes < (int64_t(24) << 20) ? 4 : 16;
     const int rb_max = (ner + min_rows - 1) / min_rows;
     int rb = target / strips;
@@ -565,7 +580,7 @@ inline LaunchGeom pick_geometry(int ner, int nec, int64_t plane_bytes, int sms, 
     if (rpc < 1) rpc = 1;
     rb = (ner + rpc - 1) / rpc;
     LaunchGeom g;
-    g.grid = dim3(strips, rb, 1);
+    g.grid = dim3(strips, rb, std::max(1, nbatch));
     g.rpc = rpc;
     return g;
 }
@@ -609,7 +624,7 @@ cudaError_t launch_forward_t(const CUtensorMap& tm, FwdArgs a, cudaStream_t st) 
     constexpr size_t smem = fwd_smem_bytes<TI>();
     static const int occ = configure(k, smem);
     const LaunchGeom g = pick_geometry(a.ner, a.nec, int64_t(a.H) * a.W * int64_t(sizeof(TI)),
-                                       device_sm_count(), occ);
+                                       device_sm_count(), occ, a.nbatch);
     a.rpc = g.rpc;
     return launch_pdl(k, g.grid, smem, st, tm, a);
 }
@@ -620,7 +635,7 @@ cudaError_t launch_inverse_t(const CUtensorMap* tm, InvArgs a, cudaStream_t st) 
     constexpr size_t smem = inv_smem_bytes<TL, TB>();
     static const int occ = configure(k, smem);
     const LaunchGeom g = pick_geometry(a.ner, a.nec, int64_t(a.H) * a.W * int64_t(sizeof(TL)),
-                                       device_sm_count(), occ);
+                                       device_sm_count(), occ, a.nbatch);
     a.rpc = g.rpc;
     return launch_pdl(k, g.grid, smem, st, tm[0], tm[1], tm[2], tm[3], a);
 }

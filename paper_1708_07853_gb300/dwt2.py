@@ -31,7 +31,8 @@ EXPORTS = ["dwt2_status_string", "dwt2_last_error", "dwt2_max_levels", "dwt2_lay
            "dwt2_check_status", "dwt2_forward", "dwt2_forward_scheme", "dwt2_inverse",
            "dwt2_forward_static", "dwt2_forward_adjoint", "dwt2_inverse_adjoint",
            "dwt2_plan_workspace_bytes", "dwt2_plan_create", "dwt2_plan_execute", "dwt2_plan_info",
-           "dwt2_plan_destroy"]
+           "dwt2_plan_destroy", "dwt2_workspace_bytes_batch", "dwt2_forward_batch",
+           "dwt2_inverse_batch", "dwt2_forward_adjoint_batch", "dwt2_inverse_adjoint_batch"]
 DIRECTIONS = {"forward": 0, "inverse": 1, "forward_adjoint": 2, "inverse_adjoint": 3}
 
 
@@ -91,10 +92,20 @@ def _lib():
         lib.dwt2_plan_info.argtypes = [vp, ctypes.POINTER(i), ctypes.POINTER(i), ctypes.POINTER(i)]
         lib.dwt2_plan_destroy.argtypes = [vp]
         lib.dwt2_inverse_adjoint.argtypes = [vp, i64, i, i, i, vp, vp, sz, i, i, i, vp]
+        lib.dwt2_workspace_bytes_batch.restype = sz
+        lib.dwt2_workspace_bytes_batch.argtypes = [i, i, i, i, i, i]
+        lib.dwt2_forward_batch.argtypes = [vp, i64, i64, i, i, i, i, vp, i64, vp, sz, i, i, i, vp]
+        lib.dwt2_inverse_batch.argtypes = [vp, i64, vp, i64, i64, i, i, i, i, vp, sz, i, i, i, vp]
+        lib.dwt2_forward_adjoint_batch.argtypes = [vp, i64, vp, i64, i64, i, i, i, i, vp, sz, i, i,
+                                                   i, vp]
+        lib.dwt2_inverse_adjoint_batch.argtypes = [vp, i64, i64, i, i, i, i, vp, i64, vp, sz, i, i,
+                                                   i, vp]
         for f in ("dwt2_max_levels", "dwt2_layout", "dwt2_workspace_init", "dwt2_check_status",
                   "dwt2_forward", "dwt2_forward_scheme", "dwt2_inverse", "dwt2_forward_static",
                   "dwt2_forward_adjoint", "dwt2_inverse_adjoint", "dwt2_plan_create",
-                  "dwt2_plan_execute", "dwt2_plan_info", "dwt2_plan_destroy"):
+                  "dwt2_plan_execute", "dwt2_plan_info", "dwt2_plan_destroy",
+                  "dwt2_forward_batch", "dwt2_inverse_batch", "dwt2_forward_adjoint_batch",
+                  "dwt2_inverse_adjoint_batch"):
             getattr(lib, f).restype = i
         _LIB = lib
     return _LIB
@@ -276,6 +287,128 @@ def inverse_adjoint(x: torch.Tensor, wavelet="cdf97", levels: int = 1, out: Coef
         _stream_ptr(stream))
     if rc:
         raise Dwt2Error(rc, "dwt2_inverse_adjoint")
+    return out
+
+
+
+# ------------------------------------------------------------------ uniform batches (N x H x W)
+def workspace_bytes_batch(N: int, H: int, W: int, levels: int, wavelet, band_dtype: int) -> int:
+    n = _lib().dwt2_workspace_bytes_batch(N, H, W, levels, _wid(wavelet), band_dtype)
+    if n == 0:
+        raise Dwt2Error(1, f"dwt2_workspace_bytes_batch({N}, {H}, {W}, {levels})")
+    return n
+
+
+def _check_batch_img(x: torch.Tensor):
+    if not x.is_cuda or x.dim() != 3 or x.stride(2) != 1:
+        raise ValueError("batched images must be CUDA tensors (N, H, W) with unit column stride")
+    if x.dtype not in TORCH_DT:
+        raise ValueError(f"unsupported image dtype {x.dtype}")
+
+
+def _check_batch_coeffs(c: torch.Tensor, N: int, nbytes: int):
+    if not c.is_cuda or c.dim() != 2 or c.shape[0] != N or c.stride(1) != 1:
+        raise ValueError("batched coefficients must be CUDA tensors (N, n) with unit stride")
+    if c.shape[1] * c.element_size() < nbytes:
+        raise ValueError(f"coefficient rows hold {c.shape[1] * c.element_size()} bytes, "
+                         f"the layout needs {nbytes}")
+
+
+def forward_batch(x: torch.Tensor, wavelet="cdf97", levels: int = 1, band_dtype=None,
+                  out: torch.Tensor | None = None, workspace: torch.Tensor | None = None,
+                  stream=None) -> torch.Tensor:
+    """dwt2_forward_batch on N images (N, H, W); returns (N, layout bytes) uint8 coefficients
+    (or fills `out`, any (N, n) CUDA tensor whose rows hold the layout)."""
+    _check_batch_img(x)
+    N, H, W = x.shape
+    wid = _wid(wavelet)
+    img_dt = TORCH_DT[x.dtype]
+    bdt = TORCH_DT[band_dtype] if isinstance(band_dtype, torch.dtype) else (
+        band_dtype if band_dtype is not None else img_dt)
+    _, nbytes = layout(H, W, levels, bdt)
+    if out is None:
+        out = torch.empty((N, max(nbytes, 16)), dtype=torch.uint8, device=x.device)
+    _check_batch_coeffs(out, N, nbytes)
+    if workspace is None:
+        workspace = new_workspace(workspace_bytes_batch(N, H, W, levels, wid, bdt), x.device)
+    es = x.element_size()
+    rc = _lib().dwt2_forward_batch(
+        x.data_ptr(), x.stride(1) * es, x.stride(0) * es, N, H, W, img_dt, out.data_ptr(),
+        out.stride(0) * out.element_size(), workspace.data_ptr(), workspace.numel(), wid, levels,
+        bdt, _stream_ptr(stream))
+    if rc:
+        raise Dwt2Error(rc, "dwt2_forward_batch")
+    return out
+
+
+def inverse_batch(c: torch.Tensor, H: int, W: int, wavelet="cdf97", levels: int = 1,
+                  band_dtype=None, out: torch.Tensor | None = None, img_dtype=None,
+                  workspace: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """dwt2_inverse_batch: (N, n) coefficient rows -> (N, H, W) images."""
+    N = c.shape[0]
+    wid = _wid(wavelet)
+    bdt = band_dtype if band_dtype is not None else (DT_I32 if wid == 0 else DT_F32)
+    _, nbytes = layout(H, W, levels, bdt)
+    _check_batch_coeffs(c, N, nbytes)
+    if out is None:
+        dt = img_dtype or (torch.int32 if wid == 0 else torch.float32)
+        out = torch.empty((N, H, W), dtype=dt, device=c.device)
+    _check_batch_img(out)
+    if workspace is None:
+        workspace = new_workspace(workspace_bytes_batch(N, H, W, levels, wid, bdt), c.device)
+    es = out.element_size()
+    rc = _lib().dwt2_inverse_batch(
+        c.data_ptr(), c.stride(0) * c.element_size(), out.data_ptr(), out.stride(1) * es,
+        out.stride(0) * es, N, H, W, TORCH_DT[out.dtype], workspace.data_ptr(), workspace.numel(),
+        wid, levels, bdt, _stream_ptr(stream))
+    if rc:
+        raise Dwt2Error(rc, "dwt2_inverse_batch")
+    return out
+
+
+def forward_adjoint_batch(g: torch.Tensor, H: int, W: int, wavelet="cdf97", levels: int = 1,
+                          out: torch.Tensor | None = None, workspace: torch.Tensor | None = None,
+                          stream=None) -> torch.Tensor:
+    """dwt2_forward_adjoint_batch: W^T on (N, n) float32 band-gradient rows -> (N, H, W)."""
+    N = g.shape[0]
+    wid = _wid(wavelet)
+    _, nbytes = layout(H, W, levels, DT_F32)
+    _check_batch_coeffs(g, N, nbytes)
+    if out is None:
+        out = torch.empty((N, H, W), dtype=torch.float32, device=g.device)
+    _check_batch_img(out)
+    if workspace is None:
+        workspace = new_workspace(workspace_bytes_batch(N, H, W, levels, wid, DT_F32), g.device)
+    es = out.element_size()
+    rc = _lib().dwt2_forward_adjoint_batch(
+        g.data_ptr(), g.stride(0) * g.element_size(), out.data_ptr(), out.stride(1) * es,
+        out.stride(0) * es, N, H, W, TORCH_DT[out.dtype], workspace.data_ptr(), workspace.numel(),
+        wid, levels, DT_F32, _stream_ptr(stream))
+    if rc:
+        raise Dwt2Error(rc, "dwt2_forward_adjoint_batch")
+    return out
+
+
+def inverse_adjoint_batch(x: torch.Tensor, wavelet="cdf97", levels: int = 1,
+                          out: torch.Tensor | None = None, workspace: torch.Tensor | None = None,
+                          stream=None) -> torch.Tensor:
+    """dwt2_inverse_adjoint_batch: W^-T on (N, H, W) float32 gradients -> (N, n) band rows."""
+    _check_batch_img(x)
+    N, H, W = x.shape
+    wid = _wid(wavelet)
+    _, nbytes = layout(H, W, levels, DT_F32)
+    if out is None:
+        out = torch.zeros((N, max(nbytes, 16) // 4), dtype=torch.float32, device=x.device)
+    _check_batch_coeffs(out, N, nbytes)
+    if workspace is None:
+        workspace = new_workspace(workspace_bytes_batch(N, H, W, levels, wid, DT_F32), x.device)
+    es = x.element_size()
+    rc = _lib().dwt2_inverse_adjoint_batch(
+        x.data_ptr(), x.stride(1) * es, x.stride(0) * es, N, H, W, TORCH_DT[x.dtype],
+        out.data_ptr(), out.stride(0) * out.element_size(), workspace.data_ptr(),
+        workspace.numel(), wid, levels, DT_F32, _stream_ptr(stream))
+    if rc:
+        raise Dwt2Error(rc, "dwt2_inverse_adjoint_batch")
     return out
 
 

@@ -106,3 +106,41 @@ def test_argument_validation_before_any_launch(lib):
                                    None) == 1
     # inverse: null coefficient buffer
     assert lib.dwt2_inverse(None, fake, 64, 8, 8, 1, fake, 1 << 20, 1, 1, 1, None) == 1
+
+
+def test_batch_validation_and_workspace(lib):
+    """Uniform-batch entry points: bad counts and strides are rejected on the host, and the
+    workspace holds the shared status header plus one intermediate-LL region per image."""
+    fake = ctypes.c_void_p(0x1000)
+    one = D.workspace_bytes(512, 512, 3, "cdf97", D.DT_F32)
+    for n in (1, 2, 7):
+        assert D.workspace_bytes_batch(n, 512, 512, 3, "cdf97", D.DT_F32) == 256 + n * (one - 256)
+    assert D.workspace_bytes_batch(5, 512, 512, 1, "cdf97", D.DT_F32) == 256
+    assert lib.dwt2_workspace_bytes_batch(0, 8, 8, 1, 1, 1) == 0
+    _, cb = D.layout(16, 16, 2, D.DT_F32)
+    ws = D.workspace_bytes_batch(4, 16, 16, 2, "cdf97", D.DT_F32)
+    f = lib.dwt2_forward_batch
+    img_b = 16 * 64
+    # N out of range
+    assert f(fake, 64, img_b, 0, 16, 16, 1, fake, cb, fake, ws, 2, 2, 1, None) == 1
+    assert f(fake, 64, img_b, 70000, 16, 16, 1, fake, cb, fake, ws, 2, 2, 1, None) == 1
+    # image batch stride smaller than one image
+    assert f(fake, 64, img_b - 64, 4, 16, 16, 1, fake, cb, fake, ws, 2, 2, 1, None) == 1
+    # image batch stride not a whole number of elements
+    assert f(fake, 64, img_b + 2, 4, 16, 16, 1, fake, cb, fake, ws, 2, 2, 1, None) == 1
+    # coefficient batch stride smaller than the layout, or not a multiple of 16
+    assert f(fake, 64, img_b, 4, 16, 16, 1, fake, cb - 16, fake, ws, 2, 2, 1, None) == 1
+    assert f(fake, 64, img_b, 4, 16, 16, 1, fake, cb + 4, fake, ws, 2, 2, 1, None) == 1
+    # workspace sized for fewer images
+    small = D.workspace_bytes_batch(3, 16, 16, 2, "cdf97", D.DT_F32)
+    assert f(fake, 64, img_b, 4, 16, 16, 1, fake, cb, fake, small, 2, 2, 1, None) == 3
+    # the other three directions check the same way
+    assert lib.dwt2_inverse_batch(fake, cb + 4, fake, 64, img_b, 4, 16, 16, 1, fake, ws, 2, 2, 1,
+                                  None) == 1
+    assert lib.dwt2_forward_adjoint_batch(fake, cb, fake, 64, img_b - 64, 4, 16, 16, 1, fake, ws,
+                                          2, 2, 1, None) == 1
+    assert lib.dwt2_inverse_adjoint_batch(fake, 64, img_b, 0, 16, 16, 1, fake, cb, fake, ws, 2, 2,
+                                          1, None) == 1
+    # integer wavelet has no adjoint
+    assert lib.dwt2_inverse_adjoint_batch(fake, 64, img_b, 4, 16, 16, 0, fake, cb, fake, ws, 0, 2,
+                                          0, None) == 2
