@@ -22,6 +22,7 @@ import hashlib
 import json
 import os
 import subprocess
+import tempfile
 import sys
 import threading
 import time
@@ -275,6 +276,151 @@ def run_precision(args, D, I, dev, flush, stream):
                       "report": report}), flush=True)
 
 
+
+# ------------------------------------------------------------------------------------------------
+# The other workloads of the scope table, timed in the default run beside the headline:
+# a batch of 512 uneven images (one persistent launch from a CUDA graph vs one call per image),
+# the autograd step on 64 x 3 x 1024^2, and 16384^2 band storage in fp32 / bf16 / fp16.
+
+def run_batch_workload(D, I, dev, run_case, steps, warmup):
+    """512 images, sides log-uniform on [63, 4096], 4 levels; int 5/3 and fp32 9/7."""
+    sizes = I.batch_sizes(512, I.seed_for(3))
+    lv = 4
+    npix = sum(h * w for h, w in sizes)
+    ab = sum(alg_bytes(h, w, lv) for h, w in sizes)
+    res = {"images": len(sizes), "levels": lv, "pixels": npix,
+           "algorithmic_bytes_per_step": ab,
+           "sizes": "each side round(exp(U[ln 63, ln 4096])), independent, seeded"}
+    for wv, dt in (("cdf53_int", torch.int32), ("cdf97", torch.float32)):
+        imgs = [I.field_device(h, w, I.seed_for(3, k), dev).to(dt) for k, (h, w) in
+                enumerate(sizes)]
+        with tempfile.TemporaryDirectory() as td:
+            plan, coeffs = D.plan_forward(imgs, wv, lv, tune_cache=os.path.join(td, "tune.txt"))
+        ms_plan = run_case(plan.run, steps, warmup)
+        status = D.check_status(plan.workspace)
+        bdt = D.TORCH_DT[dt]
+        ws = D.new_workspace(max(D.workspace_bytes(h, w, lv, wv, bdt) for h, w in sizes), dev)
+
+        def loop():
+            for x, c in zip(imgs, coeffs):
+                D.forward(x, wv, lv, out=c, workspace=ws)
+
+        ms_loop = run_case(loop, max(3, steps // 4), warmup)
+        ms_graph = None
+        try:
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g):
+                loop()
+            ms_graph = run_case(g.replay, steps, warmup)
+        except RuntimeError as e:  # report, do not hide, a capture failure
+            ms_graph = f"capture failed: {str(e).splitlines()[0]}"
+        # the plan's bits equal the per-image calls' bits
+        plan.run()
+        snap = [coeffs[k].buffer.clone() for k in (0, 255, 511)]
+        loop()
+        torch.cuda.synchronize()
+        same = all(torch.equal(a, coeffs[k].buffer) for a, k in zip(snap, (0, 255, 511)))
+
+        def rate(ms):
+            if not isinstance(ms, float):
+                return ms
+            return {"ms": round(ms, 4), "gpix_s": round(npix / (ms * 1e-3) / 1e9, 2),
+                    "gb_s": round(ab / (ms * 1e-3) / 1e9, 1)}
+
+        res[wv] = {"plan_graph": rate(ms_plan), "per_image_calls": rate(ms_loop),
+                   "per_image_calls_graph": rate(ms_graph), "plan": plan.info(),
+                   "plan_equals_per_image_calls": same, "device_status": status}
+        plan.close()
+        del imgs, coeffs, ws, plan
+        torch.cuda.empty_cache()
+    return res
+
+
+def run_autograd_workload(D, A, I, dev, run_case, steps, warmup):
+    """64 x 3 x 1024^2 fp32 in [0, 1], 3-level 9/7: loss = L1 of every high-pass band plus the
+    MSE of the reconstruction; one step = forward + backward through the autograd Functions."""
+    B, C, H, W, lv = 64, 3, 1024, 1024, 3
+    x = torch.empty((B, C, H, W), device=dev)
+    flat = x.view(-1, H, W)
+    for k in range(B * C):
+        flat[k] = I.field_device(H, W, I.seed_for(4, k), dev) / 255.0
+    x.requires_grad_(True)
+    n = A.coeff_floats(H, W, lv)
+    lay, _ = D.layout(H, W, lv, D.DT_F32)
+    mask = torch.ones(n, device=dev)
+    ll = lay[0]
+    mask[ll.offset_bytes // 4: ll.offset_bytes // 4 + ll.h * ll.pitch_bytes // 4] = 0.0
+
+    def step():
+        c = A.dwt2(x, "cdf97", lv)
+        y = A.idwt2(c, H, W, "cdf97", lv)
+        loss = (c.abs() * mask).sum() + (y - x).pow(2).mean()
+        loss.backward()
+        x.grad = None
+
+    ms_step = run_case(step, steps, warmup)
+    # the four transforms of a step alone, through the batched entry points
+    xs = x.detach().view(-1, H, W)
+    N = xs.shape[0]
+    cbuf = torch.zeros((N, n), device=dev)
+    ybuf = torch.empty_like(xs)
+    gc = torch.zeros_like(cbuf)
+    gx = torch.empty_like(xs)
+    ws = D.new_workspace(D.workspace_bytes_batch(N, H, W, lv, "cdf97", D.DT_F32), dev)
+
+    def transforms():
+        D.forward_batch(xs, "cdf97", lv, D.DT_F32, out=cbuf, workspace=ws)
+        D.inverse_batch(cbuf, H, W, "cdf97", lv, D.DT_F32, out=ybuf, workspace=ws)
+        D.inverse_adjoint_batch(ybuf, "cdf97", lv, out=gc, workspace=ws)
+        D.forward_adjoint_batch(gc, H, W, "cdf97", lv, out=gx, workspace=ws)
+
+    ms_tr = run_case(transforms, steps, warmup)
+    ms_fwd = run_case(lambda: D.forward_batch(xs, "cdf97", lv, D.DT_F32, out=cbuf, workspace=ws),
+                      steps, warmup)
+    status = D.check_status(ws)
+    npix = N * H * W
+    ab = N * alg_bytes(H, W, lv)
+    return {"batch": [B, C, H, W], "levels": lv, "pixels": npix,
+            "fwd_bwd_step": {"ms": round(ms_step, 4),
+                             "gpix_s": round(npix / (ms_step * 1e-3) / 1e9, 2)},
+            "four_transforms": {"ms": round(ms_tr, 4),
+                                "gb_s": round(4 * ab / (ms_tr * 1e-3) / 1e9, 1),
+                                "share_of_step": round(ms_tr / ms_step, 3)},
+            "forward_only_plain_f32": {"ms": round(ms_fwd, 4),
+                                       "gpix_s": round(npix / (ms_fwd * 1e-3) / 1e9, 2),
+                                       "gb_s": round(ab / (ms_fwd * 1e-3) / 1e9, 1)},
+            "algorithmic_bytes_per_transform": ab, "device_status": status}
+
+
+def run_storage_workload(D, I, dev, run_case, steps, warmup):
+    """16384^2, 0.5 * field + 0.5 * U[0, 255), CDF 9/7, 5 levels: fp32 vs bf16 / fp16 band
+    storage (fp32 arithmetic, fp32 LL), forward and inverse times.  The per-band errors against
+    the fp64 oracle come from --precision."""
+    n, lv = 16384, LEVELS
+    g = torch.Generator(device=dev).manual_seed(I.seed_for(2) + 50)
+    x = 0.5 * I.field_device(n, n, I.seed_for(2), dev, integer=False) + \
+        0.5 * 255.0 * torch.rand((n, n), generator=g, device=dev)
+    res = {}
+    for name, dt in (("f32", torch.float32), ("bf16", torch.bfloat16), ("f16", torch.float16)):
+        bdt = D.TORCH_DT[dt]
+        c = D.alloc_coeffs(n, n, lv, "cdf97", bdt, dev)
+        ws = D.new_workspace(D.workspace_bytes(n, n, lv, "cdf97", bdt), dev)
+        y = torch.empty_like(x)
+        ms_f = run_case(lambda: D.forward(x, "cdf97", lv, band_dtype=bdt, out=c, workspace=ws),
+                        steps, warmup)
+        ms_i = run_case(lambda: D.inverse(c, out=y, workspace=ws), steps, warmup)
+        nb = storage_bytes(n, n, lv, 4, 4 if dt == torch.float32 else 2)
+        res[name] = {"fwd_ms": round(ms_f, 4), "fwd_gpix_s": round(n * n / (ms_f * 1e-3) / 1e9, 2),
+                     "inv_ms": round(ms_i, 4), "inv_gpix_s": round(n * n / (ms_i * 1e-3) / 1e9, 2),
+                     "storage_bytes": nb, "fwd_gb_s": round(nb / (ms_f * 1e-3) / 1e9, 1),
+                     "roundtrip_max_abs": float((y - x).abs().max()),
+                     "device_status": D.check_status(ws)}
+        del c, ws, y
+    del x
+    torch.cuda.empty_cache()
+    return res
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -282,6 +428,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--headline-only", action="store_true",
+                    help="skip the batched, autograd and storage workloads")
     ap.add_argument("--precision", action="store_true",
                     help="16384x16384 CDF 9/7, 5 levels: per-band error of fp32 / bf16 / fp16 band "
                          "storage against the fp64 oracle, and the time of each")
@@ -437,6 +585,18 @@ def main():
            "h2d_bytes_per_step": host_in.numel() * host_in.element_size(),
            "d2h_bytes_per_step": host_out.numel()}
 
+    # ---- the other workloads (batched plan, autograd, reduced-precision storage) ----
+    workloads = None
+    if not args.headline_only:
+        from paper_1708_07853_gb300 import autograd as A
+        wsteps = max(3, min(args.steps, 20))
+        workloads = {
+            "batch_512_uneven_4lv": run_batch_workload(D, I, dev, run_case, wsteps, args.warmup),
+            "autograd_64x3x1024sq_3lv": run_autograd_workload(D, A, I, dev, run_case, wsteps,
+                                                                args.warmup),
+            "storage_16384sq_cdf97_5lv": run_storage_workload(D, I, dev, run_case, wsteps,
+                                                              args.warmup)}
+
     # ---- CPU baseline: the oracle on the host, bounded sample ----
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -458,6 +618,7 @@ def main():
             "hbm_gb_s": cases["fwd_cdf97_f32_nonsep"]["gb_s"],
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": args.steps * LEVELS, "clocks": clocks, "cases": cases,
+            "workloads": workloads,
             "device_status": status, "int53_roundtrip_exact": correct_inv}
     if rank == 0:
         print(json.dumps(line), flush=True)

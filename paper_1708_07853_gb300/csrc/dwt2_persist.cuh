@@ -185,6 +185,7 @@ __global__ void __launch_bounds__(kThreads, min_ctas<WV>())
         // all copies have landed.  After an abort, let the copies still in flight land first.  (No
         // drain otherwise: the sentinel's stage has moved one phase past its last copy.)
         if (tma_used && lane == 0 && *ring.abort) drain_ring(ring, g, p.status);
+        cp_async_wait_all();  // no-op unless this lane issued cp.async copies
         return;
     }
 
@@ -283,6 +284,7 @@ __global__ void __launch_bounds__(kThreads, min_ctas<WV>())
         // all copies have landed.  After an abort, let the copies still in flight land first.  (No
         // drain otherwise: the sentinel's stage has moved one phase past its last copy.)
         if (tma_used && lane == 0 && *ring.abort) drain_ring(ring, g, p.status);
+        cp_async_wait_all();  // no-op unless this lane issued cp.async copies
         return;
     }
 

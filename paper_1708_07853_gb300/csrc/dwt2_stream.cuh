@@ -132,6 +132,54 @@ __device__ __forceinline__ uint8_t* align128(uint8_t* p) {
 // Forward data flow: loads of extended quad row q (pixel rows 2q, 2q + 1) of the input plane.
 // Mirrored (whole-sample symmetric) rows for the transform; plain rows, zeros outside, for the
 // adjoint of the inverse.
+// Plain-load producer for planes TMA cannot address (pitch or base not 16-byte aligned).  Only
+// the caller's own image takes this path (every scratch plane is TMA-eligible), so nothing the
+// running kernel writes is read here.
+template <typename TI>
+__device__ __forceinline__ void fwd_produce_plain(const FwdArgs& a, int r0, int r1, int xs, TI* dst,
+                                               uint64_t* full, int lane, int z) {
+    const bool ok0 = r0 >= 0 && r0 < a.H, ok1 = r1 >= 0 && r1 < a.H;
+    const char* base = static_cast<const char*>(a.in) + int64_t(z) * a.in_bstride;
+    const TI* row0 = reinterpret_cast<const TI*>(base + int64_t(ok0 ? r0 : 0) * a.in_pitch);
+    const TI* row1 = reinterpret_cast<const TI*>(base + int64_t(ok1 ? r1 : 0) * a.in_pitch);
+    constexpr int kPer = kSRow / 32;
+    if constexpr (sizeof(TI) == 4) {
+        // cp.async element copies, zero-filled outside the plane: like TMA, the producer moves on
+        // to the next stage at once and the stage's full barrier completes when the copies have
+        // landed, so up to kStages stages are in flight.  Nothing waits inside the loop, so it is
+        // not unrolled (the kernels keep the instruction footprint of the TMA path).
+#pragma unroll 1
+        for (int j = 0; j < kPer; ++j) {
+            const int k = lane + 32 * j, c = xs + k;
+            const bool in = c >= 0 && c < a.W;
+            cp_async_4(dst + k, row0 + (in ? c : 0), in && ok0);
+            cp_async_4(dst + kSRow + k, row1 + (in ? c : 0), in && ok1);
+        }
+        cp_async_arrive(full);
+    } else {
+        // 16-bit elements (below cp.async's 4-byte minimum): all loads of the stage are issued
+        // before the first shared-memory store, one memory latency per stage.
+        TI v0[kPer], v1[kPer];
+#pragma unroll
+        for (int j = 0; j < kPer; ++j) {
+            const int c = xs + lane + 32 * j;
+            const bool in = c >= 0 && c < a.W;
+            v0[j] = (in && ok0) ? ldcg(row0 + c) : zero_of<TI>();
+            v1[j] = (in && ok1) ? ldcg(row1 + c) : zero_of<TI>();
+        }
+#pragma unroll
+        for (int j = 0; j < kPer; ++j) {
+            dst[lane + 32 * j] = v0[j];
+            dst[kSRow + lane + 32 * j] = v1[j];
+        }
+    }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(full);
+}
+
+// Forward data flow: loads of extended quad row q (pixel rows 2q, 2q + 1) of the input plane.
+// Mirrored (whole-sample symmetric) rows for the transform; plain rows, zeros outside, for the
+// adjoint of the inverse.
 template <typename TI>
 __device__ __forceinline__ void fwd_produce_row(const FwdArgs& a, const CUtensorMap* tm, bool adj,
                                                 int q, int xs, TI* dst, uint64_t* full, int lane,
@@ -148,19 +196,7 @@ __device__ __forceinline__ void fwd_produce_row(const FwdArgs& a, const CUtensor
             }
         }
     } else {
-        // plain loads (unaligned planes); .cg: the plane may have been written by other SMs
-        const bool ok0 = r0 >= 0 && r0 < a.H, ok1 = r1 >= 0 && r1 < a.H;
-        const char* base = static_cast<const char*>(a.in) + int64_t(z) * a.in_bstride;
-        const TI* row0 = reinterpret_cast<const TI*>(base + int64_t(ok0 ? r0 : 0) * a.in_pitch);
-        const TI* row1 = reinterpret_cast<const TI*>(base + int64_t(ok1 ? r1 : 0) * a.in_pitch);
-        for (int k = lane; k < kSRow; k += 32) {
-            const int c = xs + k;
-            const bool in = c >= 0 && c < a.W;
-            dst[k] = (in && ok0) ? ldcg(row0 + c) : zero_of<TI>();
-            dst[kSRow + k] = (in && ok1) ? ldcg(row1 + c) : zero_of<TI>();
-        }
-        __syncwarp();
-        if (lane == 0) mbar_arrive(full);
+        fwd_produce_plain<TI>(a, r0, r1, xs, dst, full, lane, z);
     }
 }
 
@@ -257,23 +293,38 @@ __device__ __forceinline__ void inv_produce_row(const InvArgs& a, const CUtensor
             }
         }
     } else {
+        // Plain loads (planes too small or too unaligned for TMA; in a persistent kernel they may
+        // have been written by other SMs, hence .cg).  All loads of the stage are issued before
+        // the first shared-memory store: one memory latency per stage.
         const int rows[4] = {re, re, ro, ro};
         const int widths[4] = {a.nec, a.ndc, a.nec, a.ndc};
         const int heights[4] = {a.ner, a.ner, a.ndr, a.ndr};
+        constexpr int kPer = kBRow / 32;
+        const char* src[4];
+        bool row_ok[4];
 #pragma unroll
         for (int b = 0; b < 4; ++b) {
-            const bool row_ok = rows[b] >= 0 && rows[b] < heights[b];
-            const char* src = static_cast<const char*>(a.band[b]) + int64_t(z) * a.band_bstride[b] +
-                              int64_t(row_ok ? rows[b] : 0) * a.band_pitch[b];
-            for (int k = lane; k < kBRow; k += 32) {
-                const int c = xb + k;
-                const bool in = row_ok && c >= 0 && c < widths[b];
-                if (b == 0)
-                    sll[k] = in ? ldcg(reinterpret_cast<const TL*>(src) + c) : zero_of<TL>();
-                else
-                    sb[(b - 1) * kBRow + k] =
-                        in ? ldcg(reinterpret_cast<const TB*>(src) + c) : zero_of<TB>();
-            }
+            row_ok[b] = rows[b] >= 0 && rows[b] < heights[b];
+            src[b] = static_cast<const char*>(a.band[b]) + int64_t(z) * a.band_bstride[b] +
+                     int64_t(row_ok[b] ? rows[b] : 0) * a.band_pitch[b];
+        }
+        TL vl[kPer];
+        TB vb[3][kPer];
+#pragma unroll
+        for (int j = 0; j < kPer; ++j) {
+            const int c = xb + lane + 32 * j;
+            vl[j] = (row_ok[0] && c >= 0 && c < widths[0])
+                        ? ldcg(reinterpret_cast<const TL*>(src[0]) + c) : zero_of<TL>();
+#pragma unroll
+            for (int b = 1; b < 4; ++b)
+                vb[b - 1][j] = (row_ok[b] && c >= 0 && c < widths[b])
+                                   ? ldcg(reinterpret_cast<const TB*>(src[b]) + c) : zero_of<TB>();
+        }
+#pragma unroll
+        for (int j = 0; j < kPer; ++j) {
+            sll[lane + 32 * j] = vl[j];
+#pragma unroll
+            for (int b = 0; b < 3; ++b) sb[b * kBRow + lane + 32 * j] = vb[b][j];
         }
         __syncwarp();
         if (lane == 0) mbar_arrive(full);
@@ -432,6 +483,7 @@ __global__ void __launch_bounds__(kThreads, min_ctas<WV>())
             issued = i + 1;
         }
         if (args.tma && lane == 0) drain_ring(ring, issued, args.status);
+        cp_async_wait_all();  // no-op unless this lane issued cp.async copies
         return;
     }
 
@@ -518,6 +570,7 @@ __global__ void __launch_bounds__(kThreads, min_ctas<WV>())
             issued = i + 1;
         }
         if (args.tma && lane == 0) drain_ring(ring, issued, args.status);
+        cp_async_wait_all();  // no-op unless this lane issued cp.async copies
         return;
     }
 
@@ -563,25 +616,39 @@ struct LaunchGeom {
     int rpc;
 };
 
-// Rows per CTA.  Large planes: about one wave of CTAs (SM count x resident CTAs per SM) with at
-// least 16 quad rows each, so the 4 halo rows of a CTA stay a small overhead on HBM reads.
-// Small planes (a few MB, served from L2 after the previous level wrote them): as many CTAs as
-// fit, down to 4 rows each, because there the per-row latency of a CTA, not bytes, sets the time.
+// Rows per CTA.  A CTA streams its rows one after another, so a launch lasts about
+// waves x (rows per CTA + a fixed cost of halo rows and pipeline fill), waves being the CTA count
+// over the resident slots (SM count x CTAs per SM).  The row-block count that minimises that
+// estimate is taken: for one large plane, one wave of CTAs; for a batch of many planes, whole
+// waves with no small last wave; for small planes, as many CTAs as fit.  Rows per CTA stay at
+// least 16 for large data (the halo is then a small overhead on HBM reads) and at least 4 for
+// data of a few MB (served from L2 after the previous level wrote it), where the per-row latency
+// of a CTA, not bytes, sets the time.
 inline LaunchGeom pick_geometry(int ner, int nec, int64_t plane_bytes, int sms, int ctas_per_sm,
                                 int nbatch) {
+    constexpr int64_t kRowCost = 8;  // halo rows + pipeline fill, in rows
+    const int n = std::max(1, nbatch);
     const int strips = (nec + kCtaQ - 1) / kCtaQ;
-    const int target = std::max(1, sms * (ctas_per_sm > 0 ? ctas_per_sm : 1) / std::max(1, nbatch));
-    const int min_rows = plane_bytes < (int64_t(24) << 20) ? 4 : 16;
-    const int rb_max = (ner + min_rows - 1) / min_rows;
-    int rb = target / strips;
-    if (rb < 1) rb = 1;
-    if (rb > rb_max) rb = rb_max;
-    int rpc = (ner + rb - 1) / rb;
-    if (rpc < 1) rpc = 1;
-    rb = (ner + rpc - 1) / rpc;
+    const int64_t slots = int64_t(std::max(1, sms)) * std::max(1, ctas_per_sm);
+    const int min_rows = plane_bytes * n < (int64_t(24) << 20) ? 4 : 16;
+    const int rb_max = std::max(1, (ner + min_rows - 1) / min_rows);
+    int best_rb = 1;
+    int64_t best = -1;
+    for (int rb = 1; rb <= rb_max; ++rb) {
+        const int rpc = (ner + rb - 1) / rb;
+        const int used = (ner + rpc - 1) / rpc;  // row blocks that are not empty
+        if (used != rb) continue;
+        const int64_t ctas = int64_t(strips) * used * n;
+        const int64_t waves = (ctas + slots - 1) / slots;
+        const int64_t cost = waves * (rpc + kRowCost);
+        if (best < 0 || cost < best) {
+            best = cost;
+            best_rb = rb;
+        }
+    }
     LaunchGeom g;
-    g.grid = dim3(strips, rb, std::max(1, nbatch));
-    g.rpc = rpc;
+    g.rpc = (ner + best_rb - 1) / best_rb;
+    g.grid = dim3(strips, (ner + g.rpc - 1) / g.rpc, n);
     return g;
 }
 

@@ -7,6 +7,10 @@ with a 1/f^2 power spectrum (the spectrum of natural images) stands in for image
 Recipe (field): z ~ N(0, 1) of shape H x W from numpy's default_rng(seed); Z = rfft2(z) * 1/|f|
 with the DC term set to 0 (amplitude 1/f, power 1/f^2); v = irfft2(Z), min-max scaled to
 [lo, hi]; for integer content rounded half-to-even.
+
+`field_device` follows the same recipe on the GPU (torch's generator and FFT, fp32) for
+benchmark workloads too large to draw on the host in seconds; its values differ from `field`'s
+for the same seed, so tests that compare against the oracle draw with `field`.
 """
 from __future__ import annotations
 
@@ -42,6 +46,28 @@ def field(H: int, W: int, seed: int, lo: float = 0.0, hi: float = 255.0,
     if integer:
         v = np.rint(v)
     return v.astype(dtype)
+
+
+def field_device(H: int, W: int, seed: int, device, lo: float = 0.0, hi: float = 255.0,
+                 integer: bool = True):
+    """`field`'s recipe drawn on a CUDA device (fp32 result); for benchmark-sized batches."""
+    import torch
+    g = torch.Generator(device=device).manual_seed(seed)
+    z = torch.randn((H, W), generator=g, device=device, dtype=torch.float32)
+    Z = torch.fft.rfft2(z)
+    fy = torch.fft.fftfreq(H, device=device)[:, None]
+    fx = torch.fft.rfftfreq(W, device=device)[None, :]
+    f = torch.sqrt(fx * fx + fy * fy)
+    f[0, 0] = float("inf")
+    v = torch.fft.irfft2(Z / f, s=(H, W))
+    vmin, vmax = v.min(), v.max()
+    if float(vmax) > float(vmin):
+        v = (v - vmin) * ((hi - lo) / (vmax - vmin)) + lo
+    else:
+        v = torch.full((H, W), lo, device=device)
+    if integer:
+        v = torch.round(v)
+    return v.contiguous()
 
 
 def field_plus_noise(H: int, W: int, seed: int, dtype=np.float32) -> np.ndarray:
