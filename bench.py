@@ -61,12 +61,17 @@ def alg_bytes(h: int, w: int, levels: int, esize: int = 4) -> int:
     return tot
 
 
-def src_hash() -> str:
+# Sources the level-1 forward kernel is compiled from: a recorded ncu capture counts only while
+# these are unchanged.
+KERNEL_SOURCES = {"fwd_l1_cdf97_f32": ["dwt2_device.cuh", "dwt2_lifting.cuh", "dwt2_stream.cuh",
+                                       "dwt2_fwd_f97.cu"]}
+
+
+def src_hash(kernel_key: str) -> str:
     d = os.path.join(ROOT, "paper_1708_07853_gb300", "csrc")
     m = hashlib.sha256()
-    for f in sorted(os.listdir(d)):
-        if f.endswith((".cu", ".cuh", ".h")):
-            m.update(open(os.path.join(d, f), "rb").read())
+    for f in KERNEL_SOURCES[kernel_key]:
+        m.update(open(os.path.join(d, f), "rb").read())
     return m.hexdigest()[:16]
 
 
@@ -77,7 +82,7 @@ def recorded_traffic(kernel_key: str):
         return None
     d = json.load(open(p))
     e = d.get(kernel_key)
-    if not e or e.get("src_hash") != src_hash():
+    if not e or e.get("src_hash") != src_hash(kernel_key):
         return None
     return e.get("dram_bytes_per_launch")
 
@@ -192,18 +197,30 @@ def run_only(args, D, dev, x_f32, x_i32, flush, stream):
         "fwd_cdf53_int": ("cdf53_int", x_i32, LEVELS, False, "nonsep"),
         "inv_cdf53_int": ("cdf53_int", x_i32, LEVELS, True, "nonsep"),
         "twopass_cdf97": ("cdf97", x_f32, LEVELS, False, "sep_twopass"),
+        "plan_cdf97": ("cdf97", x_f32, LEVELS, False, "plan"),
+        "plan_cdf53_int": ("cdf53_int", x_i32, LEVELS, False, "plan"),
     }[args.only]
+    if args.levels:
+        lv = args.levels
     bdt = D.TORCH_DT[x.dtype]
-    c = D.alloc_coeffs(H, W, lv, wv, bdt, dev)
-    ws = D.new_workspace(D.workspace_bytes(H, W, lv, wv, bdt, scheme), dev)
     out = torch.empty_like(x)
-    D.forward(x, wv, lv, scheme=scheme, out=c, workspace=ws)
+    if scheme == "plan":
+        # the same image through a one-image plan: all levels in one persistent launch
+        plan, (c,) = D.plan_forward([x], wv, lv)
+        ws = plan.workspace
 
-    def step():
-        if inv:
-            D.inverse(c, out=out, workspace=ws)
-        else:
-            D.forward(x, wv, lv, scheme=scheme, out=c, workspace=ws)
+        def step():
+            plan.run()
+    else:
+        c = D.alloc_coeffs(H, W, lv, wv, bdt, dev)
+        ws = D.new_workspace(D.workspace_bytes(H, W, lv, wv, bdt, scheme), dev)
+        D.forward(x, wv, lv, scheme=scheme, out=c, workspace=ws)
+
+        def step():
+            if inv:
+                D.inverse(c, out=out, workspace=ws)
+            else:
+                D.forward(x, wv, lv, scheme=scheme, out=c, workspace=ws)
 
     for _ in range(args.warmup):
         step()
@@ -435,8 +452,10 @@ def main():
                          "storage against the fp64 oracle, and the time of each")
     ap.add_argument("--only", default=None,
                     choices=["fwd_l1_cdf97", "fwd_cdf97", "inv_cdf97", "fwd_cdf53_int",
-                             "inv_cdf53_int", "twopass_cdf97"],
+                             "inv_cdf53_int", "twopass_cdf97", "plan_cdf97", "plan_cdf53_int"],
                     help="run one case only (for profiler captures); prints a short line")
+    ap.add_argument("--levels", type=int, default=0,
+                    help="with --only: decomposition levels instead of the case's own")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")

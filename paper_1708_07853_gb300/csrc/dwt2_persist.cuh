@@ -17,8 +17,8 @@
 
 namespace dwt2 {
 
-// One image at one level of a batched plan (64-byte aligned: the tensor maps live here).
-struct alignas(64) FwdUnit {
+// One image at one level of a batched plan (aligned like its tensor maps, which TMA reads here).
+struct FwdUnit {
     CUtensorMap tm;  // input plane (when a.tma)
     FwdArgs a;
     int item_begin;  // first ticket of the unit
@@ -27,7 +27,7 @@ struct alignas(64) FwdUnit {
     int dep;         // unit that must complete first (-1: none)
 };
 
-struct alignas(64) InvUnit {
+struct InvUnit {
     CUtensorMap tm[4];  // LL, HL, LH, HH (when a.tma)
     InvArgs a;
     int item_begin;
@@ -176,7 +176,7 @@ __global__ void __launch_bounds__(kThreads, min_ctas<WV>())
                     }
                 }
                 if (lane == 0) ring.meta[s] = t;
-                fwd_produce_row<TI>(U.a, &U.tm, kAdj, tl.qfirst + i, xs,
+                fwd_produce_row<TI, kSRow / 32>(U.a, &U.tm, kAdj, tl.qfirst + i, xs,
                                     reinterpret_cast<TI*>(ring.stage(s)), &ring.full[s], lane, 0);
             }
             if (!alive) break;

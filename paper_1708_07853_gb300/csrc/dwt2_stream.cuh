@@ -135,9 +135,9 @@ __device__ __forceinline__ uint8_t* align128(uint8_t* p) {
 // Plain-load producer for planes TMA cannot address (pitch or base not 16-byte aligned).  Only
 // the caller's own image takes this path (every scratch plane is TMA-eligible), so nothing the
 // running kernel writes is read here.
-template <typename TI>
+template <typename TI, int kUnroll>
 __device__ __forceinline__ void fwd_produce_plain(const FwdArgs& a, int r0, int r1, int xs, TI* dst,
-                                               uint64_t* full, int lane, int z) {
+                                                  uint64_t* full, int lane, int z) {
     const bool ok0 = r0 >= 0 && r0 < a.H, ok1 = r1 >= 0 && r1 < a.H;
     const char* base = static_cast<const char*>(a.in) + int64_t(z) * a.in_bstride;
     const TI* row0 = reinterpret_cast<const TI*>(base + int64_t(ok0 ? r0 : 0) * a.in_pitch);
@@ -146,9 +146,10 @@ __device__ __forceinline__ void fwd_produce_plain(const FwdArgs& a, int r0, int 
     if constexpr (sizeof(TI) == 4) {
         // cp.async element copies, zero-filled outside the plane: like TMA, the producer moves on
         // to the next stage at once and the stage's full barrier completes when the copies have
-        // landed, so up to kStages stages are in flight.  Nothing waits inside the loop, so it is
-        // not unrolled (the kernels keep the instruction footprint of the TMA path).
-#pragma unroll 1
+        // landed, so up to kStages stages are in flight.  kUnroll: 1 in the single-image kernels
+        // (their TMA path keeps its instruction footprint), fully unrolled in the persistent
+        // kernels, where unaligned images of a batch make this path common.
+#pragma unroll kUnroll
         for (int j = 0; j < kPer; ++j) {
             const int k = lane + 32 * j, c = xs + k;
             const bool in = c >= 0 && c < a.W;
@@ -180,7 +181,7 @@ __device__ __forceinline__ void fwd_produce_plain(const FwdArgs& a, int r0, int 
 // Forward data flow: loads of extended quad row q (pixel rows 2q, 2q + 1) of the input plane.
 // Mirrored (whole-sample symmetric) rows for the transform; plain rows, zeros outside, for the
 // adjoint of the inverse.
-template <typename TI>
+template <typename TI, int kUnrollPlain = 1>
 __device__ __forceinline__ void fwd_produce_row(const FwdArgs& a, const CUtensorMap* tm, bool adj,
                                                 int q, int xs, TI* dst, uint64_t* full, int lane,
                                                 int z) {
@@ -196,7 +197,7 @@ __device__ __forceinline__ void fwd_produce_row(const FwdArgs& a, const CUtensor
             }
         }
     } else {
-        fwd_produce_plain<TI>(a, r0, r1, xs, dst, full, lane, z);
+        fwd_produce_plain<TI, kUnrollPlain>(a, r0, r1, xs, dst, full, lane, z);
     }
 }
 

@@ -163,3 +163,24 @@ def test_log_uniform_batch_64():
         torch.cuda.synchronize()
         for x, c in zip(imgs, coeffs):
             _same(c, D.forward(x, wavelet, 4))
+
+
+@pytest.mark.parametrize("wavelet,dtype", [("cdf53_int", torch.int32), ("cdf97", torch.float32)])
+def test_large_image_plan_many_row_blocks(wavelet, dtype):
+    """One 4100 x 3000 image (plus two small ones), 5 levels: many tiles per level and many
+    CTAs waiting on each level's completion counter, forward and inverse, bit for bit against
+    the single-image calls."""
+    imgs = _images([(4100, 3000), (300, 517), (63, 64)], dtype, 18)
+    plan, coeffs = D.plan_forward(imgs, wavelet, 5)
+    plan.run()
+    torch.cuda.synchronize()
+    assert D.check_status(plan.workspace) == 0
+    for x, c in zip(imgs, coeffs):
+        _same(c, D.forward(x, wavelet, 5))
+    outs = [torch.empty_like(x) for x in imgs]
+    inv = D.Plan(outs, coeffs, wavelet, 5, "inverse")
+    inv.run()
+    torch.cuda.synchronize()
+    assert D.check_status(inv.workspace) == 0
+    for o, c in zip(outs, coeffs):
+        assert torch.equal(o, D.inverse(c))
