@@ -101,6 +101,28 @@ __device__ __forceinline__ Tile tile_of(const Args& a, int local, int strips) {
     return t;
 }
 
+// Starts fetching a unit's tensor maps into the TMA unit's descriptor cache.
+__device__ __forceinline__ void prefetch_unit_maps(const FwdUnit& u) {
+    if (u.a.tma) prefetch_tensormap(&u.tm);
+}
+__device__ __forceinline__ void prefetch_unit_maps(const InvUnit& u) {
+    if (u.a.tma)
+        for (int k = 0; k < 4; ++k) prefetch_tensormap(&u.tm[k]);
+}
+
+// Copies a unit's argument block into shared memory (one warp, read-only source), so that the
+// per-row code reads it there: global stores to the bands could alias a global copy, which would
+// force the compiler to reload it after every row.
+template <typename Args>
+__device__ __forceinline__ void copy_args(Args* dst, const Args* src, int lane) {
+    static_assert(sizeof(Args) % 4 == 0, "argument block is copied in words");
+    const int* s = reinterpret_cast<const int*>(src);
+    int* d = reinterpret_cast<int*>(dst);
+    __syncwarp();
+    for (int k = lane; k < int(sizeof(Args) / 4); k += 32) d[k] = __ldg(s + k);
+    __syncwarp();
+}
+
 // Producer side shared by both kernel shapes: claim the next ticket; returns -1 when the work is
 // exhausted.  Waits for the ticket's dependency.
 template <typename Unit>
@@ -112,6 +134,7 @@ __device__ __forceinline__ int claim(const PersistArgs<Unit>& p, volatile int* a
     ok = true;
     if (t >= p.n_items) return -1;
     const int u = __ldg(&p.item_unit[t]);
+    if (lane == 0) prefetch_unit_maps(p.units[u]);  // overlaps the dependency wait
     const int dep = p.units[u].dep;
     if (dep >= 0) {
         int good = 1;
@@ -152,6 +175,7 @@ __global__ void __launch_bounds__(kThreads, min_ctas<WV>())
     __syncthreads();
 
     if (warp == kNW) {  // ------------------------------------------------------ producer
+        __shared__ FwdArgs pargs;  // the current tile's unit arguments
         int g = 0;
         bool tma_used = false;
         for (;;) {
@@ -162,9 +186,10 @@ __global__ void __launch_bounds__(kThreads, min_ctas<WV>())
                 break;
             }
             const FwdUnit& U = p.units[__ldg(&p.item_unit[t])];
-            const Tile tl = tile_of(U.a, t - U.item_begin, U.strips);
+            copy_args(&pargs, &U.a, lane);
+            const Tile tl = tile_of(pargs, t - __ldg(&U.item_begin), __ldg(&U.strips));
             const int xs = 2 * tl.qx0 - kXL;
-            tma_used |= U.a.tma != 0;
+            tma_used |= pargs.tma != 0;
             bool alive = true;
             for (int i = 0; i < tl.nrows; ++i, ++g) {
                 const int s = g % kStages;
@@ -176,7 +201,7 @@ __global__ void __launch_bounds__(kThreads, min_ctas<WV>())
                     }
                 }
                 if (lane == 0) ring.meta[s] = t;
-                fwd_produce_row<TI, kSRow / 32>(U.a, &U.tm, kAdj, tl.qfirst + i, xs,
+                fwd_produce_row<TI, kSRow / 32>(pargs, &U.tm, kAdj, tl.qfirst + i, xs,
                                     reinterpret_cast<TI*>(ring.stage(s)), &ring.full[s], lane, 0);
             }
             if (!alive) break;
@@ -190,6 +215,8 @@ __global__ void __launch_bounds__(kThreads, min_ctas<WV>())
     }
 
     // ------------------------------------------------------------------------- consumers
+    __shared__ FwdArgs wargs[kNW];  // the current tile's unit arguments, one copy per warp
+    const FwdArgs& A = wargs[warp];
     const bool store_lane = lane >= 1 && lane <= 30;
     int cur = -1, i = 0, unit = 0;
     Tile tl{};
@@ -204,17 +231,18 @@ __global__ void __launch_bounds__(kThreads, min_ctas<WV>())
         if (!__all_sync(kFull, ok)) break;
         const int t = ring.meta[s];
         if (t < 0) break;
-        const FwdUnit* U = &p.units[__ldg(&p.item_unit[t])];
         if (t != cur) {  // first row of a new tile
             cur = t;
             unit = __ldg(&p.item_unit[t]);
-            tl = tile_of(U->a, t - U->item_begin, U->strips);
+            const FwdUnit* U = &p.units[unit];
+            copy_args(&wargs[warp], &U->a, lane);
+            tl = tile_of(A, t - __ldg(&U->item_begin), __ldg(&U->strips));
             const int wq = tl.qx0 - kHQ + warp * kWarpOut;
             m0 = wq + kQ * lane;
             const int xs = 2 * tl.qx0 - kXL;
-            cols.init(2 * m0, xs, U->a.W, !kAdj, (2 * wq < 0) || (2 * wq + 2 * kWarpQ > U->a.W));
-            idle = wq + kHQ >= U->a.nec;
-            if constexpr (kAdj) hw.init(m0, AxisLen{U->a.nec, U->a.ndc});
+            cols.init(2 * m0, xs, A.W, !kAdj, (2 * wq < 0) || (2 * wq + 2 * kWarpQ > A.W));
+            idle = wq + kHQ >= A.nec;
+            if constexpr (kAdj) hw.init(m0, AxisLen{A.nec, A.ndc});
             pipe.init();
             i = 0;
         }
@@ -224,12 +252,12 @@ __global__ void __launch_bounds__(kThreads, min_ctas<WV>())
             __syncwarp();
             if (lane == 0) mbar_arrive(&ring.empty[s]);
             if constexpr (kAdj)
-                pipe.push(row, tl.qfirst + i, hw, AxisLen{U->a.ner, U->a.ndr}, U->a.scale);
+                pipe.push(row, tl.qfirst + i, hw, AxisLen{A.ner, A.ndr}, A.scale);
             else
                 pipe.push(row);
             const int qo = tl.qfirst + i - Pipe::kLag;
             if (qo >= tl.n0 && qo < tl.n1 && store_lane)
-                fwd_store_row<MODE_NONSEP, TB, TL>(U->a, row, qo, m0, 0);
+                fwd_store_row<MODE_NONSEP, TB, TL>(A, row, qo, m0, 0);
         } else if (lane == 0) {
             mbar_arrive(&ring.empty[s]);
         }
@@ -250,6 +278,7 @@ __global__ void __launch_bounds__(kThreads, min_ctas<WV>())
     __syncthreads();
 
     if (warp == kNW) {  // ------------------------------------------------------ producer
+        __shared__ InvArgs pargs;  // the current tile's unit arguments
         int g = 0;
         bool tma_used = false;
         for (;;) {
@@ -260,10 +289,11 @@ __global__ void __launch_bounds__(kThreads, min_ctas<WV>())
                 break;
             }
             const InvUnit& U = p.units[__ldg(&p.item_unit[t])];
-            const Tile tl = tile_of(U.a, t - U.item_begin, U.strips);
+            copy_args(&pargs, &U.a, lane);
+            const Tile tl = tile_of(pargs, t - __ldg(&U.item_begin), __ldg(&U.strips));
             const int xb = tl.qx0 - kXLB;
             const CUtensorMap* maps[4] = {&U.tm[0], &U.tm[1], &U.tm[2], &U.tm[3]};
-            tma_used |= U.a.tma != 0;
+            tma_used |= pargs.tma != 0;
             bool alive = true;
             for (int i = 0; i < tl.nrows; ++i, ++g) {
                 const int s = g % kStages;
@@ -275,7 +305,7 @@ __global__ void __launch_bounds__(kThreads, min_ctas<WV>())
                     }
                 }
                 if (lane == 0) ring.meta[s] = t;
-                inv_produce_row<TL, TB>(U.a, maps, ADJ, tl.qfirst + i, xb, ring.stage(s),
+                inv_produce_row<TL, TB>(pargs, maps, ADJ, tl.qfirst + i, xb, ring.stage(s),
                                         &ring.full[s], lane, 0);
             }
             if (!alive) break;
@@ -289,6 +319,8 @@ __global__ void __launch_bounds__(kThreads, min_ctas<WV>())
     }
 
     // ------------------------------------------------------------------------- consumers
+    __shared__ InvArgs wargs[kNW];  // the current tile's unit arguments, one copy per warp
+    const InvArgs& A = wargs[warp];
     const bool store_lane = lane >= 1 && lane <= 30;
     int cur = -1, i = 0, unit = 0;
     Tile tl{};
@@ -303,16 +335,17 @@ __global__ void __launch_bounds__(kThreads, min_ctas<WV>())
         if (!__all_sync(kFull, ok)) break;
         const int t = ring.meta[s];
         if (t < 0) break;
-        const InvUnit* U = &p.units[__ldg(&p.item_unit[t])];
-        if (t != cur) {
+        if (t != cur) {  // first row of a new tile
             cur = t;
             unit = __ldg(&p.item_unit[t]);
-            tl = tile_of(U->a, t - U->item_begin, U->strips);
+            const InvUnit* U = &p.units[unit];
+            copy_args(&wargs[warp], &U->a, lane);
+            tl = tile_of(A, t - __ldg(&U->item_begin), __ldg(&U->strips));
             const int wq = tl.qx0 - kHQ + warp * kWarpOut;
             m0 = wq + kQ * lane;
-            cols.init(m0, tl.qx0 - kXLB, U->a.W, !ADJ, (2 * wq < 0) || (2 * wq + 2 * kWarpQ > U->a.W));
-            idle = wq + kHQ >= U->a.nec;
-            if constexpr (ADJ) hw.init(m0, AxisLen{U->a.nec, U->a.ndc});
+            cols.init(m0, tl.qx0 - kXLB, A.W, !ADJ, (2 * wq < 0) || (2 * wq + 2 * kWarpQ > A.W));
+            idle = wq + kHQ >= A.nec;
+            if constexpr (ADJ) hw.init(m0, AxisLen{A.nec, A.ndc});
             pipe.init();
             i = 0;
         }
@@ -322,11 +355,11 @@ __global__ void __launch_bounds__(kThreads, min_ctas<WV>())
             __syncwarp();
             if (lane == 0) mbar_arrive(&ring.empty[s]);
             if constexpr (ADJ)
-                pipe.push(row, tl.qfirst + i, hw, AxisLen{U->a.ner, U->a.ndr}, U->a.scale);
+                pipe.push(row, tl.qfirst + i, hw, AxisLen{A.ner, A.ndr}, A.scale);
             else
                 pipe.push(row);
             const int qo = tl.qfirst + i - Pipe::kLag;
-            if (qo >= tl.n0 && qo < tl.n1 && store_lane) inv_store_row<TO>(U->a, row, qo, m0, 0);
+            if (qo >= tl.n0 && qo < tl.n1 && store_lane) inv_store_row<TO>(A, row, qo, m0, 0);
         } else if (lane == 0) {
             mbar_arrive(&ring.empty[s]);
         }
