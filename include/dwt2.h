@@ -272,7 +272,8 @@ int dwt2_plan_create(const dwt2_image_desc* imgs, int n, int wavelet, int levels
                      const char* tune_cache, dwt2_plan** plan);
 /* Enqueue the plan's graph on stream (asynchronous). */
 int dwt2_plan_execute(dwt2_plan* plan, void* stream);
-/* The schedule in use: quad rows per tile, CTAs per SM, number of tiles. */
+/* The schedule in use: quad rows per tile at level 1 (level j uses max(4, rows >> (j - 1))), CTAs
+ * per SM, number of tiles. */
 int dwt2_plan_info(const dwt2_plan* plan, int* rows_per_tile, int* ctas_per_sm, int* n_tiles);
 int dwt2_plan_destroy(dwt2_plan* plan);
 

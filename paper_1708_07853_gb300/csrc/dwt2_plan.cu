@@ -1,7 +1,7 @@
 // dwt2_plan.cu -- batched plans: many images (any sizes), all levels, one persistent launch.
 //
 // dwt2_plan_create builds the work list (one unit per image and level, tiles of kCtaQ quad columns
-// x rows_per_tile quad rows), the TMA tensor maps and argument blocks of every unit in plan-owned
+// x level_rows(rows_per_tile, level) quad rows), the TMA tensor maps and argument blocks of every unit in plan-owned
 // device memory, and captures [memset of the tile counters, persistent kernel] into a CUDA graph;
 // dwt2_plan_execute replays it.  rows_per_tile (and the CTAs per SM) come from an autotuner that
 // times candidates on the plan itself and keeps the winner in a text cache file, or from a
@@ -97,22 +97,28 @@ int check_plan_args(const dwt2_image_desc* imgs, int n, int wavelet, int J, int 
     return DWT2_OK;
 }
 
-// Default rows per tile: about four tiles per resident CTA over the whole batch, so that the
-// tail of the ticket queue is short, within [4, 128] quad rows.
+// Quad rows per tile at level j, for `rows` at level 1: halved at every level (a level has half
+// the rows and half the strips of the one before), at least 4.  Long tiles keep the halo small
+// on the large levels; short ones keep the tail of each level (one tile's time) short on the
+// small levels, whose completion the next level waits for.
+int level_rows(int rows, int j) { return std::max(4, rows >> (j - 1)); }
+
+// Default level-1 rows per tile: about four tiles per resident CTA over the whole batch, so that
+// the tail of the ticket queue is short, within [8, 256] quad rows.
 int default_rows(const dwt2_image_desc* imgs, int n, int J, int resident) {
     double quad_rows_x_strips = 0;
     for (int i = 0; i < n; ++i) {
         int h = imgs[i].H, w = imgs[i].W;
         for (int j = 0; j < J; ++j) {
             const int ner = (h + 1) / 2, nec = (w + 1) / 2;
-            quad_rows_x_strips += double(ner) * ((nec + kCtaQ - 1) / kCtaQ);
+            quad_rows_x_strips += double(ner) * ((nec + kCtaQ - 1) / kCtaQ) * double(1 << j);
             h = ner;
             w = nec;
         }
     }
     const double want_tiles = 4.0 * std::max(1, resident);
     const int r = int(std::ceil(quad_rows_x_strips / want_tiles));
-    return std::min(128, std::max(4, r));
+    return std::min(256, std::max(8, r));
 }
 
 // Builds the units and the ticket table for rows_per_tile; returns DWT2_OK or an error.
@@ -153,7 +159,7 @@ int build_work(dwt2_plan* P, int rows, std::vector<FwdUnit>& fu, std::vector<Inv
             const dwt2_band& blh = bands[1 + 3 * (J - j) + 1];
             const dwt2_band& bhh = bands[1 + 3 * (J - j) + 2];
             const int ner = (hh + 1) / 2, nec = (ww + 1) / 2;
-            const int rpc = std::max(1, std::min(rows, ner));
+            const int rpc = std::max(1, std::min(level_rows(rows, j), ner));
             const int strips = (nec + kCtaQ - 1) / kCtaQ;
             const int n_items = strips * ((ner + rpc - 1) / rpc);
             const int dep_level = P->fwd_flow ? j - 1 : j + 1;
@@ -343,7 +349,7 @@ bool cache_lookup(const char* path, const std::string& key, int* rows, int* ctas
 // Times each candidate (rows per tile x CTAs per SM) on the plan itself: 2 warm-up and 5 timed
 // graph replays, median; keeps the fastest.
 int autotune(dwt2_plan* P, int occ) {
-    const int rows_c[] = {4, 8, 16, 32, 64, 128};
+    const int rows_c[] = {8, 16, 32, 64, 128, 256};
     std::vector<int> ctas_c = {occ};
     if (occ > 1) ctas_c.push_back(occ - 1);
     cudaStream_t st;
