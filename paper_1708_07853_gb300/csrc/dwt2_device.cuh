@@ -110,6 +110,12 @@ __device__ __forceinline__ void cp_async_4(void* smem_dst, const void* src, bool
                  : "memory");
 }
 
+// cp.async of one 16-byte chunk (both addresses 16-byte aligned), through L2 only.
+__device__ __forceinline__ void cp_async_16(void* smem_dst, const void* src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(smem_dst)), "l"(src)
+                 : "memory");
+}
+
 // The barrier's current phase also waits for every cp.async this thread has issued so far
 // (pending count +1 now, -1 when they have landed).
 __device__ __forceinline__ void cp_async_arrive(uint64_t* bar) {

@@ -202,7 +202,8 @@ __global__ void __launch_bounds__(kThreads, min_ctas<WV>())
                 }
                 if (lane == 0) ring.meta[s] = t;
                 fwd_produce_row<TI, kSRow / 32>(pargs, &U.tm, kAdj, tl.qfirst + i, xs,
-                                    reinterpret_cast<TI*>(ring.stage(s)), &ring.full[s], lane, 0);
+                                                reinterpret_cast<TI*>(ring.stage(s)),
+                                                &ring.full[s], lane, 0, &ring.shift[s]);
             }
             if (!alive) break;
         }
@@ -248,7 +249,11 @@ __global__ void __launch_bounds__(kThreads, min_ctas<WV>())
         }
         if (!idle) {
             QRow<C> row;
-            fwd_lane_row<TI, C>(reinterpret_cast<const TI*>(ring.stage(s)), cols, row);
+            if (A.tma)
+                fwd_lane_row<TI, C>(reinterpret_cast<const TI*>(ring.stage(s)), cols, row);
+            else
+                fwd_lane_row_shifted<TI, C>(reinterpret_cast<const TI*>(ring.stage(s)), cols, row,
+                                            ring.shift[s]);
             __syncwarp();
             if (lane == 0) mbar_arrive(&ring.empty[s]);
             if constexpr (kAdj)

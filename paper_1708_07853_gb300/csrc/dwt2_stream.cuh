@@ -108,12 +108,12 @@ __device__ __forceinline__ void putN(T* p, const C (&v)[N], int c0, int width, b
 template <typename TI>
 constexpr size_t fwd_smem_bytes() {
     return size_t(kStages) * 2 * kSRow * sizeof(TI) + 2 * kStages * sizeof(uint64_t) +
-           4 * (kStages + 4) + 128;
+           4 * (2 * kStages + 4) + 128;
 }
 template <typename TL, typename TB>
 constexpr size_t inv_smem_bytes() {
     return size_t(kStages) * kBRow * (sizeof(TL) + 3 * sizeof(TB)) +
-           2 * kStages * sizeof(uint64_t) + 4 * (kStages + 4) + 128;
+           2 * kStages * sizeof(uint64_t) + 4 * (2 * kStages + 4) + 128;
 }
 
 __device__ __forceinline__ uint8_t* align128(uint8_t* p) {
@@ -128,6 +128,83 @@ __device__ __forceinline__ uint8_t* align128(uint8_t* p) {
 // TMA transaction count when the stage is filled by TMA); the empty barrier takes one arrival
 // per consumer warp.
 // =============================================================================================
+
+// Forward data flow: loads of extended quad row q (pixel rows 2q, 2q + 1) of the input plane.
+// Mirrored (whole-sample symmetric) rows for the transform; plain rows, zeros outside, for the
+// adjoint of the inverse.
+// Plain-load producer for planes TMA cannot address (pitch or base not 16-byte aligned).  Only
+// the caller's own image takes this path (every scratch plane is TMA-eligible), so nothing the
+// running kernel writes is read here.
+//   transform (mirrored rows): each row is copied as the 16-byte-aligned chunks that hold its
+//     elements xs .. xs + kSRow - 1, with 16-byte cp.async (L2 only), so the row lands shifted by
+//     the misalignment m (0 .. 16 / sizeof(TI) - 1 elements) of element xs: element c sits at
+//     stage index c - xs + m.  Chunks with no element inside the row are skipped; a chunk that
+//     straddles an end of the row reads at most 15 bytes beyond it, inside the same 16-byte
+//     block (so inside mapped memory); those stage entries are never read (the consumers read
+//     mirrored columns at the plane's edges).  The shifts go to *shift_slot (row 0 in bits 0-3,
+//     row 1 in bits 4-7).
+//   adjoint (zeros outside the plane): 4-byte zero-filling cp.async copies (16-bit elements, below
+//     cp.async's minimum, are loaded before the first shared-memory store), no shift.
+// Either way the stage's full barrier completes when the copies have landed, so up to kStages
+// stages are in flight, as with TMA.  kUnroll: 1 in the single-image kernels (their TMA path keeps
+// its instruction footprint), full in the persistent kernels.
+template <typename TI, int kUnroll>
+__device__ __forceinline__ void fwd_produce_plain(const FwdArgs& a, bool adj, int r0, int r1,
+                                                  int xs, TI* dst, uint64_t* full, int lane, int z,
+                                                  volatile int* shift_slot) {
+    const bool ok0 = r0 >= 0 && r0 < a.H, ok1 = r1 >= 0 && r1 < a.H;
+    const char* base = static_cast<const char*>(a.in) + int64_t(z) * a.in_bstride;
+    const TI* row0 = reinterpret_cast<const TI*>(base + int64_t(ok0 ? r0 : 0) * a.in_pitch);
+    const TI* row1 = reinterpret_cast<const TI*>(base + int64_t(ok1 ? r1 : 0) * a.in_pitch);
+    constexpr int kPer = kSRow / 32;
+    if (!adj) {
+        constexpr int kEpc = 16 / int(sizeof(TI));  // elements per chunk
+        constexpr int kChunks = kSRow / kEpc;
+        int sh = 0;
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+            const TI* row = r ? row1 : row0;
+            const uintptr_t first = reinterpret_cast<uintptr_t>(row) + intptr_t(xs) * intptr_t(sizeof(TI));
+            const int m = int((first & 15u) / sizeof(TI));
+            const int e0 = xs - m;  // element at the first chunk's (aligned) address
+#pragma unroll kUnroll
+            for (int k = lane; k < kChunks; k += 32) {
+                const int c0 = e0 + k * kEpc;
+                if (c0 + kEpc > 0 && c0 < a.W) cp_async_16(dst + r * kSRow + k * kEpc, row + c0);
+            }
+            sh |= m << (4 * r);
+        }
+        cp_async_arrive(full);
+        if (lane == 0) *shift_slot = sh;
+    } else if constexpr (sizeof(TI) == 4) {
+#pragma unroll kUnroll
+        for (int j = 0; j < kPer; ++j) {
+            const int k = lane + 32 * j, c = xs + k;
+            const bool in = c >= 0 && c < a.W;
+            cp_async_4(dst + k, row0 + (in ? c : 0), in && ok0);
+            cp_async_4(dst + kSRow + k, row1 + (in ? c : 0), in && ok1);
+        }
+        cp_async_arrive(full);
+        if (lane == 0) *shift_slot = 0;
+    } else {
+        TI v0[kPer], v1[kPer];
+#pragma unroll
+        for (int j = 0; j < kPer; ++j) {
+            const int c = xs + lane + 32 * j;
+            const bool in = c >= 0 && c < a.W;
+            v0[j] = (in && ok0) ? ldcg(row0 + c) : zero_of<TI>();
+            v1[j] = (in && ok1) ? ldcg(row1 + c) : zero_of<TI>();
+        }
+#pragma unroll
+        for (int j = 0; j < kPer; ++j) {
+            dst[lane + 32 * j] = v0[j];
+            dst[kSRow + lane + 32 * j] = v1[j];
+        }
+        if (lane == 0) *shift_slot = 0;
+    }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(full);
+}
 
 // Forward data flow: loads of extended quad row q (pixel rows 2q, 2q + 1) of the input plane.
 // Mirrored (whole-sample symmetric) rows for the transform; plain rows, zeros outside, for the
@@ -181,13 +258,20 @@ __device__ __forceinline__ void fwd_produce_plain(const FwdArgs& a, int r0, int 
 // Forward data flow: loads of extended quad row q (pixel rows 2q, 2q + 1) of the input plane.
 // Mirrored (whole-sample symmetric) rows for the transform; plain rows, zeros outside, for the
 // adjoint of the inverse.
-template <typename TI, int kUnrollPlain = 1>
+// Which loader a kernel instantiation contains: decided per launch from a.tma (persistent
+// kernels, whose units mix aligned and unaligned planes), or fixed at compile time (single-image
+// kernels: the launcher picks the TMA or the plain-load instantiation, so the TMA kernels carry no
+// plain-load code).
+enum Loader { LOAD_RUNTIME = 0, LOAD_TMA = 1, LOAD_PLAIN = 2 };
+
+template <typename TI, int kUnrollPlain = 1, int kLoader = LOAD_RUNTIME>
 __device__ __forceinline__ void fwd_produce_row(const FwdArgs& a, const CUtensorMap* tm, bool adj,
                                                 int q, int xs, TI* dst, uint64_t* full, int lane,
-                                                int z) {
+                                                int z, volatile int* shift_slot) {
     const int r0 = adj ? 2 * q : refl(2 * q, a.H);
     const int r1 = adj ? 2 * q + 1 : refl(2 * q + 1, a.H);
-    if (a.tma) {
+    const bool use_tma = kLoader == LOAD_TMA || (kLoader == LOAD_RUNTIME && a.tma);
+    if (kLoader != LOAD_PLAIN && use_tma) {
         if (lane == 0) {
             mbar_arrive_expect_tx(full, 2 * kSRow * sizeof(TI));
 #pragma unroll
@@ -196,8 +280,8 @@ __device__ __forceinline__ void fwd_produce_row(const FwdArgs& a, const CUtensor
                 tma_load_3d(dst + kSRow + b * kBoxW, tm, full, xs + b * kBoxW, r1, z);
             }
         }
-    } else {
-        fwd_produce_plain<TI, kUnrollPlain>(a, r0, r1, xs, dst, full, lane, z);
+    } else if constexpr (kLoader != LOAD_TMA) {
+        fwd_produce_plain<TI, kUnrollPlain>(a, adj, r0, r1, xs, dst, full, lane, z, shift_slot);
     }
 }
 
@@ -232,6 +316,28 @@ __device__ __forceinline__ void fwd_lane_row(const TI* stage, const FwdCols& col
             v0[k] = to_c(r0[cols.ec[k]]);
             v1[k] = to_c(r1[cols.ec[k]]);
         }
+    }
+#pragma unroll
+    for (int q = 0; q < kQ; ++q) {
+        row.a[q] = v0[2 * q];
+        row.b[q] = v0[2 * q + 1];
+        row.c[q] = v1[2 * q];
+        row.e[q] = v1[2 * q + 1];
+    }
+}
+
+// The same from a stage filled by the plain-load path: row r of the stage is shifted by
+// (shifts >> 4r) & 15 elements; element reads, kept inside the stage.
+template <typename TI, typename C>
+__device__ __forceinline__ void fwd_lane_row_shifted(const TI* stage, const FwdCols& cols,
+                                                     QRow<C>& row, int shifts) {
+    const int s0 = shifts & 15, s1 = (shifts >> 4) & 15;
+    C v0[2 * kQ], v1[2 * kQ];
+#pragma unroll
+    for (int k = 0; k < 2 * kQ; ++k) {
+        const int i = cols.edge ? cols.ec[k] : cols.base + k;
+        v0[k] = to_c(stage[min(i + s0, kSRow - 1)]);
+        v1[k] = to_c(stage[kSRow + min(i + s1, kSRow - 1)]);
     }
 #pragma unroll
     for (int q = 0; q < kQ; ++q) {
@@ -404,7 +510,8 @@ struct Ring {
     uint64_t* full;
     uint64_t* empty;
     volatile int* abort;
-    volatile int* meta;
+    volatile int* meta;   // per stage: the ticket of its tile (persistent kernels)
+    volatile int* shift;  // per stage: element shifts of its two rows (plain-load path)
     __device__ __forceinline__ uint8_t* stage(int s) const { return stage0 + size_t(s) * stage_bytes; }
 };
 
@@ -416,6 +523,7 @@ __device__ __forceinline__ Ring make_ring(uint8_t* smem_raw, size_t stage_bytes)
     r.empty = r.full + kStages;
     r.abort = reinterpret_cast<volatile int*>(r.empty + kStages);
     r.meta = r.abort + 1;
+    r.shift = r.meta + kStages;
     return r;
 }
 
@@ -444,7 +552,7 @@ __device__ __forceinline__ void drain_ring(const Ring& r, int issued, int* statu
 // comparator); MODE_ADJ_INV is the transpose of the inverse level; every other mode is the
 // forward level.
 // =============================================================================================
-template <int WV, int MODE, typename TI, typename TB, typename TL>
+template <int WV, int MODE, typename TI, typename TB, typename TL, bool kPlain>
 __global__ void __launch_bounds__(kThreads, min_ctas<WV>())
     k_forward(const __grid_constant__ CUtensorMap tmap, const FwdArgs args) {
     constexpr bool kAdj = MODE == MODE_ADJ_INV;
@@ -464,7 +572,7 @@ __global__ void __launch_bounds__(kThreads, min_ctas<WV>())
     const int xs = 2 * qx0 - kXL;
 
     init_ring(ring);
-    if (args.tma && warp == kNW && lane == 0) prefetch_tensormap(&tmap);
+    if (!kPlain && warp == kNW && lane == 0) prefetch_tensormap(&tmap);
     __syncthreads();
     // Everything above overlaps the previous level's tail; nothing below may touch global memory
     // before that level has finished writing this level's input (and reading what we overwrite).
@@ -479,11 +587,12 @@ __global__ void __launch_bounds__(kThreads, min_ctas<WV>())
                 bool ok = mbar_wait(&ring.empty[s], ((i / kStages) - 1) & 1, ring.abort, args.status);
                 if (!__all_sync(kFull, ok)) break;
             }
-            fwd_produce_row<TI>(args, &tmap, kAdj, qfirst + i, xs,
-                                reinterpret_cast<TI*>(ring.stage(s)), &ring.full[s], lane, z);
+            fwd_produce_row<TI, 1, kPlain ? LOAD_PLAIN : LOAD_TMA>(
+                args, &tmap, kAdj, qfirst + i, xs, reinterpret_cast<TI*>(ring.stage(s)),
+                &ring.full[s], lane, z, &ring.shift[s]);
             issued = i + 1;
         }
-        if (args.tma && lane == 0) drain_ring(ring, issued, args.status);
+        if (!kPlain && lane == 0) drain_ring(ring, issued, args.status);
         cp_async_wait_all();  // no-op unless this lane issued cp.async copies
         return;
     }
@@ -511,7 +620,11 @@ __global__ void __launch_bounds__(kThreads, min_ctas<WV>())
             continue;
         }
         QRow<C> row;
-        fwd_lane_row<TI, C>(reinterpret_cast<const TI*>(ring.stage(s)), cols, row);
+        if constexpr (kPlain)
+            fwd_lane_row_shifted<TI, C>(reinterpret_cast<const TI*>(ring.stage(s)), cols, row,
+                                        ring.shift[s]);
+        else
+            fwd_lane_row<TI, C>(reinterpret_cast<const TI*>(ring.stage(s)), cols, row);
         __syncwarp();
         if (lane == 0) mbar_arrive(&ring.empty[s]);
         if constexpr (kAdj)
@@ -686,15 +799,22 @@ int configure(K kernel, size_t smem) {
     return n;
 }
 
-template <int WV, int MODE, typename TI, typename TB, typename TL>
-cudaError_t launch_forward_t(const CUtensorMap& tm, FwdArgs a, cudaStream_t st) {
-    auto k = k_forward<WV, MODE, TI, TB, TL>;
+template <int WV, int MODE, typename TI, typename TB, typename TL, bool kPlain>
+cudaError_t launch_forward_k(const CUtensorMap& tm, FwdArgs a, cudaStream_t st) {
+    auto k = k_forward<WV, MODE, TI, TB, TL, kPlain>;
     constexpr size_t smem = fwd_smem_bytes<TI>();
     static const int occ = configure(k, smem);
     const LaunchGeom g = pick_geometry(a.ner, a.nec, int64_t(a.H) * a.W * int64_t(sizeof(TI)),
                                        device_sm_count(), occ, a.nbatch);
     a.rpc = g.rpc;
     return launch_pdl(k, g.grid, smem, st, tm, a);
+}
+
+// TMA-loading or plain-loading instantiation, by whether the input plane has a tensor map.
+template <int WV, int MODE, typename TI, typename TB, typename TL>
+cudaError_t launch_forward_t(const CUtensorMap& tm, FwdArgs a, cudaStream_t st) {
+    return a.tma ? launch_forward_k<WV, MODE, TI, TB, TL, false>(tm, a, st)
+                 : launch_forward_k<WV, MODE, TI, TB, TL, true>(tm, a, st);
 }
 
 template <int WV, typename TB, typename TL, typename TO, bool ADJ = false>
