@@ -744,7 +744,7 @@ inline LaunchGeom pick_geometry(int ner, int nec, int64_t plane_bytes, int sms, 
     const int n = std::max(1, nbatch);
     const int strips = (nec + kCtaQ - 1) / kCtaQ;
     const int64_t slots = int64_t(std::max(1, sms)) * std::max(1, ctas_per_sm);
-    const int min_rows = plane_bytes * n < (int64_t(24) << 20) ? 4 : 16;
+    const int min_rows = plane_bytes * n < (int64_t(24) << 20) ? 2 : 16;
     const int rb_max = std::max(1, (ner + min_rows - 1) / min_rows);
     int best_rb = 1;
     int64_t best = -1;
