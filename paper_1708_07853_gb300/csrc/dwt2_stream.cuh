@@ -32,6 +32,13 @@ template <int WV>
 constexpr int min_ctas() {
     return WV == 2 ? 1 : 6;
 }
+// Consumer row loop unrolled by 2 for the 5/3 wavelets: the compiler then renames the row
+// pipeline's registers instead of rotating them (int 5/3 forward 4.7% faster on GB300); the 9/7
+// kernels measured 2% slower unrolled and stay rolled.
+template <int WV>
+constexpr int row_unroll() {
+    return WV == 2 ? 1 : 2;
+}
 constexpr int kStages = 8;               // quad rows in flight per CTA
 constexpr int kVHalo = 2;                // halo quad rows above and below a CTA's rows
 
@@ -611,6 +618,7 @@ __global__ void __launch_bounds__(kThreads, min_ctas<WV>())
 
     Pipe pipe;
     pipe.init();
+#pragma unroll row_unroll<WV>()
     for (int i = 0; i < nrows; ++i) {
         const int s = i % kStages;
         bool ok = mbar_wait(&ring.full[s], (i / kStages) & 1, ring.abort, args.status);
@@ -701,6 +709,7 @@ __global__ void __launch_bounds__(kThreads, min_ctas<WV>())
 
     Pipe pipe;
     pipe.init();
+#pragma unroll row_unroll<WV>()
     for (int i = 0; i < nrows; ++i) {
         const int s = i % kStages;
         bool ok = mbar_wait(&ring.full[s], (i / kStages) & 1, ring.abort, args.status);
