@@ -67,6 +67,41 @@ __device__ __forceinline__ C step_u(C d0, C d1, float u) {
     }
 }
 
+// Packed fp32: a lane's two quads (kQ == 2) take the same arithmetic, so the inverse float
+// stages evaluate both at once with the f32x2 instructions (one add and one fma per term for the
+// pair instead of per quad); x + w (s0 + s1) rounds exactly as the scalar fused form.  Measured on
+// GB300: the 9/7 inverse 1.9% faster; the forward stages, already issue-bound with the FMA pipe
+// throttling, 1.6% slower packed, so they stay scalar.
+template <typename C>
+constexpr bool kPacked = std::is_same<C, float>::value && kQ == 2;
+__device__ __forceinline__ float2 v2(const float (&v)[kQ]) { return make_float2(v[0], v[1]); }
+__device__ __forceinline__ void put2(float (&v)[kQ], float2 x) {
+    v[0] = x.x;
+    v[1] = x.y;
+}
+__device__ __forceinline__ float2 lift2(float2 x, float2 s0, float2 s1, float2 w) {
+    return __ffma2_rn(w, __fadd2_rn(s0, s1), x);
+}
+
+// Band scaling of a row (packed: one f32x2 multiply per band for the lane's two quads); used by
+// the inverse.
+__device__ __forceinline__ void scale_row(QRow<float>& r, float sa, float sb, float sc, float se) {
+    if constexpr (kQ == 2) {
+        put2(r.a, __fmul2_rn(v2(r.a), make_float2(sa, sa)));
+        put2(r.b, __fmul2_rn(v2(r.b), make_float2(sb, sb)));
+        put2(r.c, __fmul2_rn(v2(r.c), make_float2(sc, sc)));
+        put2(r.e, __fmul2_rn(v2(r.e), make_float2(se, se)));
+    } else {
+#pragma unroll
+        for (int q = 0; q < kQ; ++q) {
+            r.a[q] *= sa;
+            r.b[q] *= sb;
+            r.c[q] *= sc;
+            r.e[q] *= se;
+        }
+    }
+}
+
 // =============================================================================================
 // Non-separable scheme (Sec. 3, Eq. 5).
 //
@@ -169,6 +204,20 @@ struct InvUpdateNS {
     __device__ __forceinline__ void push(QRow<C>& r) {
         C el[kQ], hl[kQ], hll[kQ];
         left_of(r.e, el);
+        if constexpr (kPacked<C>) {
+            const float2 w = make_float2(-u, -u);
+            const float2 e = v2(r.e), c = v2(r.c);
+            const float2 h = lift2(v2(r.b), v2(pe), e, w);
+            put2(hl, h);
+            left_of(hl, hll);
+            const float2 t = lift2(v2(r.a), v2(pc), c, w);
+            put2(r.c, lift2(c, v2(el), e, w));
+            put2(r.a, lift2(t, v2(hll), h, w));
+            put2(r.b, h);
+            put2(pc, c);
+            put2(pe, e);
+            return;
+        }
 #pragma unroll
         for (int q = 0; q < kQ; ++q) hl[q] = r.b[q] - step_u(pe[q], r.e[q], u);
         left_of(hl, hll);
@@ -203,6 +252,21 @@ struct InvPredictNS {
     }
     __device__ __forceinline__ void push(const QRow<C>& y, QRow<C>& o) {
         C c[kQ], cr[kQ];
+        if constexpr (kPacked<C>) {
+            const float2 w = make_float2(-p, -p);
+            const float2 c2 = lift2(v2(x.c), v2(x.a), v2(y.a), w);
+            put2(c, c2);
+            right_of(c, cr);
+            const float2 t = lift2(v2(x.e), v2(x.b), v2(y.b), w);
+            put2(o.b, lift2(v2(x.b), v2(x.a), v2(xar), w));
+            put2(o.e, lift2(t, c2, v2(cr), w));
+            put2(o.c, c2);
+#pragma unroll
+            for (int q = 0; q < kQ; ++q) o.a[q] = x.a[q];
+            x = y;
+            right_of(y.a, xar);
+            return;
+        }
 #pragma unroll
         for (int q = 0; q < kQ; ++q) c[q] = x.c[q] - step_p(x.a[q], y.a[q], p);
         right_of(c, cr);
@@ -657,13 +721,7 @@ struct InvPipe {
             constexpr float sLL = 1.0f / (k97Low * k97Low);
             constexpr float sHL = 1.0f / (k97Low * k97High);
             constexpr float sHH = 1.0f / (k97High * k97High);
-#pragma unroll
-            for (int q = 0; q < kQ; ++q) {
-                r.a[q] *= sLL;
-                r.b[q] *= sHL;
-                r.c[q] *= sHL;
-                r.e[q] *= sHH;
-            }
+            scale_row(r, sLL, sHL, sHL, sHH);
         }
 #pragma unroll
         for (int k = 0; k < kPairs; ++k) {
