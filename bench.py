@@ -197,6 +197,7 @@ def run_only(args, D, dev, x_f32, x_i32, flush, stream):
         "fwd_cdf53_int": ("cdf53_int", x_i32, LEVELS, False, "nonsep"),
         "inv_cdf53_int": ("cdf53_int", x_i32, LEVELS, True, "nonsep"),
         "twopass_cdf97": ("cdf97", x_f32, LEVELS, False, "sep_twopass"),
+        "sepfused_cdf97": ("cdf97", x_f32, LEVELS, False, "sep_fused"),
         "plan_cdf97": ("cdf97", x_f32, LEVELS, False, "plan"),
         "plan_cdf53_int": ("cdf53_int", x_i32, LEVELS, False, "plan"),
     }[args.only]
@@ -452,7 +453,8 @@ def main():
                          "storage against the fp64 oracle, and the time of each")
     ap.add_argument("--only", default=None,
                     choices=["fwd_l1_cdf97", "fwd_cdf97", "inv_cdf97", "fwd_cdf53_int",
-                             "inv_cdf53_int", "twopass_cdf97", "plan_cdf97", "plan_cdf53_int"],
+                             "inv_cdf53_int", "twopass_cdf97", "sepfused_cdf97", "plan_cdf97",
+                             "plan_cdf53_int"],
                     help="run one case only (for profiler captures); prints a short line")
     ap.add_argument("--levels", type=int, default=0,
                     help="with --only: decomposition levels instead of the case's own")

@@ -120,36 +120,39 @@ __device__ __forceinline__ void scale_row(QRow<float>& r, float sa, float sb, fl
 //   HH  = e + P(c) + P*(hl)    = e + p (c + c[m+1]) + p (hl + hl[n+1])
 //       ( = e + P(c) + P*(b) + PP*(a) )
 // LL is unchanged ("the predict step is completely responsible for HH", Sec. 3).
-// push(y) consumes quad row n + 1 and returns row n (lag 1); hl[n+1] is computed from the raw
-// row n + 1 when it arrives.
+// Every term reads values from before the step only.  push(y) consumes quad row n + 1 and
+// returns row n (lag 1).  The terms of a row that need nothing from the next row -- hl and the
+// partial sum t = e + P(c) -- are evaluated when the row arrives, so the state carried to the
+// next push is (a, hl, c, t): the same operations as at output time, one value fewer per quad
+// to carry than (a, c, e, hl, c[m+1]).
 template <typename C>
 struct PredictNS {
     float p;
-    QRow<C> x;
-    C xhl[kQ], xcr[kQ];
+    QRow<C> x;  // row n: a, hl (in b), c, t (in e)
     __device__ __forceinline__ void init(float p_) {
         p = p_;
         zero_row(x);
-#pragma unroll
-        for (int q = 0; q < kQ; ++q) xhl[q] = xcr[q] = C(0);
     }
     __device__ __forceinline__ void push(const QRow<C>& y, QRow<C>& o) {
-        C yar[kQ], yhl[kQ];
+        C yar[kQ], ycr[kQ];
         right_of(y.a, yar);
+        right_of(y.c, ycr);
+        QRow<C> n;  // row n + 1: a, hl, c, t
 #pragma unroll
-        for (int q = 0; q < kQ; ++q) yhl[q] = y.b[q] + step_p(y.a[q], yar[q], p);
+        for (int q = 0; q < kQ; ++q) {
+            n.a[q] = y.a[q];
+            n.b[q] = y.b[q] + step_p(y.a[q], yar[q], p);
+            n.c[q] = y.c[q];
+            n.e[q] = y.e[q] + step_p(y.c[q], ycr[q], p);
+        }
 #pragma unroll
         for (int q = 0; q < kQ; ++q) {
             o.a[q] = x.a[q];
-            o.b[q] = xhl[q];
-            o.c[q] = x.c[q] + step_p(x.a[q], y.a[q], p);
-            const C t = x.e[q] + step_p(x.c[q], xcr[q], p);
-            o.e[q] = t + step_p(xhl[q], yhl[q], p);
+            o.b[q] = x.b[q];
+            o.c[q] = x.c[q] + step_p(x.a[q], n.a[q], p);
+            o.e[q] = x.e[q] + step_p(x.b[q], n.b[q], p);
         }
-        x = y;
-#pragma unroll
-        for (int q = 0; q < kQ; ++q) xhl[q] = yhl[q];
-        right_of(y.c, xcr);
+        x = n;
     }
 };
 
