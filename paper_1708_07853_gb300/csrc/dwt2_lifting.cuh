@@ -70,8 +70,8 @@ __device__ __forceinline__ C step_u(C d0, C d1, float u) {
 // Packed fp32: a lane's two quads (kQ == 2) take the same arithmetic, so the inverse float
 // stages evaluate both at once with the f32x2 instructions (one add and one fma per term for the
 // pair instead of per quad); x + w (s0 + s1) rounds exactly as the scalar fused form.  Measured on
-// GB300: the 9/7 inverse 1.9% faster; the forward stages, already issue-bound with the FMA pipe
-// throttling, 1.6% slower packed, so they stay scalar.
+// GB300: the 9/7 inverse 1.9% faster; the forward stages 1.6% and (after the predict was
+// rescheduled) 4.4% slower packed, so they stay scalar.
 template <typename C>
 constexpr bool kPacked = std::is_same<C, float>::value && kQ == 2;
 __device__ __forceinline__ float2 v2(const float (&v)[kQ]) { return make_float2(v[0], v[1]); }
