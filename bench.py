@@ -157,6 +157,26 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------------------ reference arm
+# ------------------------------------------------------------------------------ multi-rank runs
+# With N ranks (one per GPU, under torchrun) every rank runs the whole workload on its own image:
+# replicas, since one image is not split across GPUs.  The job's time is the slowest rank's,
+# and its rate counts every rank's pixels.
+
+def max_over_ranks(ms: float, world: int, device) -> float:
+    """The largest of the ranks' times (a collective over the default process group)."""
+    if world <= 1:
+        return ms
+    import torch.distributed as dist
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank: int, world: int, ms: float) -> float:
+    """Whole-job rate in giga-units per second: all ranks' units over the slowest rank's time."""
+    return world * units_per_rank / (ms * 1e-3) / 1e9
+
+
 def run_reference(args, rank: int, world: int):
     if rank != 0:
         return
@@ -543,14 +563,11 @@ def main():
     t1 = time.time()
     clocks = sampler.summary(t0, t1)
     sampler.stop()
-    if world > 1:
-        t = torch.tensor([ms_main], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_main = float(t.item())
+    ms_main = max_over_ranks(ms_main, world, dev)
     status = D.check_status(ws97)
 
     ab = alg_bytes(H, W, LEVELS)
-    gpix_main = world * npix / (ms_main * 1e-3) / 1e9
+    gpix_main = job_rate(npix, world, ms_main)
 
     def summarise(ms, nbytes=ab):
         gbs = nbytes / (ms * 1e-3) / 1e9
@@ -601,8 +618,9 @@ def main():
         host_out.copy_(c97.buffer, non_blocking=True)
 
     e2e_steps = max(3, min(args.steps, 50))
-    ms_e2e = run_case(e2e_step, e2e_steps, 3)
-    e2e = {"value": round(world * npix / (ms_e2e * 1e-3) / 1e9, 3), "unit": "Gpixel/s",
+    barrier()
+    ms_e2e = max_over_ranks(run_case(e2e_step, e2e_steps, 3), world, dev)
+    e2e = {"value": round(job_rate(npix, world, ms_e2e), 3), "unit": "Gpixel/s",
            "h2d_bytes_per_step": host_in.numel() * host_in.element_size(),
            "d2h_bytes_per_step": host_out.numel()}
 
