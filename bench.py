@@ -608,21 +608,53 @@ def main():
                 "algorithmic_bytes_per_launch": l1_bytes, "peak_kind": peak_kind}
 
     # ---- end to end through host buffers (pinned), copies inside the timed region ----
-    host_in = torch.from_numpy(field).pin_memory()
-    host_out = torch.empty(c97.buffer.numel(), dtype=torch.uint8).pin_memory()
-    dev_in = torch.empty_like(x_f32)
+    # A caller streaming images through the public API: two buffer sets and three streams, so
+    # the upload of step k + 1 overlaps the download of step k (separate copy engines).  Each
+    # step's own host->device copy of its image, its transform and the device->host copy of its
+    # coefficients all lie inside the timed region; the rate is steps x pixels over that time.
+    host_in = [torch.from_numpy(field).pin_memory() for _ in range(2)]
+    host_out = [torch.empty(c97.buffer.numel(), dtype=torch.uint8).pin_memory() for _ in range(2)]
+    dev_in = [torch.empty_like(x_f32) for _ in range(2)]
+    cbufs = [c97, make("cdf97", x_f32)[0]]
+    wss = [ws97, D.new_workspace(D.workspace_bytes(H, W, LEVELS, "cdf97", D.DT_F32), dev)]
+    s_up, s_tf, s_down = (torch.cuda.Stream(dev) for _ in range(3))
+    ev_up, ev_tf, ev_down = ([torch.cuda.Event() for _ in range(2)] for _ in range(3))
 
-    def e2e_step():
-        dev_in.copy_(host_in, non_blocking=True)
-        D.forward(dev_in, "cdf97", LEVELS, out=c97, workspace=ws97)
-        host_out.copy_(c97.buffer, non_blocking=True)
+    def e2e_run(k):
+        start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        start.record(s_up)
+        for i in range(k):
+            b = i % 2
+            with torch.cuda.stream(s_up):
+                if i >= 2:
+                    s_up.wait_event(ev_tf[b])  # dev_in[b] is read by transform i - 2
+                dev_in[b].copy_(host_in[b], non_blocking=True)
+                ev_up[b].record(s_up)
+            s_tf.wait_event(ev_up[b])
+            if i >= 2:
+                s_tf.wait_event(ev_down[b])  # cbufs[b] is read by download i - 2
+            D.forward(dev_in[b], "cdf97", LEVELS, out=cbufs[b], workspace=wss[b], stream=s_tf)
+            ev_tf[b].record(s_tf)
+            with torch.cuda.stream(s_down):
+                s_down.wait_event(ev_tf[b])
+                host_out[b].copy_(cbufs[b].buffer, non_blocking=True)
+                ev_down[b].record(s_down)
+        end.record(s_down)
+        torch.cuda.synchronize()
+        return start.elapsed_time(end) / k
 
-    e2e_steps = max(3, min(args.steps, 50))
+    e2e_run(3)  # warm-up
+    e2e_steps = max(4, min(args.steps, 50))
     barrier()
-    ms_e2e = max_over_ranks(run_case(e2e_step, e2e_steps, 3), world, dev)
+    ms_e2e = max_over_ranks(e2e_run(e2e_steps), world, dev)
+    e2e_ok = bool(torch.equal(host_out[(e2e_steps - 1) % 2].to(dev), c97.buffer)) and \
+        D.check_status(wss[1]) == 0
     e2e = {"value": round(job_rate(npix, world, ms_e2e), 3), "unit": "Gpixel/s",
-           "h2d_bytes_per_step": host_in.numel() * host_in.element_size(),
-           "d2h_bytes_per_step": host_out.numel()}
+           "h2d_bytes_per_step": host_in[0].numel() * host_in[0].element_size(),
+           "d2h_bytes_per_step": host_out[0].numel(), "ms_per_step": round(ms_e2e, 4),
+           "pipeline": "double-buffered: upload of step k+1 overlaps download of step k",
+           "result_matches_device_run": e2e_ok}
 
     # ---- the other workloads (batched plan, autograd, reduced-precision storage) ----
     workloads = None
