@@ -609,11 +609,128 @@ static void scale_quad_f(quad_f_t* q, long h, long w, int wavelet, int divide) {
 }
 
 /* ------------------------------------------------------------------------------------------
+ * Adapted non-separable scheme (Sec. 3, Fig. 3).  With P = P0 + P1, P0 = p (the constant
+ * monomial) and P1 = p z, the spatial predict matrix of Eq. 5 factors as
+ * M_P(P) = M_P(P1) M_P(P0): every factor is one of the commuting 1-D steps d += P0 s,
+ * d += P1 s along rows and columns.  Likewise M_U(U) = M_U(U1) M_U(U0) with U0 = u, U1 = u z^-1.
+ * The M(P0), M(U0) factors read only the quad itself ("constants ... never access the results
+ * belonging to extraneous cores"); the M(P1), M(U1) factors keep the non-separable form with
+ * the neighbour at m+1 / n+1 (predict) or m-1 / n-1 (update).  On the symmetric extension the
+ * "own" sample of an update at the right end of an odd-length axis is the mirrored one, so the
+ * constant part reads index ur(m) and the neighbour part ul(m), as the plain update does.
+ * ---------------------------------------------------------------------------------------- */
+
+/* M_P(P0): [1 0 0 0; p 1 0 0; p 0 1 0; p^2 p p 1] on each quad (reads the quad only). */
+static void adapted_predict_local_f(quad_f_t* q, double p) {
+    geom_t g = q->g;
+    quad_f_t o = {g, dup_f(q->a, g.ner * g.nec), dup_f(q->b, g.ner * g.ndc),
+                  dup_f(q->c, g.ndr * g.nec), dup_f(q->e, g.ndr * g.ndc)};
+    for (long n = 0; n < g.ner; ++n)
+        for (long m = 0; m < g.ndc; ++m) B_(q, n, m) = B_(&o, n, m) + p * A_(&o, n, m);
+    for (long n = 0; n < g.ndr; ++n)
+        for (long m = 0; m < g.nec; ++m) C_(q, n, m) = C_(&o, n, m) + p * A_(&o, n, m);
+    for (long n = 0; n < g.ndr; ++n)
+        for (long m = 0; m < g.ndc; ++m)
+            E_(q, n, m) = E_(&o, n, m) + p * C_(&o, n, m) + p * B_(&o, n, m) +
+                          p * p * A_(&o, n, m);
+    free(o.a); free(o.b); free(o.c); free(o.e);
+}
+
+/* M_P(P1): [1 0 0 0; pz 1 0 0; pz_n 0 1 0; p^2 z z_n, pz_n, pz, 1] (neighbours m+1, n+1). */
+static void adapted_predict_fused_f(quad_f_t* q, double p) {
+    geom_t g = q->g;
+    quad_f_t o = {g, dup_f(q->a, g.ner * g.nec), dup_f(q->b, g.ner * g.ndc),
+                  dup_f(q->c, g.ndr * g.nec), dup_f(q->e, g.ndr * g.ndc)};
+    for (long n = 0; n < g.ner; ++n)
+        for (long m = 0; m < g.ndc; ++m)
+            B_(q, n, m) = B_(&o, n, m) + p * A_(&o, n, pr_(m, g.nec));
+    for (long n = 0; n < g.ndr; ++n)
+        for (long m = 0; m < g.nec; ++m)
+            C_(q, n, m) = C_(&o, n, m) + p * A_(&o, pr_(n, g.ner), m);
+    for (long n = 0; n < g.ndr; ++n)
+        for (long m = 0; m < g.ndc; ++m) {
+            long m1 = pr_(m, g.nec), n1 = pr_(n, g.ner);
+            E_(q, n, m) = E_(&o, n, m) + p * p * A_(&o, n1, m1) + p * B_(&o, n1, m) +
+                          p * C_(&o, n, m1);
+        }
+    free(o.a); free(o.b); free(o.c); free(o.e);
+}
+
+/* M_U(U0): [1 u u u^2; 0 1 0 u; 0 0 1 u; 0 0 0 1] on each quad (own samples of the extension). */
+static void adapted_update_local_f(quad_f_t* q, double u) {
+    geom_t g = q->g;
+    quad_f_t o = {g, dup_f(q->a, g.ner * g.nec), dup_f(q->b, g.ner * g.ndc),
+                  dup_f(q->c, g.ndr * g.nec), dup_f(q->e, g.ndr * g.ndc)};
+    for (long n = 0; n < g.ner; ++n)
+        for (long m = 0; m < g.nec; ++m) {
+            double v = A_(&o, n, m);
+            long mr = ur_(m, g.ndc), nr = ur_(n, g.ndr);
+            if (g.ndc) v += u * B_(&o, n, mr);
+            if (g.ndr) v += u * C_(&o, nr, m);
+            if (g.ndr && g.ndc) v += u * u * E_(&o, nr, mr);
+            A_(q, n, m) = v;
+        }
+    if (g.ndr)
+        for (long n = 0; n < g.ner; ++n)
+            for (long m = 0; m < g.ndc; ++m)
+                B_(q, n, m) = B_(&o, n, m) + u * E_(&o, ur_(n, g.ndr), m);
+    if (g.ndc)
+        for (long n = 0; n < g.ndr; ++n)
+            for (long m = 0; m < g.nec; ++m)
+                C_(q, n, m) = C_(&o, n, m) + u * E_(&o, n, ur_(m, g.ndc));
+    free(o.a); free(o.b); free(o.c); free(o.e);
+}
+
+/* M_U(U1): [1 uz^-1 uz_n^-1 u^2 z^-1 z_n^-1; 0 1 0 uz_n^-1; 0 0 1 uz^-1; 0 0 0 1]. */
+static void adapted_update_fused_f(quad_f_t* q, double u) {
+    geom_t g = q->g;
+    quad_f_t o = {g, dup_f(q->a, g.ner * g.nec), dup_f(q->b, g.ner * g.ndc),
+                  dup_f(q->c, g.ndr * g.nec), dup_f(q->e, g.ndr * g.ndc)};
+    for (long n = 0; n < g.ner; ++n)
+        for (long m = 0; m < g.nec; ++m) {
+            double v = A_(&o, n, m);
+            long ml = ul_(m), nl = ul_(n);
+            if (g.ndc) v += u * B_(&o, n, ml);
+            if (g.ndr) v += u * C_(&o, nl, m);
+            if (g.ndr && g.ndc) v += u * u * E_(&o, nl, ml);
+            A_(q, n, m) = v;
+        }
+    if (g.ndr)
+        for (long n = 0; n < g.ner; ++n)
+            for (long m = 0; m < g.ndc; ++m) B_(q, n, m) = B_(&o, n, m) + u * E_(&o, ul_(n), m);
+    if (g.ndc)
+        for (long n = 0; n < g.ndr; ++n)
+            for (long m = 0; m < g.nec; ++m) C_(q, n, m) = C_(&o, n, m) + u * E_(&o, n, ul_(m));
+    free(o.a); free(o.b); free(o.c); free(o.e);
+}
+
+/* The k-th step of one adapted level: local predict, fused predict, local update, fused
+ * update, for each lifting pair in turn. */
+static void adapted_step_f(quad_f_t* q, const lifting_t* L, int k) {
+    const int pair = k / 4;
+    switch (k % 4) {
+    case 0: adapted_predict_local_f(q, L->p[pair]); break;
+    case 1: adapted_predict_fused_f(q, L->p[pair]); break;
+    case 2: adapted_update_local_f(q, L->u[pair]); break;
+    default: adapted_update_fused_f(q, L->u[pair]); break;
+    }
+}
+
+/* ------------------------------------------------------------------------------------------
  * One level in each direction, for every scheme.  x is the interleaved h x w plane of LL_{j-1};
  * the four outputs are dense band arrays.
  * ---------------------------------------------------------------------------------------- */
 static int level_fwd_f(const double* x, long h, long w, int wavelet, int scheme, int ext,
                        double* LL, double* HL, double* LH, double* HH) {
+    if (scheme == ORC_ADAPTED) {
+        lifting_t L;
+        if (get_lifting(wavelet, &L)) return -1;
+        quad_f_t q = {geom_of(h, w), LL, HL, LH, HH};
+        split_f(x, h, w, ORC_CDF53, LL, HL, LH, HH); /* plain split, no scaling */
+        for (int k = 0; k < 4 * L.npairs; ++k) adapted_step_f(&q, &L, k);
+        scale_quad_f(&q, h, w, wavelet, 0);
+        return 0;
+    }
     if (scheme == ORC_NONSEP_EQ5) {
         lifting_t L;
         if (get_lifting(wavelet, &L)) return -1;
@@ -784,12 +901,19 @@ static int valid_scheme(int wavelet, int scheme) {
     return scheme >= ORC_SEP_EQ3 && scheme <= ORC_NONSEP_EQ5;
 }
 
+/* The adapted scheme is defined for the float wavelets' forward transform (its constant /
+ * neighbour split of a floor term would change the integer result). */
+static int valid_forward_scheme(int wavelet, int scheme) {
+    if (scheme == ORC_ADAPTED) return wavelet == ORC_CDF53 || wavelet == ORC_CDF97;
+    return valid_scheme(wavelet, scheme);
+}
+
 int orc_forward(const void* img, int H, int W, int wavelet, int levels, int scheme,
                 int extension_form, void* out) {
     layout_t Lo;
-    if (!img || !out || !valid_scheme(wavelet, scheme) || make_layout(H, W, levels, &Lo))
+    if (!img || !out || !valid_forward_scheme(wavelet, scheme) || make_layout(H, W, levels, &Lo))
         return -1;
-    if (extension_form && scheme == ORC_NONSEP_EQ5) return -1;
+    if (extension_form && (scheme == ORC_NONSEP_EQ5 || scheme == ORC_ADAPTED)) return -1;
     long n0 = (long)H * W;
     if (wavelet == ORC_CDF53_INT) {
         int64_t* cur = dup_i((const int64_t*)img, n0);
@@ -920,5 +1044,36 @@ int orc_nonsep_steps(const double* img, int H, int W, int wavelet, int nsteps, d
         if (k % 2 == 0) nonsep_predict_f(&q, L.p[k / 2]);
         else nonsep_update_f(&q, L.u[k / 2]);
     }
+    return 0;
+}
+
+int orc_adapted_steps(const double* img, int H, int W, int wavelet, int nsteps, double* out) {
+    lifting_t L;
+    if (!img || !out || H < 1 || W < 1 || wavelet == ORC_CDF53_INT || get_lifting(wavelet, &L) ||
+        nsteps < 0 || nsteps > 4 * L.npairs)
+        return -1;
+    geom_t g = geom_of(H, W);
+    double* a = out;
+    double* b = a + g.ner * g.nec;
+    double* c = b + g.ner * g.ndc;
+    double* e = c + g.ndr * g.nec;
+    quad_f_t q = {g, a, b, c, e};
+    split_f(img, H, W, ORC_CDF53, a, b, c, e);
+    for (int k = 0; k < nsteps; ++k) adapted_step_f(&q, &L, k);
+    return 0;
+}
+
+int orc_adapted_apply(double* abce, int H, int W, int wavelet, int k0, int k1) {
+    lifting_t L;
+    if (!abce || H < 1 || W < 1 || wavelet == ORC_CDF53_INT || get_lifting(wavelet, &L) ||
+        k0 < 0 || k1 < k0 || k1 > 4 * L.npairs)
+        return -1;
+    geom_t g = geom_of(H, W);
+    double* a = abce;
+    double* b = a + g.ner * g.nec;
+    double* c = b + g.ner * g.ndc;
+    double* e = c + g.ndr * g.nec;
+    quad_f_t q = {g, a, b, c, e};
+    for (int k = k0; k < k1; ++k) adapted_step_f(&q, &L, k);
     return 0;
 }

@@ -35,9 +35,13 @@ enum { ORC_CDF53_INT = 0, ORC_CDF53 = 1, ORC_CDF97 = 2 };
  *   ORC_SEP_ROWS     the whole 1-D transform along rows, then along columns
  *   ORC_SEP_COLS     the whole 1-D transform along columns, then along rows
  *   ORC_NONSEP_EQ5   fused spatial predict / spatial update steps (Eq. 5)
+ *   ORC_ADAPTED      the adapted non-separable scheme (Sec. 3, Fig. 3): P = P0 + P1 and
+ *                    U = U0 + U1 with P0, U0 the constant monomials; each spatial step of Eq. 5
+ *                    becomes a local step with the constants (no neighbouring quad is read)
+ *                    followed by the fused step with P1, U1.  Float wavelets, forward only.
  * For the integer wavelet only ORC_SEP_EQ3 and ORC_NONSEP_EQ5 are the contract (they agree
  * bit for bit); the other orders round differently. */
-enum { ORC_SEP_EQ3 = 0, ORC_SEP_ROWS = 1, ORC_SEP_COLS = 2, ORC_NONSEP_EQ5 = 3 };
+enum { ORC_SEP_EQ3 = 0, ORC_SEP_ROWS = 1, ORC_SEP_COLS = 2, ORC_NONSEP_EQ5 = 3, ORC_ADAPTED = 4 };
 
 /* Boundary evaluation for the separable schemes:
  *   0: single whole-sample reflection inside each lifting step (x[-1] = x[1], x[N] = x[N-2]);
@@ -66,6 +70,13 @@ int orc_inverse_adjoint(const double* g_img, int H, int W, int wavelet, int leve
  * level, without the 9/7 scaling; out receives the four polyphase components a (LL), b (HL),
  * c (LH), e (HH) densely, in that order.  Used to check which components each step writes. */
 int orc_nonsep_steps(const double* img, int H, int W, int wavelet, int nsteps, double* out);
+
+/* The same for the adapted scheme: steps in order local predict (P0), fused predict (P1),
+ * local update (U0), fused update (U1), ... of one level, without the 9/7 scaling. */
+int orc_adapted_steps(const double* img, int H, int W, int wavelet, int nsteps, double* out);
+/* Applies adapted steps k0 .. k1-1 (numbered as above) in place to polyphase components given
+ * densely in abce (a, b, c, e of an H x W level, the layout orc_adapted_steps writes). */
+int orc_adapted_apply(double* abce, int H, int W, int wavelet, int k0, int k1);
 
 #ifdef __cplusplus
 }

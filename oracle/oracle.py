@@ -20,7 +20,7 @@ _SRC = os.path.join(_HERE, "dwt2_oracle.c")
 _LIB = os.path.join(_HERE, "liboracle.so")
 
 WAVELETS = {"cdf53_int": 0, "cdf53": 1, "cdf97": 2}
-SCHEMES = {"eq3": 0, "rows": 1, "cols": 2, "eq5": 3}
+SCHEMES = {"eq3": 0, "rows": 1, "cols": 2, "eq5": 3, "adapted": 4}
 
 
 def build(force: bool = False) -> str:
@@ -53,8 +53,10 @@ def _load():
         lib.orc_forward_adjoint.argtypes = [vp, i, i, i, i, vp]
         lib.orc_inverse_adjoint.argtypes = [vp, i, i, i, i, vp]
         lib.orc_nonsep_steps.argtypes = [vp, i, i, i, i, vp]
+        lib.orc_adapted_steps.argtypes = [vp, i, i, i, i, vp]
+        lib.orc_adapted_apply.argtypes = [vp, i, i, i, i, i]
         for f in ("orc_forward", "orc_inverse", "orc_forward_adjoint", "orc_inverse_adjoint",
-                  "orc_nonsep_steps"):
+                  "orc_nonsep_steps", "orc_adapted_steps", "orc_adapted_apply"):
             getattr(lib, f).restype = i
         _lib = lib
     return _lib
@@ -151,19 +153,36 @@ def inverse_adjoint(g_img, wavelet, levels: int):
     return split_bands(out, H, W, levels)
 
 
-def nonsep_steps(img, wavelet, nsteps: int):
-    """The first nsteps fused steps of Eq. 5 on one level (no scaling): returns (a, b, c, e),
-    the LL, HL, LH, HH polyphase components after those steps."""
+def nonsep_steps(img, wavelet, nsteps: int, adapted: bool = False):
+    """The first nsteps steps of one level (no scaling): returns (a, b, c, e), the LL, HL, LH,
+    HH polyphase components after those steps.  Eq. 5's fused steps (predict, update, ...), or
+    with adapted=True the adapted scheme's (local predict, fused predict, local update, fused
+    update, ...)."""
     img = np.ascontiguousarray(img, dtype=np.float64)
     H, W = img.shape
     ner, ndr, nec, ndc = (H + 1) // 2, H // 2, (W + 1) // 2, W // 2
     out = np.zeros(ner * nec + ner * ndc + ndr * nec + ndr * ndc)
-    rc = _load().orc_nonsep_steps(_ptr(img), H, W, _wid(wavelet), nsteps, _ptr(out))
+    fn = _load().orc_adapted_steps if adapted else _load().orc_nonsep_steps
+    rc = fn(_ptr(img), H, W, _wid(wavelet), nsteps, _ptr(out))
     if rc:
-        raise ValueError(f"orc_nonsep_steps failed ({rc})")
+        raise ValueError(f"oracle step function failed ({rc})")
     shapes = [(ner, nec), (ner, ndc), (ndr, nec), (ndr, ndc)]
     res, o = [], 0
     for h, w in shapes:
         res.append(out[o:o + h * w].reshape(h, w))
         o += h * w
     return res
+
+
+def adapted_apply(parts, H: int, W: int, wavelet, k0: int, k1: int):
+    """Adapted steps k0 .. k1-1 applied to the polyphase components parts = (a, b, c, e) of an
+    H x W level; returns the new (a, b, c, e)."""
+    flat = np.concatenate([np.ascontiguousarray(p, dtype=np.float64).ravel() for p in parts])
+    rc = _load().orc_adapted_apply(_ptr(flat), H, W, _wid(wavelet), k0, k1)
+    if rc:
+        raise ValueError(f"orc_adapted_apply failed ({rc})")
+    out, o = [], 0
+    for p in parts:
+        out.append(flat[o:o + p.size].reshape(p.shape))
+        o += p.size
+    return out

@@ -170,6 +170,47 @@ def test_nonseparable_equals_separable():
                 assert max((np.abs(p - q).max() if p.size else 0) for p, q in zip(a, b)) < 1e-12
 
 
+def test_adapted_scheme_equals_separable():
+    """Sec. 3's adapted scheme splits P = P0 + P1, U = U0 + U1; each spatial step factors into a
+    local step with the constants and a fused step with the rest, so the level is the same
+    linear map as Eq. 3's: within fp64 rounding, every size (odd, length 1) and level count."""
+    rng = np.random.default_rng(32)
+    for H in SIZES:
+        for W in SIZES:
+            lv = O.max_levels(H, W)
+            xf = rng.standard_normal((H, W))
+            for wv in ("cdf53", "cdf97"):
+                a = O.forward(xf, wv, lv, "eq3")
+                b = O.forward(xf, wv, lv, "adapted")
+                assert max((np.abs(p - q).max() if p.size else 0) for p, q in zip(a, b)) < 1e-12
+    with pytest.raises(ValueError):  # no integer form: the split would change the floors
+        O.forward(rng.integers(0, 9, (8, 8)), "cdf53_int", 1, "adapted")
+
+
+@pytest.mark.parametrize("wavelet", ["cdf53", "cdf97"])
+def test_adapted_local_steps_read_no_neighbours(wavelet):
+    """Sec. 3: the detached constant parts never access results of other quads.  Perturbing one
+    quad before a local step (predict or update, every lifting pair) changes that quad only;
+    before a fused step it reaches the neighbours."""
+    rng = np.random.default_rng(33)
+    H, W = 14, 18
+    ner, ndr, nec, ndc = 7, 7, 9, 9
+    shapes = [(ner, nec), (ner, ndc), (ndr, nec), (ndr, ndc)]
+    nsteps = 8 if wavelet == "cdf97" else 4
+    for k in range(nsteps):
+        base = [rng.standard_normal(s) for s in shapes]
+        pert = [p.copy() for p in base]
+        for p in pert:
+            p[3, 4] += 1.0
+        d = [q - p for p, q in zip(O.adapted_apply(base, H, W, wavelet, k, k + 1),
+                                   O.adapted_apply(pert, H, W, wavelet, k, k + 1))]
+        changed_elsewhere = max(float(np.abs(x).sum() - abs(x[3, 4])) for x in d)
+        if k % 2 == 0:  # local step
+            assert changed_elsewhere < 1e-12, (k, changed_elsewhere)
+        else:           # fused step: the perturbation reaches a neighbour
+            assert changed_elsewhere > 1e-6, k
+
+
 def test_extension_form_equals_in_step_reflection():
     """Whole-sample symmetric extension defined on the signal (extend, lift, crop) equals the
     reflection rule applied inside each lifting step."""
