@@ -218,6 +218,7 @@ def run_only(args, D, dev, x_f32, x_i32, flush, stream):
         "inv_cdf53_int": ("cdf53_int", x_i32, LEVELS, True, "nonsep"),
         "twopass_cdf97": ("cdf97", x_f32, LEVELS, False, "sep_twopass"),
         "sepfused_cdf97": ("cdf97", x_f32, LEVELS, False, "sep_fused"),
+        "adapted_cdf97": ("cdf97", x_f32, LEVELS, False, "adapted"),
         "plan_cdf97": ("cdf97", x_f32, LEVELS, False, "plan"),
         "plan_cdf53_int": ("cdf53_int", x_i32, LEVELS, False, "plan"),
     }[args.only]
@@ -473,8 +474,8 @@ def main():
                          "storage against the fp64 oracle, and the time of each")
     ap.add_argument("--only", default=None,
                     choices=["fwd_l1_cdf97", "fwd_cdf97", "inv_cdf97", "fwd_cdf53_int",
-                             "inv_cdf53_int", "twopass_cdf97", "sepfused_cdf97", "plan_cdf97",
-                             "plan_cdf53_int"],
+                             "inv_cdf53_int", "twopass_cdf97", "sepfused_cdf97", "adapted_cdf97",
+                             "plan_cdf97", "plan_cdf53_int"],
                     help="run one case only (for profiler captures); prints a short line")
     ap.add_argument("--levels", type=int, default=0,
                     help="with --only: decomposition levels instead of the case's own")
@@ -594,6 +595,11 @@ def main():
             ms = run_case(lambda: D.forward(x, wv, LEVELS, scheme=scheme, out=c, workspace=ws),
                           args.steps, args.warmup)
             cases[f"fwd_{wv}_{scheme}"] = summarise(ms)
+    # the adapted non-separable scheme (Sec. 3; float wavelets): the ablation of its split
+    c, ws, _ = make("cdf97", x_f32, "adapted")
+    cases["fwd_cdf97_adapted"] = summarise(run_case(
+        lambda: D.forward(x_f32, "cdf97", LEVELS, scheme="adapted", out=c, workspace=ws),
+        args.steps, args.warmup))
     correct_inv = bool(torch.equal(D.inverse(ci, out=out_i, workspace=wsi), x_i32))
 
     # ---- dominant kernel: the level-1 forward launch (one launch = one 1-level transform) ----

@@ -88,11 +88,16 @@ typedef enum {
  *                            horizontal lifting steps) and then a column kernel (all vertical
  *                            ones), two HBM round trips per level.  For the integer wavelet
  *                            this rounds in rows-then-columns order, which differs from Eq. 3's
- *                            order in the last bits of some coefficients. */
+ *                            order in the last bits of some coefficients.
+ *   DWT2_SCHEME_ADAPTED      the adapted non-separable scheme (Sec. 3, Fig. 3): P = P0 + P1,
+ *                            U = U0 + U1 with the constant monomials P0, U0 applied as local
+ *                            steps (no neighbouring quad read) before the fused steps with P1,
+ *                            U1.  Float wavelets only (DWT2_EUNSUPPORTED for the integer one). */
 typedef enum {
     DWT2_SCHEME_NONSEP = 0,
     DWT2_SCHEME_SEP_FUSED = 1,
-    DWT2_SCHEME_SEP_TWOPASS = 2
+    DWT2_SCHEME_SEP_TWOPASS = 2,
+    DWT2_SCHEME_ADAPTED = 3
 } dwt2_scheme;
 
 /* One subband plane inside the caller's coefficient buffer. */

@@ -275,8 +275,10 @@ static int forward_impl(const void* img, int64_t img_pitch, int H, int W, int im
     if (rc) return rc;
     if (adjoint && (wavelet == WV_CDF53_INT || img_dtype != DT_F32 || band_dtype != DT_F32))
         return DWT2_EUNSUPPORTED;
-    if (scheme < DWT2_SCHEME_NONSEP || scheme > DWT2_SCHEME_SEP_TWOPASS) return DWT2_EINVAL;
+    if (scheme < DWT2_SCHEME_NONSEP || scheme > DWT2_SCHEME_ADAPTED) return DWT2_EINVAL;
     if (scheme != DWT2_SCHEME_NONSEP && (img_dtype != band_dtype || bt.N != 1))
+        return DWT2_EUNSUPPORTED;
+    if (scheme == DWT2_SCHEME_ADAPTED && (wavelet == WV_CDF53_INT || adjoint))
         return DWT2_EUNSUPPORTED;
     Layout L;
     if ((rc = make_layout(H, W, J, band_dtype, &L))) return rc;
@@ -332,7 +334,9 @@ static int forward_impl(const void* img, int64_t img_pitch, int H, int W, int im
             const MapResult mr = make_map(&tm, in, in_pitch, in_bstride, h, w, bt.N, in_dt, kBoxW);
             if (mr == MAP_ERROR) return DWT2_EINTERNAL;
             const bool tma = mr == MAP_OK;
-            const int mode = scheme == DWT2_SCHEME_NONSEP ? MODE_NONSEP : MODE_SEP;
+            const int mode = scheme == DWT2_SCHEME_NONSEP    ? MODE_NONSEP
+                             : scheme == DWT2_SCHEME_ADAPTED ? MODE_ADAPTED
+                                                             : MODE_SEP;
             if (adjoint) {
                 a.scale = reciprocal(level_scale(wavelet, h, w));
                 a.tma = tma ? 1 : 0;
@@ -547,7 +551,7 @@ DWT2_EXPORT size_t dwt2_workspace_bytes_scheme(int H, int W, int levels, int wav
                                                int band_dtype, int scheme) {
     Layout L;
     if (make_layout(H, W, levels, band_dtype, &L) || wavelet < 0 || wavelet > 2 ||
-        scheme < DWT2_SCHEME_NONSEP || scheme > DWT2_SCHEME_SEP_TWOPASS)
+        scheme < DWT2_SCHEME_NONSEP || scheme > DWT2_SCHEME_ADAPTED)
         return 0;
     return size_t(plan_workspace(H, W, levels, wavelet, scheme).bytes);
 }

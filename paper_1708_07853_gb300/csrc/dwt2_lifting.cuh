@@ -23,7 +23,14 @@ namespace dwt2 {
 constexpr int kQ = 2;  // polyphase quads per lane (adjacent along a row)
 
 enum Wavelet { WV_CDF53_INT = 0, WV_CDF53 = 1, WV_CDF97 = 2 };
-enum Mode { MODE_NONSEP = 0, MODE_SEP = 1, MODE_ROWS = 2, MODE_COLS = 3, MODE_ADJ_INV = 4 };
+enum Mode {
+    MODE_NONSEP = 0,
+    MODE_SEP = 1,
+    MODE_ROWS = 2,
+    MODE_COLS = 3,
+    MODE_ADJ_INV = 4,
+    MODE_ADAPTED = 5
+};
 
 // CDF 9/7 lifting constants and the per-axis normalisation (low * 1/K, high * K/2).
 constexpr float k97Alpha = -1.586134342059924f;
@@ -283,6 +290,94 @@ struct InvPredictNS {
         }
         x = y;
         right_of(y.a, xar);
+    }
+};
+
+// =============================================================================================
+// Adapted non-separable scheme (Sec. 3, Fig. 3), float wavelets.  P = P0 + P1 with P0 = p (the
+// constant monomial) and P1 = p z, U = U0 + U1 with U0 = u and U1 = u z^-1; each spatial step
+// of Eq. 5 is evaluated as a local step with the constants (no other quad is read), then the
+// fused step with P1 / U1:
+//   M_P(P) = M_P(P1) M_P(P0),  M_P(P0) = [1 0 0 0; p 1 0 0; p 0 1 0; p^2 p p 1],
+//   M_U(U) = M_U(U1) M_U(U0),  M_U(U0) = [1 u u u^2; 0 1 0 u; 0 0 1 u; 0 0 0 1].
+// The same linear map as the plain scheme; fp32 rounding differs.
+// =============================================================================================
+
+// Local predict on arrival, then the fused P1 step one row later (lag 1):
+//   b' = b + p a,  c' = c + p a,  e' = e + p c + p b + p^2 a            (quad only)
+//   HL = b' + p a[m+1],  LH = c' + p a[n+1],
+//   HH = e' + p^2 a[n+1][m+1] + p b'[n+1] + p c'[m+1]
+struct AdaptedPredict {
+    float p, pp;
+    QRow<float> x;        // row n: a, b', c', e'
+    float xar[kQ], xcr[kQ];  // row n: a[m+1], c'[m+1]
+    __device__ __forceinline__ void init(float p_) {
+        p = p_;
+        pp = p_ * p_;
+        zero_row(x);
+#pragma unroll
+        for (int q = 0; q < kQ; ++q) xar[q] = xcr[q] = 0.f;
+    }
+    __device__ __forceinline__ void push(const QRow<float>& y, QRow<float>& o) {
+        QRow<float> n;  // row n + 1 after the local step
+#pragma unroll
+        for (int q = 0; q < kQ; ++q) {
+            n.a[q] = y.a[q];
+            n.b[q] = fmaf(p, y.a[q], y.b[q]);
+            n.c[q] = fmaf(p, y.a[q], y.c[q]);
+            n.e[q] = fmaf(pp, y.a[q], fmaf(p, y.b[q], fmaf(p, y.c[q], y.e[q])));
+        }
+        float yar[kQ], ycr[kQ];
+        right_of(y.a, yar);
+        right_of(n.c, ycr);
+#pragma unroll
+        for (int q = 0; q < kQ; ++q) {
+            o.a[q] = x.a[q];
+            o.b[q] = fmaf(p, xar[q], x.b[q]);
+            o.c[q] = fmaf(p, n.a[q], x.c[q]);
+            o.e[q] = fmaf(p, xcr[q], fmaf(p, n.b[q], fmaf(pp, yar[q], x.e[q])));
+        }
+        x = n;
+#pragma unroll
+        for (int q = 0; q < kQ; ++q) {
+            xar[q] = yar[q];
+            xcr[q] = ycr[q];
+        }
+    }
+};
+
+// Local update, then the fused U1 step, both on the row as it arrives (lag 0):
+//   a' = a + u b + u c + u^2 e,  b' = b + u e,  c' = c + u e            (quad only)
+//   LL = a' + u b'[m-1] + u c'[n-1] + u^2 e[n-1][m-1],  HL = b' + u e[n-1],  LH = c' + u e[m-1]
+struct AdaptedUpdate {
+    float u, uu;
+    float pc[kQ], pe[kQ], pel[kQ];  // row n - 1: c', e, e[m-1]
+    __device__ __forceinline__ void init(float u_) {
+        u = u_;
+        uu = u_ * u_;
+#pragma unroll
+        for (int q = 0; q < kQ; ++q) pc[q] = pe[q] = pel[q] = 0.f;
+    }
+    __device__ __forceinline__ void push(QRow<float>& r) {
+        float a[kQ], b[kQ], c[kQ];
+#pragma unroll
+        for (int q = 0; q < kQ; ++q) {
+            a[q] = fmaf(uu, r.e[q], fmaf(u, r.c[q], fmaf(u, r.b[q], r.a[q])));
+            b[q] = fmaf(u, r.e[q], r.b[q]);
+            c[q] = fmaf(u, r.e[q], r.c[q]);
+        }
+        float bl[kQ], el[kQ];
+        left_of(b, bl);
+        left_of(r.e, el);
+#pragma unroll
+        for (int q = 0; q < kQ; ++q) {
+            r.a[q] = fmaf(uu, pel[q], fmaf(u, pc[q], fmaf(u, bl[q], a[q])));
+            r.b[q] = fmaf(u, pe[q], b[q]);
+            r.c[q] = fmaf(u, el[q], c[q]);
+            pc[q] = c[q];
+            pe[q] = r.e[q];
+            pel[q] = el[q];
+        }
     }
 };
 
@@ -660,6 +755,8 @@ struct FwdPipe {
     UpdateSep<float> us[kPairs];
     PredictCol<float> pcol[kPairs];
     UpdateCol<float> ucol[kPairs];
+    AdaptedPredict pa[kPairs];
+    AdaptedUpdate ua[kPairs];
     __device__ __forceinline__ void init() {
         const float P[kQ] = {WV == WV_CDF97 ? k97Alpha : -0.5f, k97Gamma};
         const float U[kQ] = {WV == WV_CDF97 ? k97Beta : 0.25f, k97Delta};
@@ -668,6 +765,7 @@ struct FwdPipe {
             if constexpr (MODE == MODE_NONSEP) { pn[k].init(P[k]); un[k].init(U[k]); }
             if constexpr (MODE == MODE_SEP) { ps[k].init(P[k]); us[k].init(U[k]); }
             if constexpr (MODE == MODE_COLS) { pcol[k].init(P[k]); ucol[k].init(U[k]); }
+            if constexpr (MODE == MODE_ADAPTED) { pa[k].init(P[k]); ua[k].init(U[k]); }
         }
     }
     __device__ __forceinline__ void push(QRow<float>& r) {
@@ -681,6 +779,7 @@ struct FwdPipe {
                 if constexpr (MODE == MODE_NONSEP) { pn[k].push(r, t); un[k].push(t); }
                 if constexpr (MODE == MODE_SEP) { ps[k].push(r, t); us[k].push(t); }
                 if constexpr (MODE == MODE_COLS) { pcol[k].push(r, t); ucol[k].push(t); }
+                if constexpr (MODE == MODE_ADAPTED) { pa[k].push(r, t); ua[k].push(t); }
                 r = t;
             }
             if constexpr (WV == WV_CDF97) {

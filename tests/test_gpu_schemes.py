@@ -4,7 +4,9 @@ DWT2_SCHEME_SEP_FUSED evaluates P, P*, U, U* one after the other in a single pas
 integer wavelet it rounds in Eq. 3's order and is bit-exact with the oracle's Eq. 3 scheme.
 DWT2_SCHEME_SEP_TWOPASS runs all row steps, then all column steps (two kernels per level): for
 the integer wavelet it is bit-exact with the oracle's rows-then-columns order instead.  Float
-results meet the same 1e-3 bound as the non-separable path.
+results meet the same 1e-3 bound as the non-separable path.  DWT2_SCHEME_ADAPTED (Sec. 3's
+adapted non-separable scheme, float wavelets) is compared with the oracle's adapted form and
+with its Eq. 3 form, both within that bound.
 """
 import numpy as np
 import pytest
@@ -60,3 +62,25 @@ def test_full_size_8192_separable_matches_nonseparable():
     ti = to_gpu(x.astype(np.int32), torch.int32)
     refi = gpu_bands(D.forward(ti, "cdf53_int", 5))
     assert_bands(gpu_bands(D.forward(ti, "cdf53_int", 5, scheme="sep_fused")), refi, 0, "fused")
+
+
+@pytest.mark.parametrize("wavelet", ["cdf53", "cdf97"])
+@pytest.mark.parametrize("H,W", SIZES)
+def test_float_adapted(wavelet, H, W):
+    rng = np.random.default_rng(H + 23 * W)
+    x = rng.uniform(0, 255, (H, W)).astype(np.float32)
+    for lv in sorted({1, min(5, D.max_levels(H, W))}):
+        got = gpu_bands(D.forward(to_gpu(x, torch.float32), wavelet, lv, scheme="adapted"))
+        xd = x.astype(np.float64)
+        assert_bands(got, O.forward(xd, wavelet, lv, "adapted"), FLOAT_TOL, (wavelet, H, W, lv))
+        assert_bands(got, O.forward(xd, wavelet, lv, "eq3"), FLOAT_TOL, (wavelet, H, W, lv))
+
+
+def test_adapted_full_size_and_integer_rejected():
+    x = I.field(8192, 8192, I.seed_for(1))
+    t = to_gpu(x, torch.float32)
+    ref = gpu_bands(D.forward(t, "cdf97", 5))
+    assert_bands(gpu_bands(D.forward(t, "cdf97", 5, scheme="adapted")), ref, FLOAT_TOL, "adapted")
+    with pytest.raises(D.Dwt2Error):
+        D.forward(to_gpu(x[:64, :64].astype(np.int32), torch.int32), "cdf53_int", 2,
+                  scheme="adapted")
