@@ -219,6 +219,7 @@ def run_only(args, D, dev, x_f32, x_i32, flush, stream):
         "twopass_cdf97": ("cdf97", x_f32, LEVELS, False, "sep_twopass"),
         "sepfused_cdf97": ("cdf97", x_f32, LEVELS, False, "sep_fused"),
         "adapted_cdf97": ("cdf97", x_f32, LEVELS, False, "adapted"),
+        "conv_cdf97": ("cdf97", x_f32, LEVELS, False, "conv"),
         "plan_cdf97": ("cdf97", x_f32, LEVELS, False, "plan"),
         "plan_cdf53_int": ("cdf53_int", x_i32, LEVELS, False, "plan"),
     }[args.only]
@@ -475,7 +476,7 @@ def main():
     ap.add_argument("--only", default=None,
                     choices=["fwd_l1_cdf97", "fwd_cdf97", "inv_cdf97", "fwd_cdf53_int",
                              "inv_cdf53_int", "twopass_cdf97", "sepfused_cdf97", "adapted_cdf97",
-                             "plan_cdf97", "plan_cdf53_int"],
+                             "conv_cdf97", "plan_cdf97", "plan_cdf53_int"],
                     help="run one case only (for profiler captures); prints a short line")
     ap.add_argument("--levels", type=int, default=0,
                     help="with --only: decomposition levels instead of the case's own")
@@ -599,6 +600,11 @@ def main():
     c, ws, _ = make("cdf97", x_f32, "adapted")
     cases["fwd_cdf97_adapted"] = summarise(run_case(
         lambda: D.forward(x_f32, "cdf97", LEVELS, scheme="adapted", out=c, workspace=ws),
+        args.steps, args.warmup))
+    # the separable convolution (Eq. 4; float wavelets): the filter-bank comparator
+    cc, wsc, _ = make("cdf97", x_f32, "conv")
+    cases["fwd_cdf97_conv"] = summarise(run_case(
+        lambda: D.forward(x_f32, "cdf97", LEVELS, scheme="conv", out=cc, workspace=wsc),
         args.steps, args.warmup))
     correct_inv = bool(torch.equal(D.inverse(ci, out=out_i, workspace=wsi), x_i32))
 

@@ -92,12 +92,16 @@ typedef enum {
  *   DWT2_SCHEME_ADAPTED      the adapted non-separable scheme (Sec. 3, Fig. 3): P = P0 + P1,
  *                            U = U0 + U1 with the constant monomials P0, U0 applied as local
  *                            steps (no neighbouring quad read) before the fused steps with P1,
- *                            U1.  Float wavelets only (DWT2_EUNSUPPORTED for the integer one). */
+ *                            U1.  Float wavelets only (DWT2_EUNSUPPORTED for the integer one).
+ *   DWT2_SCHEME_CONV         the separable convolution (Eq. 4): the whole 1-D analysis filter
+ *                            bank along rows as one step, then along columns, each followed by
+ *                            the subsampling (one pass per level).  Float wavelets only. */
 typedef enum {
     DWT2_SCHEME_NONSEP = 0,
     DWT2_SCHEME_SEP_FUSED = 1,
     DWT2_SCHEME_SEP_TWOPASS = 2,
-    DWT2_SCHEME_ADAPTED = 3
+    DWT2_SCHEME_ADAPTED = 3,
+    DWT2_SCHEME_CONV = 4
 } dwt2_scheme;
 
 /* One subband plane inside the caller's coefficient buffer. */

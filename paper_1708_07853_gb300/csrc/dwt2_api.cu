@@ -275,10 +275,11 @@ static int forward_impl(const void* img, int64_t img_pitch, int H, int W, int im
     if (rc) return rc;
     if (adjoint && (wavelet == WV_CDF53_INT || img_dtype != DT_F32 || band_dtype != DT_F32))
         return DWT2_EUNSUPPORTED;
-    if (scheme < DWT2_SCHEME_NONSEP || scheme > DWT2_SCHEME_ADAPTED) return DWT2_EINVAL;
+    if (scheme < DWT2_SCHEME_NONSEP || scheme > DWT2_SCHEME_CONV) return DWT2_EINVAL;
     if (scheme != DWT2_SCHEME_NONSEP && (img_dtype != band_dtype || bt.N != 1))
         return DWT2_EUNSUPPORTED;
-    if (scheme == DWT2_SCHEME_ADAPTED && (wavelet == WV_CDF53_INT || adjoint))
+    if ((scheme == DWT2_SCHEME_ADAPTED || scheme == DWT2_SCHEME_CONV) &&
+        (wavelet == WV_CDF53_INT || adjoint))
         return DWT2_EUNSUPPORTED;
     Layout L;
     if ((rc = make_layout(H, W, J, band_dtype, &L))) return rc;
@@ -336,6 +337,7 @@ static int forward_impl(const void* img, int64_t img_pitch, int H, int W, int im
             const bool tma = mr == MAP_OK;
             const int mode = scheme == DWT2_SCHEME_NONSEP    ? MODE_NONSEP
                              : scheme == DWT2_SCHEME_ADAPTED ? MODE_ADAPTED
+                             : scheme == DWT2_SCHEME_CONV    ? MODE_CONV
                                                              : MODE_SEP;
             if (adjoint) {
                 a.scale = reciprocal(level_scale(wavelet, h, w));
@@ -551,7 +553,7 @@ DWT2_EXPORT size_t dwt2_workspace_bytes_scheme(int H, int W, int levels, int wav
                                                int band_dtype, int scheme) {
     Layout L;
     if (make_layout(H, W, levels, band_dtype, &L) || wavelet < 0 || wavelet > 2 ||
-        scheme < DWT2_SCHEME_NONSEP || scheme > DWT2_SCHEME_ADAPTED)
+        scheme < DWT2_SCHEME_NONSEP || scheme > DWT2_SCHEME_CONV)
         return 0;
     return size_t(plan_workspace(H, W, levels, wavelet, scheme).bytes);
 }

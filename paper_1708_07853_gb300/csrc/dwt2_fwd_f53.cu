@@ -27,6 +27,7 @@ cudaError_t launch_fwd_f53(int mode, int ti, int tb, const CUtensorMap& tm,
     case MODE_ROWS: return go<MODE_ROWS, float, float>(tm, a, s);
     case MODE_COLS: return go<MODE_COLS, float, float>(tm, a, s);
     case MODE_ADAPTED: return go<MODE_ADAPTED, float, float>(tm, a, s);
+    case MODE_CONV: return go<MODE_CONV, float, float>(tm, a, s);
     default: return cudaErrorNotSupported;
     }
 }

@@ -29,7 +29,8 @@ enum Mode {
     MODE_ROWS = 2,
     MODE_COLS = 3,
     MODE_ADJ_INV = 4,
-    MODE_ADAPTED = 5
+    MODE_ADAPTED = 5,
+    MODE_CONV = 6
 };
 
 // CDF 9/7 lifting constants and the per-axis normalisation (low * 1/K, high * K/2).
@@ -377,6 +378,91 @@ struct AdaptedUpdate {
             pc[q] = c[q];
             pe[q] = r.e[q];
             pel[q] = el[q];
+        }
+    }
+};
+
+// =============================================================================================
+// Separable convolution (Eq. 4), float wavelets: N^H, the whole 1-D analysis along rows as one
+// filtering step, then N^V along columns, each followed by the subsampling.  The analysis
+// filters are the impulse responses of the 1-D lifting steps above (with the per-axis 9/7
+// scaling), evaluated at compile time: low taps -kL..kL around the even sample, high taps
+// -kH..kH around the odd one.  They are symmetric, so the whole-sample symmetric extension the
+// loaders supply is the boundary rule here too.
+// =============================================================================================
+template <int WV>
+struct ConvTaps {
+    static constexpr int kL = WV == WV_CDF97 ? 4 : 2;
+    static constexpr int kH = WV == WV_CDF97 ? 3 : 1;
+    float lo[2 * kL + 1] = {};
+    float hi[2 * kH + 1] = {};
+};
+
+template <int WV>
+constexpr ConvTaps<WV> conv_taps() {
+    ConvTaps<WV> t{};
+    constexpr int kN = 16, kN0 = 4;  // half-length of the probe signal, observed output index
+    constexpr int kPairs = WV == WV_CDF97 ? 2 : 1;
+    const double P[2] = {WV == WV_CDF97 ? double(k97Alpha) : -0.5, double(k97Gamma)};
+    const double U[2] = {WV == WV_CDF97 ? double(k97Beta) : 0.25, double(k97Delta)};
+    for (int k = 2 * kN0 - t.kL; k <= 2 * kN0 + 1 + t.kH; ++k) {
+        double sv[kN] = {}, dv[kN] = {};  // even / odd samples of the unit impulse at k
+        if (k % 2 == 0) sv[k / 2] = 1.0;
+        else dv[k / 2] = 1.0;
+        for (int j = 0; j < kPairs; ++j) {
+            for (int i = 0; i + 1 < kN; ++i) dv[i] += P[j] * (sv[i] + sv[i + 1]);
+            for (int i = kN - 1; i >= 1; --i) sv[i] += U[j] * (dv[i - 1] + dv[i]);
+        }
+        const double ls = WV == WV_CDF97 ? double(k97Low) : 1.0;
+        const double hs = WV == WV_CDF97 ? double(k97High) : 1.0;
+        const int tl = k - 2 * kN0, th = k - 2 * kN0 - 1;
+        if (tl >= -t.kL && tl <= t.kL) t.lo[tl + t.kL] = float(ls * sv[kN0]);
+        if (th >= -t.kH && th <= t.kH) t.hi[th + t.kH] = float(hs * dv[kN0]);
+    }
+    return t;
+}
+
+// Vertical step N^V over the horizontally filtered quad rows (a: low column of row 2n, b: high
+// column of row 2n, c: low column of row 2n + 1, e: high column of row 2n + 1).  Keeps a window
+// of 2 kLag + 1 quad rows; push(row n + kLag) returns output quad row n (LL, HL, LH, HH).
+template <int WV>
+struct ConvV {
+    static constexpr int kL = ConvTaps<WV>::kL, kH = ConvTaps<WV>::kH;
+    static constexpr int kLag = (kL + 1) / 2;
+    static constexpr int kWin = 2 * kLag + 1;
+    QRow<float> w[kWin];
+    __device__ __forceinline__ void init() {
+#pragma unroll
+        for (int j = 0; j < kWin; ++j) zero_row(w[j]);
+    }
+    // pixel row 2n + t of the low (hi = false) or high column of quad q
+    __device__ __forceinline__ float pix(int t, bool high, int q) const {
+        const int j = kLag + (t >= 0 ? t / 2 : -((1 - t) / 2));
+        const bool odd = (t & 1) != 0;
+        return high ? (odd ? w[j].e[q] : w[j].b[q]) : (odd ? w[j].c[q] : w[j].a[q]);
+    }
+    __device__ __forceinline__ void push(QRow<float>& r) {
+        constexpr ConvTaps<WV> T = conv_taps<WV>();
+#pragma unroll
+        for (int j = 0; j + 1 < kWin; ++j) w[j] = w[j + 1];
+        w[kWin - 1] = r;
+#pragma unroll
+        for (int q = 0; q < kQ; ++q) {
+            float ll = 0.f, hl = 0.f, lh = 0.f, hh = 0.f;
+#pragma unroll
+            for (int t = -kL; t <= kL; ++t) {
+                ll = fmaf(T.lo[t + kL], pix(t, false, q), ll);
+                hl = fmaf(T.lo[t + kL], pix(t, true, q), hl);
+            }
+#pragma unroll
+            for (int t = -kH; t <= kH; ++t) {
+                lh = fmaf(T.hi[t + kH], pix(t + 1, false, q), lh);
+                hh = fmaf(T.hi[t + kH], pix(t + 1, true, q), hh);
+            }
+            r.a[q] = ll;
+            r.b[q] = hl;
+            r.c[q] = lh;
+            r.e[q] = hh;
         }
     }
 };
@@ -757,7 +843,10 @@ struct FwdPipe {
     UpdateCol<float> ucol[kPairs];
     AdaptedPredict pa[kPairs];
     AdaptedUpdate ua[kPairs];
+    ConvV<WV> cv;
+    static_assert(MODE != MODE_CONV || ConvV<WV>::kLag == kPairs, "lag of the convolution");
     __device__ __forceinline__ void init() {
+        if constexpr (MODE == MODE_CONV) cv.init();
         const float P[kQ] = {WV == WV_CDF97 ? k97Alpha : -0.5f, k97Gamma};
         const float U[kQ] = {WV == WV_CDF97 ? k97Beta : 0.25f, k97Delta};
 #pragma unroll
@@ -771,6 +860,9 @@ struct FwdPipe {
     __device__ __forceinline__ void push(QRow<float>& r) {
         if constexpr (MODE == MODE_ROWS) {
             rows_only<float, WV>(r);
+            return;
+        } else if constexpr (MODE == MODE_CONV) {
+            cv.push(r);  // the taps include the scaling
             return;
         } else {
 #pragma unroll

@@ -356,6 +356,58 @@ __device__ __forceinline__ void fwd_lane_row_shifted(const TI* stage, const FwdC
     }
 }
 
+// Separable convolution (Eq. 4): stage offsets of the 11 pixel columns 2 m0 - 4 .. 2 m0 + 6 a
+// lane's two quads filter over; at the plane's edges each column's whole-sample-symmetric
+// source.  Computed once per tile.
+struct ConvCols {
+    static constexpr int kN = 11;
+    bool edge;
+    int base;
+    int idx[kN];
+    __device__ __forceinline__ void init(int col0, int xs, int W, bool at_edge) {
+        edge = at_edge;
+        base = col0 - 4 - xs;
+#pragma unroll
+        for (int j = 0; j < kN; ++j)
+            idx[j] = edge ? min(max(refl(col0 - 4 + j, W) - xs, 0), kSRow - 1) : base + j;
+    }
+};
+
+// N^H on one stage: the low / high analysis filters along both pixel rows, at the lane's two
+// quads (row r shifted by (shifts >> 4r) & 15 elements, as the plain-load path fills it).
+template <int WV, typename TI>
+__device__ __forceinline__ void conv_lane_row(const TI* stage, const ConvCols& cols, int shifts,
+                                              QRow<float>& row) {
+    constexpr ConvTaps<WV> T = conv_taps<WV>();
+    constexpr int kL = ConvTaps<WV>::kL, kH = ConvTaps<WV>::kH;
+    const int s0 = shifts & 15, s1 = (shifts >> 4) & 15;
+    float x0[ConvCols::kN], x1[ConvCols::kN];
+#pragma unroll
+    for (int j = 0; j < ConvCols::kN; ++j) {
+        x0[j] = to_c(stage[min(cols.idx[j] + s0, kSRow - 1)]);
+        x1[j] = to_c(stage[kSRow + min(cols.idx[j] + s1, kSRow - 1)]);
+    }
+#pragma unroll
+    for (int q = 0; q < kQ; ++q) {
+        const int c = 4 + 2 * q;  // the quad's even column in x0 / x1
+        float l0 = 0.f, l1 = 0.f, h0 = 0.f, h1 = 0.f;
+#pragma unroll
+        for (int t = -kL; t <= kL; ++t) {
+            l0 = fmaf(T.lo[t + kL], x0[c + t], l0);
+            l1 = fmaf(T.lo[t + kL], x1[c + t], l1);
+        }
+#pragma unroll
+        for (int t = -kH; t <= kH; ++t) {
+            h0 = fmaf(T.hi[t + kH], x0[c + 1 + t], h0);
+            h1 = fmaf(T.hi[t + kH], x1[c + 1 + t], h1);
+        }
+        row.a[q] = l0;
+        row.b[q] = h0;
+        row.c[q] = l1;
+        row.e[q] = h1;
+    }
+}
+
 // Stores a finished quad row qo: the four band rows, or (MODE_ROWS) two interleaved pixel rows.
 template <int MODE, typename TB, typename TL, typename C>
 __device__ __forceinline__ void fwd_store_row(const FwdArgs& a, const QRow<C>& row, int qo, int m0,
@@ -611,6 +663,9 @@ __global__ void __launch_bounds__(kThreads, min_ctas<WV>())
     const bool store_lane = lane >= 1 && lane <= 30;
     FwdCols cols;
     cols.init(2 * m0, xs, args.W, !kAdj, (2 * wq < 0) || (2 * wq + 2 * kWarpQ > args.W));
+    ConvCols ccols;
+    if constexpr (MODE == MODE_CONV)
+        ccols.init(2 * m0, xs, args.W, (2 * wq - 4 < 0) || (2 * wq + 2 * kWarpQ + 4 > args.W));
     // a warp whose output quads all lie beyond the plane only cycles the barriers
     const bool idle = wq + kHQ >= args.nec;
     LaneW hw;
@@ -629,7 +684,10 @@ __global__ void __launch_bounds__(kThreads, min_ctas<WV>())
             continue;
         }
         QRow<C> row;
-        if constexpr (kPlain)
+        if constexpr (MODE == MODE_CONV)
+            conv_lane_row<WV, TI>(reinterpret_cast<const TI*>(ring.stage(s)), ccols,
+                                  kPlain ? int(ring.shift[s]) : 0, row);
+        else if constexpr (kPlain)
             fwd_lane_row_shifted<TI, C>(reinterpret_cast<const TI*>(ring.stage(s)), cols, row,
                                         ring.shift[s]);
         else

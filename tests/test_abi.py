@@ -107,6 +107,11 @@ def test_argument_validation_before_any_launch(lib):
     # the adapted scheme (3) has no integer form
     assert lib.dwt2_forward_scheme(fake, 32, 8, 8, 0, fake, fake, 1 << 20, 0, 1, 0, 3,
                                    None) == 2
+    # nor the convolution (4)
+    assert lib.dwt2_forward_scheme(fake, 32, 8, 8, 0, fake, fake, 1 << 20, 0, 1, 0, 4,
+                                   None) == 2
+    assert lib.dwt2_forward_scheme(fake, 64, 8, 8, 1, fake, fake, 1 << 20, 1, 1, 1, 5,
+                                   None) == 1
     # inverse: null coefficient buffer
     assert lib.dwt2_inverse(None, fake, 64, 8, 8, 1, fake, 1 << 20, 1, 1, 1, None) == 1
 

@@ -6,7 +6,10 @@ DWT2_SCHEME_SEP_TWOPASS runs all row steps, then all column steps (two kernels p
 the integer wavelet it is bit-exact with the oracle's rows-then-columns order instead.  Float
 results meet the same 1e-3 bound as the non-separable path.  DWT2_SCHEME_ADAPTED (Sec. 3's
 adapted non-separable scheme, float wavelets) is compared with the oracle's adapted form and
-with its Eq. 3 form, both within that bound.
+with its Eq. 3 form, both within that bound.  DWT2_SCHEME_CONV (the separable convolution of
+Eq. 4, float wavelets) filters with taps the kernel derives from its own lifting constants; the
+oracle's lifting result, whose equality with the published filter banks is pinned on the CPU,
+is the reference, within the same bound.
 """
 import numpy as np
 import pytest
@@ -84,3 +87,25 @@ def test_adapted_full_size_and_integer_rejected():
     with pytest.raises(D.Dwt2Error):
         D.forward(to_gpu(x[:64, :64].astype(np.int32), torch.int32), "cdf53_int", 2,
                   scheme="adapted")
+
+
+@pytest.mark.parametrize("wavelet", ["cdf53", "cdf97"])
+@pytest.mark.parametrize("H,W", SIZES + [(2, 2), (3, 4), (5, 2), (1, 17)])
+def test_float_convolution(wavelet, H, W):
+    rng = np.random.default_rng(H + 29 * W)
+    x = rng.uniform(0, 255, (H, W)).astype(np.float32)
+    for lv in sorted({1, min(5, D.max_levels(H, W))}):
+        got = gpu_bands(D.forward(to_gpu(x, torch.float32), wavelet, lv, scheme="conv"))
+        assert_bands(got, O.forward(x.astype(np.float64), wavelet, lv), FLOAT_TOL,
+                     (wavelet, H, W, lv))
+
+
+def test_convolution_unaligned_pitch_and_full_size():
+    x = I.field(8192, 8192, I.seed_for(1))
+    t = to_gpu(x, torch.float32)
+    ref = gpu_bands(D.forward(t, "cdf97", 5))
+    assert_bands(gpu_bands(D.forward(t, "cdf97", 5, scheme="conv")), ref, FLOAT_TOL, "conv")
+    small = x[:300, :517]
+    want = O.forward(small.astype(np.float64), "cdf97", 4)
+    got = gpu_bands(D.forward(to_gpu(small, torch.float32, pad=3), "cdf97", 4, scheme="conv"))
+    assert_bands(got, want, FLOAT_TOL, "conv, plain-load path")
