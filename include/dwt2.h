@@ -287,6 +287,18 @@ int dwt2_plan_info(const dwt2_plan* plan, int* rows_per_tile, int* ctas_per_sm, 
 int dwt2_plan_destroy(dwt2_plan* plan);
 
 /* ---------------------------------------------------------------------------------------------
+ * Self-test of the bounded device waits (no counterpart in the paper; failure detection for the
+ * library).  Every wait inside the kernels -- on a stage barrier, or in the persistent kernels on
+ * another tile's completion counter -- gives up after a time limit of 2 s: the kernel raises its
+ * abort flag, records DWT2_ETIMEOUT in the workspace status word and returns.  This call launches
+ * one warp that waits on a barrier phase nothing completes (which = 0) or on a counter in the
+ * workspace header that nothing increments (which = 1).
+ *   workspace  at least 256 bytes, prepared by dwt2_workspace_init (which zeroes the counter).
+ * Returns DWT2_OK once launched; about 2 s later dwt2_check_status(workspace, stream) reports
+ * DWT2_ETIMEOUT.  The context stays usable. */
+int dwt2_selftest_wait_timeout(int which, void* workspace, size_t ws_bytes, void* stream);
+
+/* ---------------------------------------------------------------------------------------------
  * Forward transform without a caller-provided workspace.  The paper has no counterpart: this
  * entry point exists for callers that cannot allocate device memory (for example code whose host
  * application owns all device memory and passes in only the input and output buffers, or a

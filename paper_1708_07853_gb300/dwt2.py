@@ -32,7 +32,8 @@ EXPORTS = ["dwt2_status_string", "dwt2_last_error", "dwt2_max_levels", "dwt2_lay
            "dwt2_forward_static", "dwt2_forward_adjoint", "dwt2_inverse_adjoint",
            "dwt2_plan_workspace_bytes", "dwt2_plan_create", "dwt2_plan_execute", "dwt2_plan_info",
            "dwt2_plan_destroy", "dwt2_workspace_bytes_batch", "dwt2_forward_batch",
-           "dwt2_inverse_batch", "dwt2_forward_adjoint_batch", "dwt2_inverse_adjoint_batch"]
+           "dwt2_inverse_batch", "dwt2_forward_adjoint_batch", "dwt2_inverse_adjoint_batch",
+           "dwt2_selftest_wait_timeout"]
 DIRECTIONS = {"forward": 0, "inverse": 1, "forward_adjoint": 2, "inverse_adjoint": 3}
 
 
@@ -100,12 +101,13 @@ def _lib():
                                                    i, vp]
         lib.dwt2_inverse_adjoint_batch.argtypes = [vp, i64, i64, i, i, i, i, vp, i64, vp, sz, i, i,
                                                    i, vp]
+        lib.dwt2_selftest_wait_timeout.argtypes = [i, vp, sz, vp]
         for f in ("dwt2_max_levels", "dwt2_layout", "dwt2_workspace_init", "dwt2_check_status",
                   "dwt2_forward", "dwt2_forward_scheme", "dwt2_inverse", "dwt2_forward_static",
                   "dwt2_forward_adjoint", "dwt2_inverse_adjoint", "dwt2_plan_create",
                   "dwt2_plan_execute", "dwt2_plan_info", "dwt2_plan_destroy",
                   "dwt2_forward_batch", "dwt2_inverse_batch", "dwt2_forward_adjoint_batch",
-                  "dwt2_inverse_adjoint_batch"):
+                  "dwt2_inverse_adjoint_batch", "dwt2_selftest_wait_timeout"):
             getattr(lib, f).restype = i
         _LIB = lib
     return _LIB
@@ -410,6 +412,15 @@ def inverse_adjoint_batch(x: torch.Tensor, wavelet="cdf97", levels: int = 1,
     if rc:
         raise Dwt2Error(rc, "dwt2_inverse_adjoint_batch")
     return out
+
+
+def selftest_wait_timeout(which: int, workspace: torch.Tensor, stream=None) -> None:
+    """dwt2_selftest_wait_timeout: one warp waits on something nothing signals (0: a barrier
+    phase, 1: a counter); about 2 s later check_status(workspace) reports DWT2_ETIMEOUT."""
+    rc = _lib().dwt2_selftest_wait_timeout(which, workspace.data_ptr(), workspace.numel(),
+                                           _stream_ptr(stream))
+    if rc:
+        raise Dwt2Error(rc, "dwt2_selftest_wait_timeout")
 
 
 class Plan:

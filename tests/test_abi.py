@@ -152,3 +152,10 @@ def test_batch_validation_and_workspace(lib):
     # integer wavelet has no adjoint
     assert lib.dwt2_inverse_adjoint_batch(fake, 64, img_b, 4, 16, 16, 0, fake, cb, fake, ws, 0, 2,
                                           0, None) == 2
+
+
+def test_selftest_validation(lib):
+    fake = ctypes.c_void_p(0x1000)
+    assert lib.dwt2_selftest_wait_timeout(2, fake, 4096, None) == 1
+    assert lib.dwt2_selftest_wait_timeout(0, None, 4096, None) == 1
+    assert lib.dwt2_selftest_wait_timeout(0, fake, 128, None) == 1
