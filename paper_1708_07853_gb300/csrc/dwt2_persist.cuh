@@ -110,18 +110,17 @@ __device__ __forceinline__ void prefetch_unit_maps(const InvUnit& u) {
         for (int k = 0; k < 4; ++k) prefetch_tensormap(&u.tm[k]);
 }
 
-// Copies a unit's argument block into shared memory (one warp, read-only source), so that the
-// per-row code reads it there: global stores to the bands could alias a global copy, which would
-// force the compiler to reload it after every row.
-template <typename Args>
-__device__ __forceinline__ void copy_args(Args* dst, const Args* src, int lane) {
-    static_assert(sizeof(Args) % 4 == 0, "argument block is copied in words");
-    const int* s = reinterpret_cast<const int*>(src);
-    int* d = reinterpret_cast<int*>(dst);
-    __syncwarp();
-    for (int k = lane; k < int(sizeof(Args) / 4); k += 32) d[k] = __ldg(s + k);
-    __syncwarp();
+// Resident CTAs per SM of the persistent kernels: the per-tile arguments they hold in registers
+// do not fit the single-image kernels' 64-register budget of the 5/3 wavelets without spilling.
+template <int WV>
+constexpr int persist_min_ctas() {
+    return WV == 2 ? 1 : 4;
 }
+
+// Per-tile arguments.  Each warp copies its tile's unit arguments into a local variable once per
+// tile; every helper that reads them is inlined, so the compiler keeps the fields the per-row
+// code uses in registers.  A copy in global or shared memory would be reloaded after every row's
+// band stores and barrier operations (their memory clobbers), doubling the instructions per row.
 
 // Producer side shared by both kernel shapes: claim the next ticket; returns -1 when the work is
 // exhausted.  Waits for the ticket's dependency.
@@ -163,7 +162,7 @@ __device__ __forceinline__ void post_sentinel(const Ring& ring, int g, int lane,
 }
 
 template <int WV, int MODE, typename TI, typename TB, typename TL>
-__global__ void __launch_bounds__(kThreads, min_ctas<WV>())
+__global__ void __launch_bounds__(kThreads, persist_min_ctas<WV>())
     k_forward_persistent(const PersistArgs<FwdUnit> p) {
     constexpr bool kAdj = MODE == MODE_ADJ_INV;
     using Pipe = std::conditional_t<kAdj, AdjInvPipe<WV>, FwdPipe<WV, MODE_NONSEP>>;
@@ -175,7 +174,7 @@ __global__ void __launch_bounds__(kThreads, min_ctas<WV>())
     __syncthreads();
 
     if (warp == kNW) {  // ------------------------------------------------------ producer
-        __shared__ FwdArgs pargs;  // the current tile's unit arguments
+        FwdArgs pargs;  // the current tile's unit arguments, held in registers (see below)
         int g = 0;
         bool tma_used = false;
         for (;;) {
@@ -186,7 +185,7 @@ __global__ void __launch_bounds__(kThreads, min_ctas<WV>())
                 break;
             }
             const FwdUnit& U = p.units[__ldg(&p.item_unit[t])];
-            copy_args(&pargs, &U.a, lane);
+            pargs = U.a;
             const Tile tl = tile_of(pargs, t - __ldg(&U.item_begin), __ldg(&U.strips));
             const int xs = 2 * tl.qx0 - kXL;
             tma_used |= pargs.tma != 0;
@@ -216,8 +215,7 @@ __global__ void __launch_bounds__(kThreads, min_ctas<WV>())
     }
 
     // ------------------------------------------------------------------------- consumers
-    __shared__ FwdArgs wargs[kNW];  // the current tile's unit arguments, one copy per warp
-    const FwdArgs& A = wargs[warp];
+    FwdArgs A;  // the current tile's unit arguments, held in registers (see below)
     const bool store_lane = lane >= 1 && lane <= 30;
     int cur = -1, i = 0, unit = 0;
     Tile tl{};
@@ -236,7 +234,7 @@ __global__ void __launch_bounds__(kThreads, min_ctas<WV>())
             cur = t;
             unit = __ldg(&p.item_unit[t]);
             const FwdUnit* U = &p.units[unit];
-            copy_args(&wargs[warp], &U->a, lane);
+            A = U->a;
             tl = tile_of(A, t - __ldg(&U->item_begin), __ldg(&U->strips));
             const int wq = tl.qx0 - kHQ + warp * kWarpOut;
             m0 = wq + kQ * lane;
@@ -271,7 +269,7 @@ __global__ void __launch_bounds__(kThreads, min_ctas<WV>())
 }
 
 template <int WV, typename TB, typename TL, typename TO, bool ADJ>
-__global__ void __launch_bounds__(kThreads, min_ctas<WV>())
+__global__ void __launch_bounds__(kThreads, persist_min_ctas<WV>())
     k_inverse_persistent(const PersistArgs<InvUnit> p) {
     using Pipe = std::conditional_t<ADJ, AdjFwdPipe<WV>, InvPipe<WV>>;
     using C = typename Pipe::C;
@@ -283,7 +281,7 @@ __global__ void __launch_bounds__(kThreads, min_ctas<WV>())
     __syncthreads();
 
     if (warp == kNW) {  // ------------------------------------------------------ producer
-        __shared__ InvArgs pargs;  // the current tile's unit arguments
+        InvArgs pargs;  // the current tile's unit arguments, held in registers (see below)
         int g = 0;
         bool tma_used = false;
         for (;;) {
@@ -294,7 +292,7 @@ __global__ void __launch_bounds__(kThreads, min_ctas<WV>())
                 break;
             }
             const InvUnit& U = p.units[__ldg(&p.item_unit[t])];
-            copy_args(&pargs, &U.a, lane);
+            pargs = U.a;
             const Tile tl = tile_of(pargs, t - __ldg(&U.item_begin), __ldg(&U.strips));
             const int xb = tl.qx0 - kXLB;
             const CUtensorMap* maps[4] = {&U.tm[0], &U.tm[1], &U.tm[2], &U.tm[3]};
@@ -324,8 +322,7 @@ __global__ void __launch_bounds__(kThreads, min_ctas<WV>())
     }
 
     // ------------------------------------------------------------------------- consumers
-    __shared__ InvArgs wargs[kNW];  // the current tile's unit arguments, one copy per warp
-    const InvArgs& A = wargs[warp];
+    InvArgs A;  // the current tile's unit arguments, held in registers (see below)
     const bool store_lane = lane >= 1 && lane <= 30;
     int cur = -1, i = 0, unit = 0;
     Tile tl{};
@@ -344,7 +341,7 @@ __global__ void __launch_bounds__(kThreads, min_ctas<WV>())
             cur = t;
             unit = __ldg(&p.item_unit[t]);
             const InvUnit* U = &p.units[unit];
-            copy_args(&wargs[warp], &U->a, lane);
+            A = U->a;
             tl = tile_of(A, t - __ldg(&U->item_begin), __ldg(&U->strips));
             const int wq = tl.qx0 - kHQ + warp * kWarpOut;
             m0 = wq + kQ * lane;
