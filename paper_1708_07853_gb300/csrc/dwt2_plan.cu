@@ -1,8 +1,8 @@
 // dwt2_plan.cu -- batched plans: many images (any sizes), all levels, one persistent launch.
 //
-// dwt2_plan_create builds the work list (one unit per image and level, tiles of kCtaQ quad columns
-// x level_rows(rows_per_tile, level) quad rows), the TMA tensor maps and argument blocks of every unit in plan-owned
-// device memory, and captures [memset of the tile counters, persistent kernel] into a CUDA graph;
+// dwt2_plan_create builds the work list (one unit per image and level; tiles of kCtaQ quad columns
+// by a per-level number of quad rows), the TMA tensor maps and argument blocks of every unit in
+// plan-owned device memory, and captures [memset of the tile counters, persistent kernel] into a CUDA graph;
 // dwt2_plan_execute replays it.  rows_per_tile (and the CTAs per SM) come from an autotuner that
 // times candidates on the plan itself and keeps the winner in a text cache file, or from a
 // default when no cache file is given.
@@ -97,11 +97,62 @@ int check_plan_args(const dwt2_image_desc* imgs, int n, int wavelet, int J, int 
     return DWT2_OK;
 }
 
-// Quad rows per tile at level j, for `rows` at level 1: halved at every level (a level has half
-// the rows and half the strips of the one before), at least 4.  Long tiles keep the halo small
-// on the large levels; short ones keep the tail of each level (one tile's time) short on the
-// small levels, whose completion the next level waits for.
+// Upper bound on the quad rows per tile at level j, for `rows` at level 1: halved at every level
+// (a level has half the rows and half the strips of the one before), at least 4.
 int level_rows(int rows, int j) { return std::max(4, rows >> (j - 1)); }
+
+// Quad rows per tile at every level (index j = 1..J), at most level_rows(rows, j).  Long tiles
+// keep the halo small, but the next level waits for the whole level, and the tiles of one image
+// size run in waves of the resident CTAs.
+// * Images of one size: each level takes the rows (2 .. cap) that minimise waves x (rows +
+//   per-tile overhead), the estimate the single-image launches use.
+// * Mixed sizes: the claim queue evens out tiles of different lengths, so a level keeps the cap
+//   unless its tiles would leave resident CTAs idle; then it takes the estimate's rows.
+std::vector<int> plan_level_rows(const dwt2_plan* P, int rows, int resident) {
+    constexpr int64_t kRowCost = 8;  // halo rows + pipeline fill, in rows
+    const int J = P->levels;
+    std::vector<int> out(J + 1, 0);
+    std::vector<int> h(P->n), w(P->n);
+    bool one_size = true;
+    for (int i = 0; i < P->n; ++i) {
+        h[i] = P->imgs[i].H;
+        w[i] = P->imgs[i].W;
+        one_size = one_size && h[i] == h[0] && w[i] == w[0];
+    }
+    const int64_t slots = std::max(1, resident);
+    auto tiles_of = [&](int r, int* longest) {
+        int64_t tiles = 0;
+        *longest = 1;
+        for (int i = 0; i < P->n; ++i) {
+            const int ner = (h[i] + 1) / 2, nec = (w[i] + 1) / 2;
+            const int rpc = std::max(1, std::min(r, ner));
+            tiles += int64_t((nec + kCtaQ - 1) / kCtaQ) * ((ner + rpc - 1) / rpc);
+            *longest = std::max(*longest, rpc);
+        }
+        return tiles;
+    };
+    for (int j = 1; j <= J; ++j) {
+        const int cap = level_rows(rows, j);
+        int longest = 1;
+        out[j] = cap;
+        if (one_size || tiles_of(cap, &longest) < slots) {
+            int64_t best = -1;
+            for (int r = cap; r >= 2; --r) {
+                const int64_t tiles = tiles_of(r, &longest);
+                const int64_t cost = (tiles + slots - 1) / slots * (longest + kRowCost);
+                if (best < 0 || cost < best) {
+                    best = cost;
+                    out[j] = r;
+                }
+            }
+        }
+        for (int i = 0; i < P->n; ++i) {
+            h[i] = (h[i] + 1) / 2;
+            w[i] = (w[i] + 1) / 2;
+        }
+    }
+    return out;
+}
 
 // Default level-1 rows per tile: about four tiles per resident CTA over the whole batch, so that
 // the tail of the ticket queue is short, within [8, 256] quad rows.
@@ -136,6 +187,7 @@ int build_work(dwt2_plan* P, int rows, std::vector<FwdUnit>& fu, std::vector<Inv
         return int64_t(P->imgs[a].H) * P->imgs[a].W > int64_t(P->imgs[b].H) * P->imgs[b].W;
     });
     std::vector<int> unit_of(size_t(n) * (J + 1), -1);  // (image, level) -> unit
+    const std::vector<int> lrows = plan_level_rows(P, rows, P->ctas_per_sm * device_sm_count());
     fu.clear();
     iu.clear();
     item_unit.clear();
@@ -159,7 +211,7 @@ int build_work(dwt2_plan* P, int rows, std::vector<FwdUnit>& fu, std::vector<Inv
             const dwt2_band& blh = bands[1 + 3 * (J - j) + 1];
             const dwt2_band& bhh = bands[1 + 3 * (J - j) + 2];
             const int ner = (hh + 1) / 2, nec = (ww + 1) / 2;
-            const int rpc = std::max(1, std::min(level_rows(rows, j), ner));
+            const int rpc = std::max(1, std::min(lrows[j], ner));
             const int strips = (nec + kCtaQ - 1) / kCtaQ;
             const int n_items = strips * ((ner + rpc - 1) / rpc);
             const int dep_level = P->fwd_flow ? j - 1 : j + 1;
