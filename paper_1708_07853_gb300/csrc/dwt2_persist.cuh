@@ -89,15 +89,15 @@ struct Tile {
     int qx0, n0, n1, nrows, qfirst;
 };
 
-template <typename Args>
+template <int kVH, typename Args>
 __device__ __forceinline__ Tile tile_of(const Args& a, int local, int strips) {
     Tile t;
     const int rb = local / strips, strip = local - rb * strips;
     t.qx0 = strip * kCtaQ;
     t.n0 = rb * a.rpc;
     t.n1 = min(t.n0 + a.rpc, a.ner);
-    t.nrows = t.n1 - t.n0 + 2 * kVHalo;
-    t.qfirst = t.n0 - kVHalo;
+    t.nrows = t.n1 - t.n0 + 2 * kVH;
+    t.qfirst = t.n0 - kVH;
     return t;
 }
 
@@ -167,6 +167,7 @@ __global__ void __launch_bounds__(kThreads, persist_min_ctas<WV>())
     constexpr bool kAdj = MODE == MODE_ADJ_INV;
     using Pipe = std::conditional_t<kAdj, AdjInvPipe<WV>, FwdPipe<WV, MODE_NONSEP>>;
     using C = typename Pipe::C;
+    constexpr int kVH = vhalo<Pipe, kAdj>();
     extern __shared__ __align__(128) uint8_t smem_raw[];
     const Ring ring = make_ring(smem_raw, size_t(2) * kSRow * sizeof(TI));
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -186,7 +187,7 @@ __global__ void __launch_bounds__(kThreads, persist_min_ctas<WV>())
             }
             const FwdUnit& U = p.units[__ldg(&p.item_unit[t])];
             pargs = U.a;
-            const Tile tl = tile_of(pargs, t - __ldg(&U.item_begin), __ldg(&U.strips));
+            const Tile tl = tile_of<kVH>(pargs, t - __ldg(&U.item_begin), __ldg(&U.strips));
             const int xs = 2 * tl.qx0 - kXL;
             tma_used |= pargs.tma != 0;
             bool alive = true;
@@ -235,7 +236,7 @@ __global__ void __launch_bounds__(kThreads, persist_min_ctas<WV>())
             unit = __ldg(&p.item_unit[t]);
             const FwdUnit* U = &p.units[unit];
             A = U->a;
-            tl = tile_of(A, t - __ldg(&U->item_begin), __ldg(&U->strips));
+            tl = tile_of<kVH>(A, t - __ldg(&U->item_begin), __ldg(&U->strips));
             const int wq = tl.qx0 - kHQ + warp * kWarpOut;
             m0 = wq + kQ * lane;
             const int xs = 2 * tl.qx0 - kXL;
@@ -273,6 +274,7 @@ __global__ void __launch_bounds__(kThreads, persist_min_ctas<WV>())
     k_inverse_persistent(const PersistArgs<InvUnit> p) {
     using Pipe = std::conditional_t<ADJ, AdjFwdPipe<WV>, InvPipe<WV>>;
     using C = typename Pipe::C;
+    constexpr int kVH = vhalo<Pipe, ADJ>();
     constexpr size_t kStageBytes = size_t(kBRow) * (sizeof(TL) + 3 * sizeof(TB));
     extern __shared__ __align__(128) uint8_t smem_raw[];
     const Ring ring = make_ring(smem_raw, kStageBytes);
@@ -293,7 +295,7 @@ __global__ void __launch_bounds__(kThreads, persist_min_ctas<WV>())
             }
             const InvUnit& U = p.units[__ldg(&p.item_unit[t])];
             pargs = U.a;
-            const Tile tl = tile_of(pargs, t - __ldg(&U.item_begin), __ldg(&U.strips));
+            const Tile tl = tile_of<kVH>(pargs, t - __ldg(&U.item_begin), __ldg(&U.strips));
             const int xb = tl.qx0 - kXLB;
             const CUtensorMap* maps[4] = {&U.tm[0], &U.tm[1], &U.tm[2], &U.tm[3]};
             tma_used |= pargs.tma != 0;
@@ -342,7 +344,7 @@ __global__ void __launch_bounds__(kThreads, persist_min_ctas<WV>())
             unit = __ldg(&p.item_unit[t]);
             const InvUnit* U = &p.units[unit];
             A = U->a;
-            tl = tile_of(A, t - __ldg(&U->item_begin), __ldg(&U->strips));
+            tl = tile_of<kVH>(A, t - __ldg(&U->item_begin), __ldg(&U->strips));
             const int wq = tl.qx0 - kHQ + warp * kWarpOut;
             m0 = wq + kQ * lane;
             cols.init(m0, tl.qx0 - kXLB, A.W, !ADJ, (2 * wq < 0) || (2 * wq + 2 * kWarpQ > A.W));

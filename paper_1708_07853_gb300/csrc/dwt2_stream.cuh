@@ -41,7 +41,17 @@ constexpr int row_unroll() {
     return WV == 2 ? 1 : 2;
 }
 constexpr int kStages = 8;               // quad rows in flight per CTA
-constexpr int kVHalo = 2;                // halo quad rows above and below a CTA's rows
+constexpr int kVHalo = 2;                // halo quad rows above and below a CTA's rows (adjoints)
+
+// Halo quad rows above and below a CTA's rows.  A level's output quad row n depends on its input
+// quad rows n - kLag .. n + kLag (the reach of kLag lifting pairs along the columns: 1 for the
+// 5/3 wavelets, 2 for the 9/7), and its pipeline returns row n when row n + kLag is pushed, so
+// the forward and inverse levels load exactly kLag halo rows on each side.  The adjoint levels
+// keep kVHalo.
+template <typename Pipe, bool kAdjoint>
+constexpr int vhalo() {
+    return kAdjoint ? kVHalo : Pipe::kLag;
+}
 
 // Forward: a stage holds 2 pixel rows of the strip's pixel columns [2*qx0 - kXL, +kSRow), loaded
 // as 256-wide boxes (every TMA destination starts on a 128-byte boundary).
@@ -618,7 +628,7 @@ __global__ void __launch_bounds__(kThreads, min_ctas<WV>())
     constexpr bool kAdj = MODE == MODE_ADJ_INV;
     using Pipe = std::conditional_t<kAdj, AdjInvPipe<WV>, FwdPipe<WV, kAdj ? MODE_NONSEP : MODE>>;
     using C = typename Pipe::C;
-    constexpr int kVH = MODE == MODE_ROWS ? 0 : kVHalo;
+    constexpr int kVH = vhalo<Pipe, kAdj>();  // 0 for the row pass (MODE_ROWS)
     extern __shared__ __align__(128) uint8_t smem_raw[];
     const Ring ring = make_ring(smem_raw, size_t(2) * kSRow * sizeof(TI));
 
@@ -721,8 +731,9 @@ __global__ void __launch_bounds__(kThreads, min_ctas<WV>())
     const int qx0 = blockIdx.x * kCtaQ;
     const int n0 = blockIdx.y * args.rpc;
     const int n1 = min(n0 + args.rpc, args.ner);
-    const int nrows = n1 - n0 + 2 * kVHalo;
-    const int qfirst = n0 - kVHalo;
+    constexpr int kVH = vhalo<Pipe, ADJ>();
+    const int nrows = n1 - n0 + 2 * kVH;
+    const int qfirst = n0 - kVH;
     const int xb = qx0 - kXLB;
 
     init_ring(ring);
