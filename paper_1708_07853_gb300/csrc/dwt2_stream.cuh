@@ -147,9 +147,6 @@ __device__ __forceinline__ uint8_t* align128(uint8_t* p) {
 // per consumer warp.
 // =============================================================================================
 
-// Forward data flow: loads of extended quad row q (pixel rows 2q, 2q + 1) of the input plane.
-// Mirrored (whole-sample symmetric) rows for the transform; plain rows, zeros outside, for the
-// adjoint of the inverse.
 // Plain-load producer for planes TMA cannot address (pitch or base not 16-byte aligned).  Only
 // the caller's own image takes this path (every scratch plane is TMA-eligible), so nothing the
 // running kernel writes is read here.
@@ -224,64 +221,15 @@ __device__ __forceinline__ void fwd_produce_plain(const FwdArgs& a, bool adj, in
     if (lane == 0) mbar_arrive(full);
 }
 
-// Forward data flow: loads of extended quad row q (pixel rows 2q, 2q + 1) of the input plane.
-// Mirrored (whole-sample symmetric) rows for the transform; plain rows, zeros outside, for the
-// adjoint of the inverse.
-// Plain-load producer for planes TMA cannot address (pitch or base not 16-byte aligned).  Only
-// the caller's own image takes this path (every scratch plane is TMA-eligible), so nothing the
-// running kernel writes is read here.
-template <typename TI, int kUnroll>
-__device__ __forceinline__ void fwd_produce_plain(const FwdArgs& a, int r0, int r1, int xs, TI* dst,
-                                                  uint64_t* full, int lane, int z) {
-    const bool ok0 = r0 >= 0 && r0 < a.H, ok1 = r1 >= 0 && r1 < a.H;
-    const char* base = static_cast<const char*>(a.in) + int64_t(z) * a.in_bstride;
-    const TI* row0 = reinterpret_cast<const TI*>(base + int64_t(ok0 ? r0 : 0) * a.in_pitch);
-    const TI* row1 = reinterpret_cast<const TI*>(base + int64_t(ok1 ? r1 : 0) * a.in_pitch);
-    constexpr int kPer = kSRow / 32;
-    if constexpr (sizeof(TI) == 4) {
-        // cp.async element copies, zero-filled outside the plane: like TMA, the producer moves on
-        // to the next stage at once and the stage's full barrier completes when the copies have
-        // landed, so up to kStages stages are in flight.  kUnroll: 1 in the single-image kernels
-        // (their TMA path keeps its instruction footprint), fully unrolled in the persistent
-        // kernels, where unaligned images of a batch make this path common.
-#pragma unroll kUnroll
-        for (int j = 0; j < kPer; ++j) {
-            const int k = lane + 32 * j, c = xs + k;
-            const bool in = c >= 0 && c < a.W;
-            cp_async_4(dst + k, row0 + (in ? c : 0), in && ok0);
-            cp_async_4(dst + kSRow + k, row1 + (in ? c : 0), in && ok1);
-        }
-        cp_async_arrive(full);
-    } else {
-        // 16-bit elements (below cp.async's 4-byte minimum): all loads of the stage are issued
-        // before the first shared-memory store, one memory latency per stage.
-        TI v0[kPer], v1[kPer];
-#pragma unroll
-        for (int j = 0; j < kPer; ++j) {
-            const int c = xs + lane + 32 * j;
-            const bool in = c >= 0 && c < a.W;
-            v0[j] = (in && ok0) ? ldcg(row0 + c) : zero_of<TI>();
-            v1[j] = (in && ok1) ? ldcg(row1 + c) : zero_of<TI>();
-        }
-#pragma unroll
-        for (int j = 0; j < kPer; ++j) {
-            dst[lane + 32 * j] = v0[j];
-            dst[kSRow + lane + 32 * j] = v1[j];
-        }
-    }
-    __syncwarp();
-    if (lane == 0) mbar_arrive(full);
-}
-
-// Forward data flow: loads of extended quad row q (pixel rows 2q, 2q + 1) of the input plane.
-// Mirrored (whole-sample symmetric) rows for the transform; plain rows, zeros outside, for the
-// adjoint of the inverse.
 // Which loader a kernel instantiation contains: decided per launch from a.tma (persistent
 // kernels, whose units mix aligned and unaligned planes), or fixed at compile time (single-image
 // kernels: the launcher picks the TMA or the plain-load instantiation, so the TMA kernels carry no
 // plain-load code).
 enum Loader { LOAD_RUNTIME = 0, LOAD_TMA = 1, LOAD_PLAIN = 2 };
 
+// Forward data flow: loads of extended quad row q (pixel rows 2q, 2q + 1) of the input plane.
+// Mirrored (whole-sample symmetric) rows for the transform; plain rows, zeros outside, for the
+// adjoint of the inverse.
 template <typename TI, int kUnrollPlain = 1, int kLoader = LOAD_RUNTIME>
 __device__ __forceinline__ void fwd_produce_row(const FwdArgs& a, const CUtensorMap* tm, bool adj,
                                                 int q, int xs, TI* dst, uint64_t* full, int lane,
