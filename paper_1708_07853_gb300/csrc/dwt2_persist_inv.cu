@@ -8,7 +8,7 @@ namespace {
 template <int WV, typename TB, typename TL, typename TO, bool ADJ>
 cudaError_t go(const PersistArgs<InvUnit>& p, int ctas_per_sm, cudaStream_t st, int* occ_out) {
     auto k = k_inverse_persistent<WV, TB, TL, TO, ADJ>;
-    constexpr size_t smem = inv_smem_bytes<TL, TB>();
+    constexpr size_t smem = inv_smem_bytes<TL, TB, kPersistStages>();
     static const int occ = configure(k, smem);
     if (occ_out) {
         *occ_out = occ;

@@ -40,7 +40,18 @@ template <int WV>
 constexpr int row_unroll() {
     return WV == 2 ? 1 : 2;
 }
-constexpr int kStages = 8;               // quad rows in flight per CTA
+// Ring depth (quad rows in flight per CTA) per wavelet and data flow, from same-box A/B runs
+// at 8192^2 over depths 6, 8 and 12: the 5/3 kernels are 2-3% faster with 12 (shared memory
+// then holds them to 4 CTAs per SM, which still beats 6 CTAs with 8 stages), the 9/7 forward is
+// 0.6% faster with 6 than with 8, and the 9/7 inverse is fastest with 8.
+template <int WV>
+constexpr int fwd_stages() {
+    return WV == 2 ? 6 : 12;
+}
+template <int WV>
+constexpr int inv_stages() {
+    return WV == 2 ? 8 : 12;
+}
 constexpr int kVHalo = 2;                // halo quad rows above and below a CTA's rows (adjoints)
 
 // Halo quad rows above and below a CTA's rows.  A level's output quad row n depends on its input
@@ -122,16 +133,17 @@ __device__ __forceinline__ void putN(T* p, const C (&v)[N], int c0, int width, b
     }
 }
 
-// Bytes of dynamic shared memory of the kernels (+128 to align the base to 128 bytes).
-template <typename TI>
+// Bytes of dynamic shared memory of the kernels with NS ring stages (+128 to align the base to
+// 128 bytes).
+template <typename TI, int NS>
 constexpr size_t fwd_smem_bytes() {
-    return size_t(kStages) * 2 * kSRow * sizeof(TI) + 2 * kStages * sizeof(uint64_t) +
-           4 * (2 * kStages + 4) + 128;
+    return size_t(NS) * 2 * kSRow * sizeof(TI) + 2 * NS * sizeof(uint64_t) + 4 * (2 * NS + 4) +
+           128;
 }
-template <typename TL, typename TB>
+template <typename TL, typename TB, int NS>
 constexpr size_t inv_smem_bytes() {
-    return size_t(kStages) * kBRow * (sizeof(TL) + 3 * sizeof(TB)) +
-           2 * kStages * sizeof(uint64_t) + 4 * (2 * kStages + 4) + 128;
+    return size_t(NS) * kBRow * (sizeof(TL) + 3 * sizeof(TB)) + 2 * NS * sizeof(uint64_t) +
+           4 * (2 * NS + 4) + 128;
 }
 
 __device__ __forceinline__ uint8_t* align128(uint8_t* p) {
@@ -160,8 +172,8 @@ __device__ __forceinline__ uint8_t* align128(uint8_t* p) {
 //     row 1 in bits 4-7).
 //   adjoint (zeros outside the plane): 4-byte zero-filling cp.async copies (16-bit elements, below
 //     cp.async's minimum, are loaded before the first shared-memory store), no shift.
-// Either way the stage's full barrier completes when the copies have landed, so up to kStages
-// stages are in flight, as with TMA.  kUnroll: 1 in the single-image kernels (their TMA path keeps
+// Either way the stage's full barrier completes when the copies have landed, so every stage of
+// the ring can be in flight, as with TMA.  kUnroll: 1 in the single-image kernels (their TMA path keeps
 // its instruction footprint), full in the persistent kernels.
 template <typename TI, int kUnroll>
 __device__ __forceinline__ void fwd_produce_plain(const FwdArgs& a, bool adj, int r0, int r1,
@@ -520,9 +532,11 @@ __device__ __forceinline__ void inv_store_row(const InvArgs& a, const QRow<C>& r
         putN<2 * kQ>(row_ptr<TO>(a.out, 2 * qo + 1, z) + c0, vc, c0, a.W, a.out_vec != 0);
 }
 
-// Shared-memory ring: kStages stages, then the full / empty barriers, the abort flag and the
+// Shared-memory ring: NS stages, then the full / empty barriers, the abort flag and the
 // per-stage tile ids (persistent kernels).
+template <int NS>
 struct Ring {
+    static constexpr int kN = NS;
     uint8_t* stage0;
     size_t stage_bytes;
     uint64_t* full;
@@ -533,22 +547,24 @@ struct Ring {
     __device__ __forceinline__ uint8_t* stage(int s) const { return stage0 + size_t(s) * stage_bytes; }
 };
 
-__device__ __forceinline__ Ring make_ring(uint8_t* smem_raw, size_t stage_bytes) {
-    Ring r;
+template <int NS>
+__device__ __forceinline__ Ring<NS> make_ring(uint8_t* smem_raw, size_t stage_bytes) {
+    Ring<NS> r;
     r.stage0 = align128(smem_raw);
     r.stage_bytes = stage_bytes;
-    r.full = reinterpret_cast<uint64_t*>(r.stage0 + kStages * stage_bytes);
-    r.empty = r.full + kStages;
-    r.abort = reinterpret_cast<volatile int*>(r.empty + kStages);
+    r.full = reinterpret_cast<uint64_t*>(r.stage0 + NS * stage_bytes);
+    r.empty = r.full + NS;
+    r.abort = reinterpret_cast<volatile int*>(r.empty + NS);
     r.meta = r.abort + 1;
-    r.shift = r.meta + kStages;
+    r.shift = r.meta + NS;
     return r;
 }
 
 // Thread 0 initialises the barriers; every thread must call __syncthreads() afterwards.
-__device__ __forceinline__ void init_ring(const Ring& r) {
+template <int NS>
+__device__ __forceinline__ void init_ring(const Ring<NS>& r) {
     if (threadIdx.x == 0) {
-        for (int s = 0; s < kStages; ++s) {
+        for (int s = 0; s < NS; ++s) {
             mbar_init(&r.full[s], 1);
             mbar_init(&r.empty[s], kNW);
         }
@@ -558,10 +574,11 @@ __device__ __forceinline__ void init_ring(const Ring& r) {
 }
 
 // Lets the last TMA copies of a producer land before its CTA exits (bounded).
-__device__ __forceinline__ void drain_ring(const Ring& r, int issued, int* status) {
+template <int NS>
+__device__ __forceinline__ void drain_ring(const Ring<NS>& r, int issued, int* status) {
     volatile int no_abort = 0;
-    for (int i = max(0, issued - kStages); i < issued; ++i)
-        if (!mbar_wait(&r.full[i % kStages], (i / kStages) & 1, &no_abort, status)) break;
+    for (int i = max(0, issued - NS); i < issued; ++i)
+        if (!mbar_wait(&r.full[i % NS], (i / NS) & 1, &no_abort, status)) break;
 }
 
 // =============================================================================================
@@ -577,8 +594,9 @@ __global__ void __launch_bounds__(kThreads, min_ctas<WV>())
     using Pipe = std::conditional_t<kAdj, AdjInvPipe<WV>, FwdPipe<WV, kAdj ? MODE_NONSEP : MODE>>;
     using C = typename Pipe::C;
     constexpr int kVH = vhalo<Pipe, kAdj>();  // 0 for the row pass (MODE_ROWS)
+    constexpr int kS = fwd_stages<WV>();
     extern __shared__ __align__(128) uint8_t smem_raw[];
-    const Ring ring = make_ring(smem_raw, size_t(2) * kSRow * sizeof(TI));
+    const Ring<kS> ring = make_ring<kS>(smem_raw, size_t(2) * kSRow * sizeof(TI));
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int z = blockIdx.z;  // image of a batch
@@ -600,9 +618,9 @@ __global__ void __launch_bounds__(kThreads, min_ctas<WV>())
     if (warp == kNW) {  // ------------------------------------------------------ producer
         int issued = 0;
         for (int i = 0; i < nrows; ++i) {
-            const int s = i % kStages;
-            if (i >= kStages) {
-                bool ok = mbar_wait(&ring.empty[s], ((i / kStages) - 1) & 1, ring.abort, args.status);
+            const int s = i % kS;
+            if (i >= kS) {
+                bool ok = mbar_wait(&ring.empty[s], ((i / kS) - 1) & 1, ring.abort, args.status);
                 if (!__all_sync(kFull, ok)) break;
             }
             fwd_produce_row<TI, 1, kPlain ? LOAD_PLAIN : LOAD_TMA>(
@@ -634,8 +652,8 @@ __global__ void __launch_bounds__(kThreads, min_ctas<WV>())
     pipe.init();
 #pragma unroll row_unroll<WV>()
     for (int i = 0; i < nrows; ++i) {
-        const int s = i % kStages;
-        bool ok = mbar_wait(&ring.full[s], (i / kStages) & 1, ring.abort, args.status);
+        const int s = i % kS;
+        bool ok = mbar_wait(&ring.full[s], (i / kS) & 1, ring.abort, args.status);
         if (!__all_sync(kFull, ok)) break;
         if (idle) {
             if (lane == 0) mbar_arrive(&ring.empty[s]);
@@ -671,8 +689,9 @@ __global__ void __launch_bounds__(kThreads, min_ctas<WV>())
     using Pipe = std::conditional_t<ADJ, AdjFwdPipe<WV>, InvPipe<WV>>;
     using C = typename Pipe::C;
     constexpr size_t kStageBytes = size_t(kBRow) * (sizeof(TL) + 3 * sizeof(TB));
+    constexpr int kS = inv_stages<WV>();
     extern __shared__ __align__(128) uint8_t smem_raw[];
-    const Ring ring = make_ring(smem_raw, kStageBytes);
+    const Ring<kS> ring = make_ring<kS>(smem_raw, kStageBytes);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int z = blockIdx.z;  // image of a batch
@@ -700,9 +719,9 @@ __global__ void __launch_bounds__(kThreads, min_ctas<WV>())
         const CUtensorMap* maps[4] = {&tm_ll, &tm_hl, &tm_lh, &tm_hh};
         int issued = 0;
         for (int i = 0; i < nrows; ++i) {
-            const int s = i % kStages;
-            if (i >= kStages) {
-                bool ok = mbar_wait(&ring.empty[s], ((i / kStages) - 1) & 1, ring.abort, args.status);
+            const int s = i % kS;
+            if (i >= kS) {
+                bool ok = mbar_wait(&ring.empty[s], ((i / kS) - 1) & 1, ring.abort, args.status);
                 if (!__all_sync(kFull, ok)) break;
             }
             inv_produce_row<TL, TB>(args, maps, ADJ, qfirst + i, xb, ring.stage(s), &ring.full[s],
@@ -729,8 +748,8 @@ __global__ void __launch_bounds__(kThreads, min_ctas<WV>())
     pipe.init();
 #pragma unroll row_unroll<WV>()
     for (int i = 0; i < nrows; ++i) {
-        const int s = i % kStages;
-        bool ok = mbar_wait(&ring.full[s], (i / kStages) & 1, ring.abort, args.status);
+        const int s = i % kS;
+        bool ok = mbar_wait(&ring.full[s], (i / kS) & 1, ring.abort, args.status);
         if (!__all_sync(kFull, ok)) break;
         if (idle) {
             if (lane == 0) mbar_arrive(&ring.empty[s]);
@@ -829,7 +848,7 @@ int configure(K kernel, size_t smem) {
 template <int WV, int MODE, typename TI, typename TB, typename TL, bool kPlain>
 cudaError_t launch_forward_k(const CUtensorMap& tm, FwdArgs a, cudaStream_t st) {
     auto k = k_forward<WV, MODE, TI, TB, TL, kPlain>;
-    constexpr size_t smem = fwd_smem_bytes<TI>();
+    constexpr size_t smem = fwd_smem_bytes<TI, fwd_stages<WV>()>();
     static const int occ = configure(k, smem);
     const LaunchGeom g = pick_geometry(a.ner, a.nec, int64_t(a.H) * a.W * int64_t(sizeof(TI)),
                                        device_sm_count(), occ, a.nbatch);
@@ -847,7 +866,7 @@ cudaError_t launch_forward_t(const CUtensorMap& tm, FwdArgs a, cudaStream_t st) 
 template <int WV, typename TB, typename TL, typename TO, bool ADJ = false>
 cudaError_t launch_inverse_t(const CUtensorMap* tm, InvArgs a, cudaStream_t st) {
     auto k = k_inverse<WV, TB, TL, TO, ADJ>;
-    constexpr size_t smem = inv_smem_bytes<TL, TB>();
+    constexpr size_t smem = inv_smem_bytes<TL, TB, inv_stages<WV>()>();
     static const int occ = configure(k, smem);
     const LaunchGeom g = pick_geometry(a.ner, a.nec, int64_t(a.H) * a.W * int64_t(sizeof(TL)),
                                        device_sm_count(), occ, a.nbatch);
