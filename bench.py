@@ -20,6 +20,7 @@ from __future__ import annotations
 import argparse
 import hashlib
 import json
+import re
 import os
 import subprocess
 import tempfile
@@ -62,16 +63,25 @@ def alg_bytes(h: int, w: int, levels: int, esize: int = 4) -> int:
 
 
 # Sources the level-1 forward kernel is compiled from: a recorded ncu capture counts only while
-# these are unchanged.
+# their code is unchanged.
 KERNEL_SOURCES = {"fwd_l1_cdf97_f32": ["dwt2_device.cuh", "dwt2_lifting.cuh", "dwt2_stream.cuh",
                                        "dwt2_fwd_f97.cu"]}
 
 
+def _code_only(text: str) -> str:
+    """C++ source without comments and with whitespace collapsed (string literals in these
+    files hold no comment markers)."""
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", " ", text)
+    return " ".join(text.split())
+
+
 def src_hash(kernel_key: str) -> str:
+    """Hash of the code (not the comments) of a kernel's sources."""
     d = os.path.join(ROOT, "paper_1708_07853_gb300", "csrc")
     m = hashlib.sha256()
     for f in KERNEL_SOURCES[kernel_key]:
-        m.update(open(os.path.join(d, f), "rb").read())
+        m.update(_code_only(open(os.path.join(d, f)).read()).encode())
     return m.hexdigest()[:16]
 
 

@@ -7,7 +7,8 @@
 //   CTA   = a strip of kCtaQ output quad columns (4 warps x 30 lanes x kQ) x rpc quad rows;
 //   warp  = a window of 32 x kQ quad columns (kQ adjacent quads per lane); lanes 0 and 31 are halo
 //           (they compute but never store: the lifting reaches 2 quads to each side);
-//   rows  = the CTA streams its rpc rows plus 2 halo quad rows above and below.
+//   rows  = the CTA streams its rpc rows plus halo quad rows above and below (one per lifting
+//           pair: 1 for the 5/3 wavelets, 2 for the 9/7; the adjoints take 2).
 // Boundaries: the producer maps every (extended) row to its whole-sample-symmetric source row;
 // warps whose window crosses the left or right image edge read each column from its mirrored
 // source column.  The lifting then runs on the symmetric extension with no boundary rule.
