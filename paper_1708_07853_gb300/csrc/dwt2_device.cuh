@@ -101,6 +101,17 @@ __device__ __forceinline__ void tma_load_3d(void* smem_dst, const CUtensorMap* m
         : "memory");
 }
 
+// Bulk (non-tensor) copy of `bytes` bytes from global to shared memory, completing on an
+// mbarrier (transaction bytes).  Both addresses 16-byte aligned, bytes a multiple of 16.
+__device__ __forceinline__ void bulk_copy_g2s(void* smem_dst, const void* src, uint32_t bytes,
+                                              uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+        ::"r"(smem_u32(smem_dst)), "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes),
+        "r"(smem_u32(bar))
+        : "memory");
+}
+
 // cp.async of one 4-byte element into shared memory; valid == false writes zero and reads
 // nothing.  Goes through L1 (.ca), so it is only used on planes that no CTA of the running kernel
 // writes.

@@ -117,6 +117,13 @@ constexpr int persist_min_ctas() {
     return WV == 2 ? 1 : 4;
 }
 
+// Plain-load path of the persistent kernels: 16-byte cp.async chunks issued by all producer
+// lanes and elementwise reads of the shifted stages.  The single-image kernels' bulk copies and
+// vector reads each made the 512-image batch about 1% slower here (its unaligned images are
+// mostly small, so their rows are short).
+constexpr bool kPersistBulk = false;
+constexpr bool kPersistVec = false;
+
 // Ring depth of the persistent kernels: 8 stages for every wavelet (the single-image depths, 6
 // for the 9/7 forward and 12 for the 5/3, made the 512-image batch 1.4% and 0.4% slower).
 constexpr int kPersistStages = 8;
@@ -183,7 +190,7 @@ __global__ void __launch_bounds__(kThreads, persist_min_ctas<WV>())
     if (warp == kNW) {  // ------------------------------------------------------ producer
         FwdArgs pargs;  // the current tile's unit arguments, held in registers (see below)
         int g = 0;
-        bool tma_used = false;
+        bool bulk_used = false;  // TMA or bulk copies (async, tracked by the stage barriers)
         for (;;) {
             bool ok;
             const int t = claim(p, ring.abort, lane, ok);
@@ -195,7 +202,7 @@ __global__ void __launch_bounds__(kThreads, persist_min_ctas<WV>())
             pargs = U.a;
             const Tile tl = tile_of<kVH>(pargs, t - __ldg(&U.item_begin), __ldg(&U.strips));
             const int xs = 2 * tl.qx0 - kXL;
-            tma_used |= pargs.tma != 0;
+            bulk_used |= pargs.tma != 0 || (kPersistBulk && !kAdj);
             bool alive = true;
             for (int i = 0; i < tl.nrows; ++i, ++g) {
                 const int s = g % kS;
@@ -207,7 +214,8 @@ __global__ void __launch_bounds__(kThreads, persist_min_ctas<WV>())
                     }
                 }
                 if (lane == 0) ring.meta[s] = t;
-                fwd_produce_row<TI, kSRow / 32>(pargs, &U.tm, kAdj, tl.qfirst + i, xs,
+                fwd_produce_row<TI, kSRow / 32, LOAD_RUNTIME, kPersistBulk>(
+                                                pargs, &U.tm, kAdj, tl.qfirst + i, xs,
                                                 reinterpret_cast<TI*>(ring.stage(s)),
                                                 &ring.full[s], lane, 0, &ring.shift[s]);
             }
@@ -216,7 +224,7 @@ __global__ void __launch_bounds__(kThreads, persist_min_ctas<WV>())
         // Normally the consumers take every stage (the sentinel last) before the CTA can exit, so
         // all copies have landed.  After an abort, let the copies still in flight land first.  (No
         // drain otherwise: the sentinel's stage has moved one phase past its last copy.)
-        if (tma_used && lane == 0 && *ring.abort) drain_ring(ring, g, p.status);
+        if (bulk_used && lane == 0 && *ring.abort) drain_ring(ring, g, p.status);
         cp_async_wait_all();  // no-op unless this lane issued cp.async copies
         return;
     }
@@ -257,8 +265,8 @@ __global__ void __launch_bounds__(kThreads, persist_min_ctas<WV>())
             if (A.tma)
                 fwd_lane_row<TI, C>(reinterpret_cast<const TI*>(ring.stage(s)), cols, row);
             else
-                fwd_lane_row_shifted<TI, C>(reinterpret_cast<const TI*>(ring.stage(s)), cols, row,
-                                            ring.shift[s]);
+                fwd_lane_row_shifted<TI, C, kPersistVec>(reinterpret_cast<const TI*>(ring.stage(s)),
+                                                         cols, row, ring.shift[s]);
             __syncwarp();
             if (lane == 0) mbar_arrive(&ring.empty[s]);
             if constexpr (kAdj)

@@ -164,19 +164,20 @@ __device__ __forceinline__ uint8_t* align128(uint8_t* p) {
 // the caller's own image takes this path (every scratch plane is TMA-eligible), so nothing the
 // running kernel writes is read here.
 //   transform (mirrored rows): each row is copied as the 16-byte-aligned chunks that hold its
-//     elements xs .. xs + kSRow - 1, with 16-byte cp.async (L2 only), so the row lands shifted by
-//     the misalignment m (0 .. 16 / sizeof(TI) - 1 elements) of element xs: element c sits at
-//     stage index c - xs + m.  Chunks with no element inside the row are skipped; a chunk that
-//     straddles an end of the row reads at most 15 bytes beyond it, inside the same 16-byte
-//     block (so inside mapped memory); those stage entries are never read (the consumers read
-//     mirrored columns at the plane's edges).  The shifts go to *shift_slot (row 0 in bits 0-3,
-//     row 1 in bits 4-7).
+//     elements xs .. xs + kSRow - 1, in one bulk copy per row, so the row lands shifted by the
+//     misalignment m (0 .. 16 / sizeof(TI) - 1 elements) of element xs: element c sits at stage
+//     index c - xs + m.  The copied chunks are those holding at least one element of the row: a
+//     chunk that straddles an end of the row reads at most 15 bytes beyond it, inside the same
+//     16-byte block (so inside mapped memory); those stage entries are never read (the
+//     consumers read mirrored columns at the plane's edges).  Like a TMA load, the copy
+//     completes on the stage's full barrier with its byte count.  The shifts go to *shift_slot
+//     (row 0 in bits 0-3, row 1 in bits 4-7).
 //   adjoint (zeros outside the plane): 4-byte zero-filling cp.async copies (16-bit elements, below
 //     cp.async's minimum, are loaded before the first shared-memory store), no shift.
 // Either way the stage's full barrier completes when the copies have landed, so every stage of
-// the ring can be in flight, as with TMA.  kUnroll: 1 in the single-image kernels (their TMA path keeps
-// its instruction footprint), full in the persistent kernels.
-template <typename TI, int kUnroll>
+// the ring can be in flight, as with TMA.  kUnroll: 1 in the single-image kernels (their TMA path
+// keeps its instruction footprint), full in the persistent kernels.
+template <typename TI, int kUnroll, bool kBulk>
 __device__ __forceinline__ void fwd_produce_plain(const FwdArgs& a, bool adj, int r0, int r1,
                                                   int xs, TI* dst, uint64_t* full, int lane, int z,
                                                   volatile int* shift_slot) {
@@ -185,14 +186,15 @@ __device__ __forceinline__ void fwd_produce_plain(const FwdArgs& a, bool adj, in
     const TI* row0 = reinterpret_cast<const TI*>(base + int64_t(ok0 ? r0 : 0) * a.in_pitch);
     const TI* row1 = reinterpret_cast<const TI*>(base + int64_t(ok1 ? r1 : 0) * a.in_pitch);
     constexpr int kPer = kSRow / 32;
-    if (!adj) {
+    if (!adj && !kBulk) {
         constexpr int kEpc = 16 / int(sizeof(TI));  // elements per chunk
         constexpr int kChunks = kSRow / kEpc;
         int sh = 0;
 #pragma unroll
         for (int r = 0; r < 2; ++r) {
             const TI* row = r ? row1 : row0;
-            const uintptr_t first = reinterpret_cast<uintptr_t>(row) + intptr_t(xs) * intptr_t(sizeof(TI));
+            const uintptr_t first =
+                reinterpret_cast<uintptr_t>(row) + intptr_t(xs) * intptr_t(sizeof(TI));
             const int m = int((first & 15u) / sizeof(TI));
             const int e0 = xs - m;  // element at the first chunk's (aligned) address
 #pragma unroll kUnroll
@@ -204,6 +206,36 @@ __device__ __forceinline__ void fwd_produce_plain(const FwdArgs& a, bool adj, in
         }
         cp_async_arrive(full);
         if (lane == 0) *shift_slot = sh;
+    } else if (!adj) {
+        if (lane == 0) {
+            constexpr int kEpc = 16 / int(sizeof(TI));  // elements per chunk
+            constexpr int kChunks = kSRow / kEpc;
+            const char* src[2];
+            uint32_t bytes[2], dofs[2];
+            int sh = 0;
+#pragma unroll
+            for (int r = 0; r < 2; ++r) {
+                const TI* row = r ? row1 : row0;
+                const uintptr_t first =
+                    reinterpret_cast<uintptr_t>(row) + intptr_t(xs) * intptr_t(sizeof(TI));
+                const int m = int((first & 15u) / sizeof(TI));
+                const int e0 = xs - m;  // element at the first chunk's (aligned) address
+                // chunks k of the stage row hold elements e0 + k kEpc ..; those with an element
+                // of the row are k_lo .. k_hi - 1
+                const int k_lo = e0 >= 0 ? 0 : (-e0) / kEpc;
+                const int k_hi = min(kChunks, (a.W - e0 + kEpc - 1) / kEpc);
+                bytes[r] = k_hi > k_lo ? uint32_t(16 * (k_hi - k_lo)) : 0u;
+                src[r] = reinterpret_cast<const char*>(first & ~uintptr_t(15)) + 16 * k_lo;
+                dofs[r] = uint32_t(r * kSRow * int(sizeof(TI)) + 16 * k_lo);
+                sh |= m << (4 * r);
+            }
+            *shift_slot = sh;
+            mbar_arrive_expect_tx(full, bytes[0] + bytes[1]);
+#pragma unroll
+            for (int r = 0; r < 2; ++r)
+                if (bytes[r]) bulk_copy_g2s(reinterpret_cast<char*>(dst) + dofs[r], src[r], bytes[r], full);
+        }
+        return;
     } else if constexpr (sizeof(TI) == 4) {
 #pragma unroll kUnroll
         for (int j = 0; j < kPer; ++j) {
@@ -243,7 +275,7 @@ enum Loader { LOAD_RUNTIME = 0, LOAD_TMA = 1, LOAD_PLAIN = 2 };
 // Forward data flow: loads of extended quad row q (pixel rows 2q, 2q + 1) of the input plane.
 // Mirrored (whole-sample symmetric) rows for the transform; plain rows, zeros outside, for the
 // adjoint of the inverse.
-template <typename TI, int kUnrollPlain = 1, int kLoader = LOAD_RUNTIME>
+template <typename TI, int kUnrollPlain = 1, int kLoader = LOAD_RUNTIME, bool kBulk = true>
 __device__ __forceinline__ void fwd_produce_row(const FwdArgs& a, const CUtensorMap* tm, bool adj,
                                                 int q, int xs, TI* dst, uint64_t* full, int lane,
                                                 int z, volatile int* shift_slot) {
@@ -260,7 +292,8 @@ __device__ __forceinline__ void fwd_produce_row(const FwdArgs& a, const CUtensor
             }
         }
     } else if constexpr (kLoader != LOAD_TMA) {
-        fwd_produce_plain<TI, kUnrollPlain>(a, adj, r0, r1, xs, dst, full, lane, z, shift_slot);
+        fwd_produce_plain<TI, kUnrollPlain, kBulk>(a, adj, r0, r1, xs, dst, full, lane, z,
+                                                   shift_slot);
     }
 }
 
@@ -305,18 +338,39 @@ __device__ __forceinline__ void fwd_lane_row(const TI* stage, const FwdCols& col
     }
 }
 
-// The same from a stage filled by the plain-load path: row r of the stage is shifted by
-// (shifts >> 4r) & 15 elements; element reads, kept inside the stage.
+// Four consecutive 4-byte elements starting sh (0..3) past the 16-byte-aligned p: two aligned
+// vector loads and a selection (sh is the same across the warp).
 template <typename TI, typename C>
+__device__ __forceinline__ void ld4_shifted(const TI* p, int sh, C (&v)[4]) {
+    C x[4], y[4];
+    ld4(p, x);
+    ld4(p + 4, y);
+    switch (sh) {
+    case 0: v[0] = x[0]; v[1] = x[1]; v[2] = x[2]; v[3] = x[3]; break;
+    case 1: v[0] = x[1]; v[1] = x[2]; v[2] = x[3]; v[3] = y[0]; break;
+    case 2: v[0] = x[2]; v[1] = x[3]; v[2] = y[0]; v[3] = y[1]; break;
+    default: v[0] = x[3]; v[1] = y[0]; v[2] = y[1]; v[3] = y[2]; break;
+    }
+}
+
+// The same from a stage filled by the plain-load path: row r of the stage is shifted by
+// (shifts >> 4r) & 15 elements.  Lanes inside the plane read 4-byte elements with aligned vector
+// loads; lanes at an edge (and 16-bit elements) read elementwise, kept inside the stage.
+template <typename TI, typename C, bool kVec = true>
 __device__ __forceinline__ void fwd_lane_row_shifted(const TI* stage, const FwdCols& cols,
                                                      QRow<C>& row, int shifts) {
     const int s0 = shifts & 15, s1 = (shifts >> 4) & 15;
     C v0[2 * kQ], v1[2 * kQ];
+    if (kVec && sizeof(TI) == 4 && 2 * kQ == 4 && !cols.edge) {
+        ld4_shifted(stage + cols.base, s0, v0);
+        ld4_shifted(stage + kSRow + cols.base, s1, v1);
+    } else {
 #pragma unroll
-    for (int k = 0; k < 2 * kQ; ++k) {
-        const int i = cols.edge ? cols.ec[k] : cols.base + k;
-        v0[k] = to_c(stage[min(i + s0, kSRow - 1)]);
-        v1[k] = to_c(stage[kSRow + min(i + s1, kSRow - 1)]);
+        for (int k = 0; k < 2 * kQ; ++k) {
+            const int i = cols.edge ? cols.ec[k] : cols.base + k;
+            v0[k] = to_c(stage[min(i + s0, kSRow - 1)]);
+            v1[k] = to_c(stage[kSRow + min(i + s1, kSRow - 1)]);
+        }
     }
 #pragma unroll
     for (int q = 0; q < kQ; ++q) {
@@ -629,7 +683,7 @@ __global__ void __launch_bounds__(kThreads, min_ctas<WV>())
                 &ring.full[s], lane, z, &ring.shift[s]);
             issued = i + 1;
         }
-        if (!kPlain && lane == 0) drain_ring(ring, issued, args.status);
+        if (lane == 0) drain_ring(ring, issued, args.status);
         cp_async_wait_all();  // no-op unless this lane issued cp.async copies
         return;
     }
