@@ -35,8 +35,9 @@ constexpr int min_ctas() {
     return WV == 2 ? 1 : 6;
 }
 // Consumer row loop unrolled by 2 for the 5/3 wavelets: the compiler then renames the row
-// pipeline's registers instead of rotating them (int 5/3 forward 4.7% faster on GB300); the 9/7
-// kernels measured 2% slower unrolled and stay rolled.
+// pipeline's registers instead of rotating them (int 5/3 forward 4.7% faster on GB300).  The 9/7
+// kernels stay rolled: unrolled they measured 2% slower, and a hand-written loop over row pairs
+// executed 19% more instructions (ALU and uniform-pipe work for the pair bookkeeping).
 template <int WV>
 constexpr int row_unroll() {
     return WV == 2 ? 1 : 2;
@@ -44,7 +45,8 @@ constexpr int row_unroll() {
 // Ring depth (quad rows in flight per CTA) per wavelet and data flow, from same-box A/B runs
 // at 8192^2 over depths 6, 8 and 12: the 5/3 kernels are 2-3% faster with 12 (shared memory
 // then holds them to 4 CTAs per SM, which still beats 6 CTAs with 8 stages), the 9/7 forward is
-// 0.6% faster with 6 than with 8, and the 9/7 inverse is fastest with 8.
+// 0.9% faster with 6 than with 8 (4, 5 and 7 are no better), and the 9/7 inverse is fastest
+// with 8.
 template <int WV>
 constexpr int fwd_stages() {
     return WV == 2 ? 6 : 12;
