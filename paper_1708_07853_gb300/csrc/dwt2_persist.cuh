@@ -238,6 +238,7 @@ __global__ void __launch_bounds__(kThreads, persist_min_ctas<WV>())
     LaneW hw;
     bool idle = false;
     int m0 = 0;
+    BandRows bands;
     Pipe pipe;
     for (int g = 0;; ++g) {
         const int s = g % kS;
@@ -257,6 +258,7 @@ __global__ void __launch_bounds__(kThreads, persist_min_ctas<WV>())
             cols.init(2 * m0, xs, A.W, !kAdj, (2 * wq < 0) || (2 * wq + 2 * kWarpQ > A.W));
             idle = wq + kHQ >= A.nec;
             if constexpr (kAdj) hw.init(m0, AxisLen{A.nec, A.ndc});
+            bands.init<TB, TL>(A, tl.n0, m0, 0);
             pipe.init();
             i = 0;
         }
@@ -274,8 +276,10 @@ __global__ void __launch_bounds__(kThreads, persist_min_ctas<WV>())
             else
                 pipe.push(row);
             const int qo = tl.qfirst + i - Pipe::kLag;
-            if (qo >= tl.n0 && qo < tl.n1 && store_lane)
-                fwd_store_row<MODE_NONSEP, TB, TL>(A, row, qo, m0, 0);
+            if (qo >= tl.n0 && qo < tl.n1) {
+                if (store_lane) fwd_store_bands<TB, TL>(A, bands, row, qo, m0);
+                bands.next(A);
+            }
         } else if (lane == 0) {
             mbar_arrive(&ring.empty[s]);
         }
@@ -347,6 +351,7 @@ __global__ void __launch_bounds__(kThreads, persist_min_ctas<WV>())
     LaneW hw;
     bool idle = false;
     int m0 = 0;
+    char* out_p = nullptr;  // the lane's position in the output plane at the tile's next row
     Pipe pipe;
     for (int g = 0;; ++g) {
         const int s = g % kS;
@@ -365,6 +370,7 @@ __global__ void __launch_bounds__(kThreads, persist_min_ctas<WV>())
             cols.init(m0, tl.qx0 - kXLB, A.W, !ADJ, (2 * wq < 0) || (2 * wq + 2 * kWarpQ > A.W));
             idle = wq + kHQ >= A.nec;
             if constexpr (ADJ) hw.init(m0, AxisLen{A.nec, A.ndc});
+            out_p = reinterpret_cast<char*>(row_ptr<TO>(A.out, 2 * tl.n0, 0) + 2 * m0);
             pipe.init();
             i = 0;
         }
@@ -378,7 +384,10 @@ __global__ void __launch_bounds__(kThreads, persist_min_ctas<WV>())
             else
                 pipe.push(row);
             const int qo = tl.qfirst + i - Pipe::kLag;
-            if (qo >= tl.n0 && qo < tl.n1 && store_lane) inv_store_row<TO>(A, row, qo, m0, 0);
+            if (qo >= tl.n0 && qo < tl.n1) {
+                if (store_lane) inv_store_rows_at<TO>(A, row, qo, m0, out_p);
+                out_p += 2 * A.out.pitch;
+            }
         } else if (lane == 0) {
             mbar_arrive(&ring.empty[s]);
         }

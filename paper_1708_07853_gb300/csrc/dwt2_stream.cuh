@@ -435,30 +435,52 @@ __device__ __forceinline__ void conv_lane_row(const TI* stage, const ConvCols& c
     }
 }
 
-// Stores a finished quad row qo: the four band rows, or (MODE_ROWS) two interleaved pixel rows.
-template <int MODE, typename TB, typename TL, typename C>
-__device__ __forceinline__ void fwd_store_row(const FwdArgs& a, const QRow<C>& row, int qo, int m0,
-                                              int z) {
+// The row pass of the two-pass comparator (MODE_ROWS): stores quad row qo as two interleaved
+// pixel rows (the band-plane modes store through fwd_store_bands).
+template <typename TL, typename C>
+__device__ __forceinline__ void fwd_store_interleaved(const FwdArgs& a, const QRow<C>& row, int qo,
+                                                      int m0, int z) {
     const int col0 = 2 * m0;
-    if constexpr (MODE == MODE_ROWS) {
-        C va[2 * kQ], vc[2 * kQ];
+    C va[2 * kQ], vc[2 * kQ];
 #pragma unroll
-        for (int q = 0; q < kQ; ++q) {
-            va[2 * q] = row.a[q];
-            va[2 * q + 1] = row.b[q];
-            vc[2 * q] = row.c[q];
-            vc[2 * q + 1] = row.e[q];
-        }
-        putN<2 * kQ>(row_ptr<TL>(a.ll, 2 * qo, z) + col0, va, col0, a.W, true);
-        if (2 * qo + 1 < a.H)
-            putN<2 * kQ>(row_ptr<TL>(a.ll, 2 * qo + 1, z) + col0, vc, col0, a.W, true);
-    } else {
-        putN<kQ>(row_ptr<TL>(a.ll, qo, z) + m0, row.a, m0, a.nec, true);
-        putN<kQ>(row_ptr<TB>(a.hl, qo, z) + m0, row.b, m0, a.ndc, true);
-        if (qo < a.ndr) {
-            putN<kQ>(row_ptr<TB>(a.lh, qo, z) + m0, row.c, m0, a.nec, true);
-            putN<kQ>(row_ptr<TB>(a.hh, qo, z) + m0, row.e, m0, a.ndc, true);
-        }
+    for (int q = 0; q < kQ; ++q) {
+        va[2 * q] = row.a[q];
+        va[2 * q + 1] = row.b[q];
+        vc[2 * q] = row.c[q];
+        vc[2 * q + 1] = row.e[q];
+    }
+    putN<2 * kQ>(row_ptr<TL>(a.ll, 2 * qo, z) + col0, va, col0, a.W, true);
+    if (2 * qo + 1 < a.H) putN<2 * kQ>(row_ptr<TL>(a.ll, 2 * qo + 1, z) + col0, vc, col0, a.W, true);
+}
+
+// A lane's output positions (column m0) in the four band planes, at one quad row; advanced a
+// row at a time, so the per-row addresses cost one add per band instead of a multiply.
+struct BandRows {
+    char* p[4];  // LL, HL, LH, HH
+    template <typename TB, typename TL>
+    __device__ __forceinline__ void init(const FwdArgs& a, int q, int m0, int z) {
+        p[0] = reinterpret_cast<char*>(row_ptr<TL>(a.ll, q, z) + m0);
+        p[1] = reinterpret_cast<char*>(row_ptr<TB>(a.hl, q, z) + m0);
+        p[2] = reinterpret_cast<char*>(row_ptr<TB>(a.lh, q, z) + m0);
+        p[3] = reinterpret_cast<char*>(row_ptr<TB>(a.hh, q, z) + m0);
+    }
+    __device__ __forceinline__ void next(const FwdArgs& a) {
+        p[0] += a.ll.pitch;
+        p[1] += a.hl.pitch;
+        p[2] += a.lh.pitch;
+        p[3] += a.hh.pitch;
+    }
+};
+
+// The four band rows of finished quad row qo at the positions br holds.
+template <typename TB, typename TL, typename C>
+__device__ __forceinline__ void fwd_store_bands(const FwdArgs& a, const BandRows& br,
+                                                const QRow<C>& row, int qo, int m0) {
+    putN<kQ>(reinterpret_cast<TL*>(br.p[0]), row.a, m0, a.nec, true);
+    putN<kQ>(reinterpret_cast<TB*>(br.p[1]), row.b, m0, a.ndc, true);
+    if (qo < a.ndr) {
+        putN<kQ>(reinterpret_cast<TB*>(br.p[2]), row.c, m0, a.nec, true);
+        putN<kQ>(reinterpret_cast<TB*>(br.p[3]), row.e, m0, a.ndc, true);
     }
 }
 
@@ -571,10 +593,12 @@ __device__ __forceinline__ void inv_lane_row(const uint8_t* stage, const InvCols
     }
 }
 
-// Stores a reconstructed quad row qo as pixel rows 2qo and 2qo + 1 of the output plane.
+// Stores a reconstructed quad row qo as pixel rows 2qo and 2qo + 1 of the output plane; p is the
+// lane's position in it (pixel row 2 qo, column 2 m0), kept by the caller and advanced by two
+// rows per quad row.
 template <typename TO, typename C>
-__device__ __forceinline__ void inv_store_row(const InvArgs& a, const QRow<C>& row, int qo, int m0,
-                                              int z) {
+__device__ __forceinline__ void inv_store_rows_at(const InvArgs& a, const QRow<C>& row, int qo,
+                                                  int m0, char* p) {
     const int c0 = 2 * m0;
     C va[2 * kQ], vc[2 * kQ];
 #pragma unroll
@@ -584,9 +608,9 @@ __device__ __forceinline__ void inv_store_row(const InvArgs& a, const QRow<C>& r
         vc[2 * q] = row.c[q];
         vc[2 * q + 1] = row.e[q];
     }
-    putN<2 * kQ>(row_ptr<TO>(a.out, 2 * qo, z) + c0, va, c0, a.W, a.out_vec != 0);
+    putN<2 * kQ>(reinterpret_cast<TO*>(p), va, c0, a.W, a.out_vec != 0);
     if (2 * qo + 1 < a.H)
-        putN<2 * kQ>(row_ptr<TO>(a.out, 2 * qo + 1, z) + c0, vc, c0, a.W, a.out_vec != 0);
+        putN<2 * kQ>(reinterpret_cast<TO*>(p + a.out.pitch), vc, c0, a.W, a.out_vec != 0);
 }
 
 // Shared-memory ring: NS stages, then the full / empty barriers, the abort flag and the
@@ -705,6 +729,8 @@ __global__ void __launch_bounds__(kThreads, min_ctas<WV>())
     if constexpr (kAdj) hw.init(m0, AxisLen{args.nec, args.ndc});
     const AxisLen rows{args.ner, args.ndr};
 
+    BandRows bands;
+    if constexpr (MODE != MODE_ROWS) bands.init<TB, TL>(args, n0, m0, z);
     Pipe pipe;
     pipe.init();
 #pragma unroll row_unroll<WV>()
@@ -732,7 +758,12 @@ __global__ void __launch_bounds__(kThreads, min_ctas<WV>())
         else
             pipe.push(row);
         const int qo = qfirst + i - Pipe::kLag;
-        if (qo >= n0 && qo < n1 && store_lane) fwd_store_row<MODE, TB, TL>(args, row, qo, m0, z);
+        if constexpr (MODE == MODE_ROWS) {
+            if (qo >= n0 && qo < n1 && store_lane) fwd_store_interleaved<TL>(args, row, qo, m0, z);
+        } else if (qo >= n0 && qo < n1) {
+            if (store_lane) fwd_store_bands<TB, TL>(args, bands, row, qo, m0);
+            bands.next(args);
+        }
     }
 }
 
@@ -801,6 +832,7 @@ __global__ void __launch_bounds__(kThreads, min_ctas<WV>())
     if constexpr (ADJ) hw.init(m0, AxisLen{args.nec, args.ndc});
     const AxisLen rows{args.ner, args.ndr};
 
+    char* out_p = reinterpret_cast<char*>(row_ptr<TO>(args.out, 2 * n0, z) + 2 * m0);
     Pipe pipe;
     pipe.init();
 #pragma unroll row_unroll<WV>()
@@ -821,7 +853,10 @@ __global__ void __launch_bounds__(kThreads, min_ctas<WV>())
         else
             pipe.push(row);
         const int qo = qfirst + i - Pipe::kLag;
-        if (qo >= n0 && qo < n1 && store_lane) inv_store_row<TO>(args, row, qo, m0, z);
+        if (qo >= n0 && qo < n1) {
+            if (store_lane) inv_store_rows_at<TO>(args, row, qo, m0, out_p);
+            out_p += 2 * args.out.pitch;
+        }
     }
 }
 
