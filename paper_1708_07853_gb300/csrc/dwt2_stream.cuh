@@ -628,6 +628,20 @@ struct Ring {
     __device__ __forceinline__ uint8_t* stage(int s) const { return stage0 + size_t(s) * stage_bytes; }
 };
 
+// A position in a ring of NS stages: the stage and the parity of its current phase, advanced one
+// row at a time (no division by the ring depth per row).
+template <int NS>
+struct RingPos {
+    int s = 0;
+    uint32_t ph = 0;
+    __device__ __forceinline__ void next() {
+        if (++s == NS) {
+            s = 0;
+            ph ^= 1u;
+        }
+    }
+};
+
 template <int NS>
 __device__ __forceinline__ Ring<NS> make_ring(uint8_t* smem_raw, size_t stage_bytes) {
     Ring<NS> r;
@@ -698,10 +712,13 @@ __global__ void __launch_bounds__(kThreads, min_ctas<WV>())
 
     if (warp == kNW) {  // ------------------------------------------------------ producer
         int issued = 0;
+        RingPos<kS> rp;
         for (int i = 0; i < nrows; ++i) {
-            const int s = i % kS;
+            const int s = rp.s;
+            const uint32_t par = rp.ph;
+            rp.next();
             if (i >= kS) {
-                bool ok = mbar_wait(&ring.empty[s], ((i / kS) - 1) & 1, ring.abort, args.status);
+                bool ok = mbar_wait(&ring.empty[s], par ^ 1u, ring.abort, args.status);
                 if (!__all_sync(kFull, ok)) break;
             }
             fwd_produce_row<TI, 1, kPlain ? LOAD_PLAIN : LOAD_TMA>(
@@ -733,10 +750,13 @@ __global__ void __launch_bounds__(kThreads, min_ctas<WV>())
     if constexpr (MODE != MODE_ROWS) bands.init<TB, TL>(args, n0, m0, z);
     Pipe pipe;
     pipe.init();
+    RingPos<kS> rp;
 #pragma unroll row_unroll<WV>()
     for (int i = 0; i < nrows; ++i) {
-        const int s = i % kS;
-        bool ok = mbar_wait(&ring.full[s], (i / kS) & 1, ring.abort, args.status);
+        const int s = rp.s;
+        const uint32_t par = rp.ph;
+        rp.next();
+        bool ok = mbar_wait(&ring.full[s], par, ring.abort, args.status);
         if (!__all_sync(kFull, ok)) break;
         if (idle) {
             if (lane == 0) mbar_arrive(&ring.empty[s]);
@@ -806,10 +826,13 @@ __global__ void __launch_bounds__(kThreads, min_ctas<WV>())
         // pointers to the __grid_constant__ parameters (TMA reads the maps where they live)
         const CUtensorMap* maps[4] = {&tm_ll, &tm_hl, &tm_lh, &tm_hh};
         int issued = 0;
+        RingPos<kS> rp;
         for (int i = 0; i < nrows; ++i) {
-            const int s = i % kS;
+            const int s = rp.s;
+            const uint32_t par = rp.ph;
+            rp.next();
             if (i >= kS) {
-                bool ok = mbar_wait(&ring.empty[s], ((i / kS) - 1) & 1, ring.abort, args.status);
+                bool ok = mbar_wait(&ring.empty[s], par ^ 1u, ring.abort, args.status);
                 if (!__all_sync(kFull, ok)) break;
             }
             inv_produce_row<TL, TB>(args, maps, ADJ, qfirst + i, xb, ring.stage(s), &ring.full[s],
@@ -835,10 +858,13 @@ __global__ void __launch_bounds__(kThreads, min_ctas<WV>())
     char* out_p = reinterpret_cast<char*>(row_ptr<TO>(args.out, 2 * n0, z) + 2 * m0);
     Pipe pipe;
     pipe.init();
+    RingPos<kS> rp;
 #pragma unroll row_unroll<WV>()
     for (int i = 0; i < nrows; ++i) {
-        const int s = i % kS;
-        bool ok = mbar_wait(&ring.full[s], (i / kS) & 1, ring.abort, args.status);
+        const int s = rp.s;
+        const uint32_t par = rp.ph;
+        rp.next();
+        bool ok = mbar_wait(&ring.full[s], par, ring.abort, args.status);
         if (!__all_sync(kFull, ok)) break;
         if (idle) {
             if (lane == 0) mbar_arrive(&ring.empty[s]);
