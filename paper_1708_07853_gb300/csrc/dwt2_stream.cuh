@@ -27,9 +27,10 @@ constexpr int kWarpOut = kWarpQ - 2 * kHQ;  // output quads per warp (30 lanes)
 constexpr int kCtaQ = kNW * kWarpOut;    // output quads per CTA strip
 constexpr int kThreads = 32 * (kNW + 1);
 // Resident CTAs per SM the kernels are compiled for.  Measured on GB300: holding the cheap
-// wavelets (integer and float CDF 5/3) to 64 registers for 6 CTAs per SM is 7% faster.  The CDF
-// 9/7 kernels are left free (about 85 registers, 4 CTAs per SM): bound to 5 CTAs per SM (72
-// registers, no spills) the forward measured 6% and the inverse 9% slower.
+// wavelets (integer and float CDF 5/3) to 64 registers for 6 CTAs per SM was 7% faster with an
+// 8-stage ring (their 12-stage ring now holds them to 4 CTAs per SM by shared memory, which is
+// faster still).  The CDF 9/7 kernels are left free (78-80 registers, 4 CTAs per SM): bound to
+// 5 CTAs per SM (72 registers, no spills) the forward measured 6% and the inverse 9% slower.
 template <int WV>
 constexpr int min_ctas() {
     return WV == 2 ? 1 : 6;
