@@ -167,14 +167,15 @@ __device__ __forceinline__ uint8_t* align128(uint8_t* p) {
 // the caller's own image takes this path (every scratch plane is TMA-eligible), so nothing the
 // running kernel writes is read here.
 //   transform (mirrored rows): each row is copied as the 16-byte-aligned chunks that hold its
-//     elements xs .. xs + kSRow - 1, in one bulk copy per row, so the row lands shifted by the
+//     elements xs .. xs + kSRow - 1 -- in one bulk copy per row issued by lane 0 (kBulk), or as
+//     16-byte cp.async chunks spread over the lanes -- so the row lands shifted by the
 //     misalignment m (0 .. 16 / sizeof(TI) - 1 elements) of element xs: element c sits at stage
 //     index c - xs + m.  The copied chunks are those holding at least one element of the row: a
 //     chunk that straddles an end of the row reads at most 15 bytes beyond it, inside the same
 //     16-byte block (so inside mapped memory); those stage entries are never read (the
-//     consumers read mirrored columns at the plane's edges).  Like a TMA load, the copy
-//     completes on the stage's full barrier with its byte count.  The shifts go to *shift_slot
-//     (row 0 in bits 0-3, row 1 in bits 4-7).
+//     consumers read mirrored columns at the plane's edges).  Like a TMA load, a bulk copy
+//     completes on the stage's full barrier with its byte count; cp.async chunks arrive on it
+//     when they land.  The shifts go to *shift_slot (row 0 in bits 0-3, row 1 in bits 4-7).
 //   adjoint (zeros outside the plane): 4-byte zero-filling cp.async copies (16-bit elements, below
 //     cp.async's minimum, are loaded before the first shared-memory store), no shift.
 // Either way the stage's full barrier completes when the copies have landed, so every stage of
