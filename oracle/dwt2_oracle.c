@@ -17,6 +17,9 @@
  * Readings where the paper is silent (wavelet constants, 9/7 normalisation, integer rounding,
  * boundary handling, length-1 axes) are stated next to the code that takes them.
  */
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 #include "dwt2_oracle.h"
 
 #include <stdlib.h>
@@ -144,28 +147,40 @@ static void line_step_adj_f(double* g, long n, long s, int parity, double coef) 
     }
 }
 
-/* A step along every row (horizontal, the paper's P / U) or every column (vertical, P* / U*). */
+/* A step along every row (horizontal, the paper's P / U) or every column (vertical, P* / U*).
+ * The lines of one step are independent (a line step reads and writes its own line only), so
+ * with more than one thread (orc_set_threads) they are shared out among the threads; each line
+ * is still computed by one thread in the same order, so the results do not depend on it. */
 enum { AX_ROWS = 0, AX_COLS = 1 };
 
 static void plane_step_f(double* x, long H, long W, int axis, int parity, double coef, int mirror) {
-    if (axis == AX_ROWS)
+    if (axis == AX_ROWS) {
+#pragma omp parallel for schedule(static)
         for (long r = 0; r < H; ++r) line_step_f(x + r * W, W, 1, parity, coef, mirror);
-    else
+    } else {
+#pragma omp parallel for schedule(static)
         for (long c = 0; c < W; ++c) line_step_f(x + c, H, W, parity, coef, mirror);
+    }
 }
 
 static void plane_step_i(int64_t* x, long H, long W, int axis, int parity, int sign, int mirror) {
-    if (axis == AX_ROWS)
+    if (axis == AX_ROWS) {
+#pragma omp parallel for schedule(static)
         for (long r = 0; r < H; ++r) line_step_i(x + r * W, W, 1, parity, sign, mirror);
-    else
+    } else {
+#pragma omp parallel for schedule(static)
         for (long c = 0; c < W; ++c) line_step_i(x + c, H, W, parity, sign, mirror);
+    }
 }
 
 static void plane_step_adj_f(double* g, long H, long W, int axis, int parity, double coef) {
-    if (axis == AX_ROWS)
+    if (axis == AX_ROWS) {
+#pragma omp parallel for schedule(static)
         for (long r = 0; r < H; ++r) line_step_adj_f(g + r * W, W, 1, parity, coef);
-    else
+    } else {
+#pragma omp parallel for schedule(static)
         for (long c = 0; c < W; ++c) line_step_adj_f(g + c, H, W, parity, coef);
+    }
 }
 
 /* ------------------------------------------------------------------------------------------
@@ -620,20 +635,20 @@ static void scale_quad_f(quad_f_t* q, long h, long w, int wavelet, int divide) {
  * constant part reads index ur(m) and the neighbour part ul(m), as the plain update does.
  * ---------------------------------------------------------------------------------------- */
 
-/* M_P(P0): [1 0 0 0; p 1 0 0; p 0 1 0; p^2 p p 1] on each quad (reads the quad only). */
+/* M_P(P0) = [1 0 0 0; p 1 0 0; p 0 1 0; p^2 p p 1] on each quad (reads the quad only), computed,
+ * as Sec. 3 computes the constant parts, with the separable scheme: the horizontal step
+ * b += p a, e += p c, then the vertical step c += p a, e += p b (b as the horizontal step left
+ * it).  Multiplied out, e gains p c + p b + p^2 a: the matrix above. */
 static void adapted_predict_local_f(quad_f_t* q, double p) {
     geom_t g = q->g;
-    quad_f_t o = {g, dup_f(q->a, g.ner * g.nec), dup_f(q->b, g.ner * g.ndc),
-                  dup_f(q->c, g.ndr * g.nec), dup_f(q->e, g.ndr * g.ndc)};
-    for (long n = 0; n < g.ner; ++n)
-        for (long m = 0; m < g.ndc; ++m) B_(q, n, m) = B_(&o, n, m) + p * A_(&o, n, m);
+    for (long n = 0; n < g.ner; ++n) /* horizontal */
+        for (long m = 0; m < g.ndc; ++m) B_(q, n, m) += p * A_(q, n, m);
     for (long n = 0; n < g.ndr; ++n)
-        for (long m = 0; m < g.nec; ++m) C_(q, n, m) = C_(&o, n, m) + p * A_(&o, n, m);
+        for (long m = 0; m < g.ndc; ++m) E_(q, n, m) += p * C_(q, n, m);
+    for (long n = 0; n < g.ndr; ++n) /* vertical */
+        for (long m = 0; m < g.nec; ++m) C_(q, n, m) += p * A_(q, n, m);
     for (long n = 0; n < g.ndr; ++n)
-        for (long m = 0; m < g.ndc; ++m)
-            E_(q, n, m) = E_(&o, n, m) + p * C_(&o, n, m) + p * B_(&o, n, m) +
-                          p * p * A_(&o, n, m);
-    free(o.a); free(o.b); free(o.c); free(o.e);
+        for (long m = 0; m < g.ndc; ++m) E_(q, n, m) += p * B_(q, n, m);
 }
 
 /* M_P(P1): [1 0 0 0; pz 1 0 0; pz_n 0 1 0; p^2 z z_n, pz_n, pz, 1] (neighbours m+1, n+1). */
@@ -656,29 +671,25 @@ static void adapted_predict_fused_f(quad_f_t* q, double p) {
     free(o.a); free(o.b); free(o.c); free(o.e);
 }
 
-/* M_U(U0): [1 u u u^2; 0 1 0 u; 0 0 1 u; 0 0 0 1] on each quad (own samples of the extension). */
+/* M_U(U0) = [1 u u u^2; 0 1 0 u; 0 0 1 u; 0 0 0 1] on each quad (own samples of the extension),
+ * with the separable scheme: the horizontal step a += u b, c += u e, then the vertical step
+ * a += u c, b += u e (c as the horizontal step left it).  Multiplied out, a gains
+ * u b + u c + u^2 e: the matrix above.  The "own" sample of the last quad of an odd-length axis
+ * is the mirrored one (ur_). */
 static void adapted_update_local_f(quad_f_t* q, double u) {
     geom_t g = q->g;
-    quad_f_t o = {g, dup_f(q->a, g.ner * g.nec), dup_f(q->b, g.ner * g.ndc),
-                  dup_f(q->c, g.ndr * g.nec), dup_f(q->e, g.ndr * g.ndc)};
-    for (long n = 0; n < g.ner; ++n)
-        for (long m = 0; m < g.nec; ++m) {
-            double v = A_(&o, n, m);
-            long mr = ur_(m, g.ndc), nr = ur_(n, g.ndr);
-            if (g.ndc) v += u * B_(&o, n, mr);
-            if (g.ndr) v += u * C_(&o, nr, m);
-            if (g.ndr && g.ndc) v += u * u * E_(&o, nr, mr);
-            A_(q, n, m) = v;
-        }
-    if (g.ndr)
+    if (g.ndc) { /* horizontal */
         for (long n = 0; n < g.ner; ++n)
-            for (long m = 0; m < g.ndc; ++m)
-                B_(q, n, m) = B_(&o, n, m) + u * E_(&o, ur_(n, g.ndr), m);
-    if (g.ndc)
+            for (long m = 0; m < g.nec; ++m) A_(q, n, m) += u * B_(q, n, ur_(m, g.ndc));
         for (long n = 0; n < g.ndr; ++n)
-            for (long m = 0; m < g.nec; ++m)
-                C_(q, n, m) = C_(&o, n, m) + u * E_(&o, n, ur_(m, g.ndc));
-    free(o.a); free(o.b); free(o.c); free(o.e);
+            for (long m = 0; m < g.nec; ++m) C_(q, n, m) += u * E_(q, n, ur_(m, g.ndc));
+    }
+    if (g.ndr) { /* vertical */
+        for (long n = 0; n < g.ner; ++n)
+            for (long m = 0; m < g.nec; ++m) A_(q, n, m) += u * C_(q, ur_(n, g.ndr), m);
+        for (long n = 0; n < g.ner; ++n)
+            for (long m = 0; m < g.ndc; ++m) B_(q, n, m) += u * E_(q, ur_(n, g.ndr), m);
+    }
 }
 
 /* M_U(U1): [1 uz^-1 uz_n^-1 u^2 z^-1 z_n^-1; 0 1 0 uz_n^-1; 0 0 1 uz^-1; 0 0 0 1]. */
@@ -849,6 +860,18 @@ static int level_inv_adj_f(const double* gx_in, long h, long w, int wavelet, dou
  * bands of ceil/floor halves.  The band list is LL_J, then HL_J, LH_J, HH_J, ..., HL_1, LH_1,
  * HH_1, each dense.
  * ---------------------------------------------------------------------------------------- */
+/* Threads for the line loops of the separable steps (1 = the plain sequential oracle, the
+ * default).  Returns the count in effect (1 when built without OpenMP). */
+int orc_set_threads(int n) {
+#ifdef _OPENMP
+    omp_set_num_threads(n < 1 ? 1 : n);
+    return n < 1 ? 1 : n;
+#else
+    (void)n;
+    return 1;
+#endif
+}
+
 int orc_max_levels(int H, int W) {
     long n = H > W ? H : W;
     int L = 0;

@@ -48,6 +48,11 @@ enum { ORC_SEP_EQ3 = 0, ORC_SEP_ROWS = 1, ORC_SEP_COLS = 2, ORC_NONSEP_EQ5 = 3, 
  *   1: the signal is first extended by repeated whole-sample reflection (period 2N-2) and
  *      lifted with no boundary rule at all, then cropped.  Both must agree. */
 
+/* Threads for the line loops of the separable steps (default 1, the sequential oracle).  More
+ * threads share out the independent lines of each 1-D step; every value is computed the same
+ * way, so results are bit-identical for any count.  Returns the count in effect. */
+int orc_set_threads(int n);
+
 int orc_max_levels(int H, int W);
 /* number of elements of the concatenated band list for (H, W, levels) */
 int64_t orc_coeff_count(int H, int W, int levels);

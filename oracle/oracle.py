@@ -24,14 +24,15 @@ SCHEMES = {"eq3": 0, "rows": 1, "cols": 2, "eq5": 3, "adapted": 4}
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle with gcc into oracle/liboracle.so (plain -O2, single thread)."""
+    """Compile the oracle with gcc into oracle/liboracle.so (plain -O2).  OpenMP, when gcc has
+    it, only shares out independent lines among threads (set_threads; one thread by default)."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < max(
         os.path.getmtime(_SRC), os.path.getmtime(os.path.join(_HERE, "dwt2_oracle.h"))
     ):
         tmp = _LIB + f".tmp{os.getpid()}"
-        subprocess.check_call(
-            ["gcc", "-std=c11", "-O2", "-fPIC", "-shared", "-Wall", "-o", tmp, _SRC]
-        )
+        base = ["gcc", "-std=c11", "-O2", "-fPIC", "-shared", "-Wall", "-o", tmp, _SRC]
+        if subprocess.call(base + ["-fopenmp"], stderr=subprocess.DEVNULL) != 0:
+            subprocess.check_call(base)
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -44,6 +45,8 @@ def _load():
     if _lib is None:
         lib = ctypes.CDLL(build())
         vp, i = ctypes.c_void_p, ctypes.c_int
+        lib.orc_set_threads.argtypes = [i]
+        lib.orc_set_threads.restype = i
         lib.orc_max_levels.argtypes = [i, i]
         lib.orc_max_levels.restype = i
         lib.orc_coeff_count.argtypes = [i, i, i]
@@ -58,6 +61,7 @@ def _load():
         for f in ("orc_forward", "orc_inverse", "orc_forward_adjoint", "orc_inverse_adjoint",
                   "orc_nonsep_steps", "orc_adapted_steps", "orc_adapted_apply"):
             getattr(lib, f).restype = i
+        lib.orc_set_threads(1)  # the sequential oracle unless a caller asks for more threads
         _lib = lib
     return _lib
 
@@ -68,6 +72,12 @@ def _wid(wavelet) -> int:
 
 def _dtype(wavelet):
     return np.int64 if _wid(wavelet) == 0 else np.float64
+
+
+def set_threads(n: int) -> int:
+    """Threads for the oracle's line loops (1 = sequential, the default); the results are the
+    same bits for any count.  Returns the count in effect (1 without OpenMP)."""
+    return _load().orc_set_threads(int(n))
 
 
 def max_levels(H: int, W: int) -> int:

@@ -284,6 +284,28 @@ def test_constant_input(wavelet):
                 assert np.abs(band).max() <= tol
 
 
+@pytest.mark.parametrize("wavelet", ["cdf53", "cdf97"])
+def test_dc_level_shift_is_exact(wavelet):
+    """The float kernels transform x - c and add c back to LL_J (a DC level shift that keeps
+    their fp32 intermediates small).  By linearity and the constant-input facts above (LL gain
+    1, zero high-pass) that is the same transform: W(x - c) + c e_LL = W(x), and the inverse
+    of the bands with LL_J - c, plus c, is the inverse of the bands.  Checked on odd sizes,
+    length-1 axes and every level count, where the symmetric extension meets the boundary."""
+    rng = np.random.default_rng(17)
+    for H, W in [(1, 9), (6, 1), (13, 9), (33, 64), (40, 17)]:
+        x = rng.uniform(0, 255, (H, W))
+        for lv in range(1, O.max_levels(H, W) + 1):
+            c = 131.0
+            want = O.forward(x, wavelet, lv)
+            got = O.forward(x - c, wavelet, lv)
+            got[0] = got[0] + c
+            for g, w in zip(got, want):
+                assert np.abs(g - w).max(initial=0) <= 1e-12 * 255, (H, W, lv)
+            shifted = [want[0] - c] + list(want[1:])
+            r = O.inverse(shifted, H, W, wavelet, lv) + c
+            assert np.abs(r - x).max() <= 1e-12 * 255, (H, W, lv)
+
+
 def _h1d(x, wavelet):
     return O.forward(np.asarray(x)[None, :], wavelet, 1)[1].ravel()
 
@@ -393,6 +415,27 @@ def test_adjoint_dot_product(wavelet):
 
 
 # ----------------------------------------------------------------------------- layout, args
+
+def test_threads_do_not_change_results():
+    """The multi-threaded oracle (the CPU baseline over all host cores) only shares out the
+    independent lines of each 1-D step among threads: every value is the same bits."""
+    rng = np.random.default_rng(3)
+    x = rng.uniform(0, 255, (301, 517))
+    xi = rng.integers(-(2 ** 15), 2 ** 15, (301, 517))
+    try:
+        O.set_threads(4)
+        many = [O.forward(x, "cdf97", 4), O.forward(xi, "cdf53_int", 4),
+                O.forward_adjoint(O.forward(x, "cdf97", 4), 301, 517, "cdf97", 4)]
+        many.append(O.inverse(many[0], 301, 517, "cdf97", 4))
+    finally:
+        O.set_threads(1)
+    one = [O.forward(x, "cdf97", 4), O.forward(xi, "cdf53_int", 4),
+           O.forward_adjoint(O.forward(x, "cdf97", 4), 301, 517, "cdf97", 4)]
+    one.append(O.inverse(one[0], 301, 517, "cdf97", 4))
+    for a, b in zip(many, one):
+        for u, v in zip(a if isinstance(a, list) else [a], b if isinstance(b, list) else [b]):
+            assert np.array_equal(u, v)
+
 
 def test_layout_and_level_limits():
     assert O.max_levels(1, 1) == 1
