@@ -311,13 +311,19 @@ int dwt2_selftest_wait_timeout(int which, void* workspace, size_t ws_bytes, void
  *     exceeds it; 4096 x 4096 fp32 or int32 fits at any level count, and one level fits at any
  *     size.
  *   - It allocates nothing: no cudaMalloc, no cudaFree, no allocating library call.
- *   - The first call on each device looks up the scratch's device address on the current
- *     device; make that first call before any stream capture.
- *   - Every call clears the status word at the start of the scratch on stream; the scratch keeps
- *     the previous call's contents otherwise.  All calls share the one scratch array: calls
- *     that may run at the same time on the GPU (other streams, other host threads) race and must
- *     be ordered by the caller.  Device-side wait timeouts are recorded only in that scratch and
- *     are not reported by this entry point. */
+ *   - Every call looks up the scratch's device address in the current device's current context
+ *     (a host-side lookup, so a device reset or a switch of context is followed); the first
+ *     call in a context also loads the library's device code there: make that first call
+ *     before any stream capture.
+ *   - Invalid arguments are rejected before anything is queued on the stream.  A valid call
+ *     clears the status word at the start of the scratch on stream; the scratch keeps the
+ *     previous call's contents otherwise.  All calls share the one scratch array: calls that may
+ *     run at the same time on the GPU (other streams, other host threads) race and must be
+ *     ordered by the caller.
+ *   - Device-side wait timeouts (see dwt2_selftest_wait_timeout) are recorded only in that
+ *     scratch, which the caller cannot read, and the next call clears them: this entry point
+ *     does not report them.  A caller that must learn of a timeout uses dwt2_forward with a
+ *     workspace and dwt2_check_status. */
 #define DWT2_STATIC_SCRATCH_BYTES (24u << 20)
 int dwt2_forward_static(const void* img, int64_t img_pitch_bytes, int H, int W, int img_dtype,
                         void* coeffs, int wavelet, int levels, int band_dtype, void* stream);

@@ -265,12 +265,30 @@ static int check_batch(const Batch& b, int H, int64_t img_pitch, int img_dtype, 
 // Bytes between the workspace regions of consecutive images of a batch.
 static int64_t ws_region(const WsPlan& wp) { return align_up(wp.bytes - kHeader, 256); }
 
+// The DC level shift of a float transform (ShiftSrc in dwt2_stream.cuh): c is sampled from the
+// plane p (the image for a forward transform, LL_J for an inverse), taken off at the first
+// level and put back at the last.  mode: kShiftIn and / or kShiftOut for this level.
+static ShiftSrc shift_from(const void* p, int64_t pitch, int64_t bstride, int h, int w, int dt,
+                           int mode) {
+    ShiftSrc s;
+    s.ptr = mode ? p : nullptr;
+    s.pitch = pitch;
+    s.bstride = bstride;
+    s.h = h;
+    s.w = w;
+    s.dt = dt;
+    s.mode = mode;
+    return s;
+}
+
 // adjoint = true: W^-T, the transpose of the inverse (image-shaped gradient in, band gradients
 // out), level by level 1..J with the forward kernel's data flow.
+// clear_status: zero the workspace's status header on st once the arguments have passed every
+// check (the built-in scratch of dwt2_forward_static, which no caller can initialise).
 static int forward_impl(const void* img, int64_t img_pitch, int H, int W, int img_dtype,
                         void* coeffs, void* ws, size_t ws_bytes, int wavelet, int J,
                         int band_dtype, int scheme, cudaStream_t st, bool adjoint = false,
-                        Batch bt = Batch{1, 0, 0}) {
+                        Batch bt = Batch{1, 0, 0}, bool clear_status = false) {
     int rc = check_types(wavelet, img_dtype, band_dtype);
     if (rc) return rc;
     if (adjoint && (wavelet == WV_CDF53_INT || img_dtype != DT_F32 || band_dtype != DT_F32))
@@ -290,6 +308,10 @@ static int forward_impl(const void* img, int64_t img_pitch, int H, int W, int im
     const int64_t region = ws_region(wp);
     if (int64_t(ws_bytes) < kHeader + bt.N * region) return DWT2_ENOMEM;
     const int64_t cbs = bt.N > 1 ? bt.coeff_bstride : 0;
+    if (clear_status) {
+        const cudaError_t e = cudaMemsetAsync(ws, 0, kHeader, st);
+        if (e != cudaSuccess) return cuda_fail(e, "status header");
+    }
 
     char* cb = static_cast<char*>(coeffs);
     char* wb = static_cast<char*>(ws);
@@ -299,9 +321,13 @@ static int forward_impl(const void* img, int64_t img_pitch, int H, int W, int im
     const void* in = img;
     int64_t in_pitch = img_pitch, in_bstride = bt.N > 1 ? bt.img_bstride : 0;
     int in_dt = img_dtype;
+    // float lifting takes the DC level shift; the adjoint and the convolution scheme do not
+    const bool shifted = wavelet != WV_CDF53_INT && !adjoint && scheme != DWT2_SCHEME_CONV;
     for (int j = 1; j <= J; ++j) {
         const int h = L.h[j - 1], w = L.w[j - 1];
         FwdArgs a = level_args(in, in_pitch, in_bstride, h, w, bt.N, status);
+        const int smode = shifted ? (j == 1 ? kShiftIn : 0) | (j == J ? kShiftOut : 0) : 0;
+        a.shift = shift_from(img, img_pitch, bt.N > 1 ? bt.img_bstride : 0, H, W, img_dtype, smode);
         const dwt2_band &bhl = band_of(L, j, 0), &blh = band_of(L, j, 1), &bhh = band_of(L, j, 2);
         a.hl = {cb + bhl.offset_bytes, bhl.pitch_bytes, cbs};
         a.lh = {cb + blh.offset_bytes, blh.pitch_bytes, cbs};
@@ -318,6 +344,8 @@ static int forward_impl(const void* img, int64_t img_pitch, int H, int W, int im
             bool tma = mr == MAP_OK;
             FwdArgs r = a;
             r.ll = {wb + wp.off[2], wp.pitch[2], 0};
+            r.shift.mode &= kShiftIn;  // the row pass takes the shift off the image
+            if (!r.shift.mode) r.shift.ptr = nullptr;
             e = launch_fwd(wavelet, MODE_ROWS, in_dt, band_dtype, tma, tm, r, st);
             if (e != cudaSuccess) return cuda_fail(e, "row pass");
             FwdArgs c = level_args(wb + wp.off[2], wp.pitch[2], 0, h, w, 1, status);
@@ -325,6 +353,9 @@ static int forward_impl(const void* img, int64_t img_pitch, int H, int W, int im
             c.hl = a.hl;
             c.lh = a.lh;
             c.hh = a.hh;
+            c.shift = a.shift;  // the column pass puts it back onto LL_J
+            c.shift.mode &= kShiftOut;
+            if (!c.shift.mode) c.shift.ptr = nullptr;
             mr = make_map(&tm, wb + wp.off[2], wp.pitch[2], 0, h, w, 1, ll_dt, kBoxW);
             if (mr == MAP_ERROR) return DWT2_EINTERNAL;
             tma = mr == MAP_OK;
@@ -383,10 +414,14 @@ static int inverse_impl(const void* coeffs, void* img, int64_t img_pitch, int H,
     int* status = reinterpret_cast<int*>(wb);
     const int ll_dt = wavelet == WV_CDF53_INT ? DT_I32 : DT_F32;
 
+    const bool shifted = wavelet != WV_CDF53_INT && !adjoint;
     for (int j = J; j >= 1; --j) {
         const int h = L.h[j - 1], w = L.w[j - 1];
         InvArgs a;
         std::memset(&a, 0, sizeof(a));
+        const int smode = shifted ? (j == J ? kShiftIn : 0) | (j == 1 ? kShiftOut : 0) : 0;
+        a.shift = shift_from(cb + L.band[0].offset_bytes, L.band[0].pitch_bytes, cbs, L.h[J],
+                             L.w[J], DT_F32, smode);
         a.H = h;
         a.W = w;
         a.ner = (h + 1) / 2;
@@ -449,6 +484,15 @@ static int inverse_impl(const void* coeffs, void* img, int64_t img_pitch, int H,
         if (e != cudaSuccess) return cuda_fail(e, "inverse level");
     }
     return DWT2_OK;
+}
+
+// The forward transform of dwt2_forward_static: dwt2_forward into the built-in scratch, whose
+// status header is cleared once the arguments are known to be valid.
+int forward_into_scratch(const void* img, int64_t img_pitch, int H, int W, int img_dtype,
+                         void* coeffs, void* scratch, size_t scratch_bytes, int wavelet, int J,
+                         int band_dtype, cudaStream_t st) {
+    return forward_impl(img, img_pitch, H, W, img_dtype, coeffs, scratch, scratch_bytes, wavelet,
+                        J, band_dtype, DWT2_SCHEME_NONSEP, st, false, Batch{1, 0, 0}, true);
 }
 
 // ------------------------------------------------------------------ helpers for batched plans

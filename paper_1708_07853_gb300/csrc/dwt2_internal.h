@@ -38,4 +38,10 @@ cudaError_t launch_fwd_persistent(int wavelet, int mode, int tb, const PersistAr
 cudaError_t launch_inv_persistent(int wavelet, bool adj, int tb, const PersistArgs<InvUnit>& p,
                                   int ctas_per_sm, cudaStream_t st, int* occ);
 
+// dwt2_forward with the status header of the workspace cleared after the argument checks (the
+// built-in scratch of dwt2_forward_static).
+int forward_into_scratch(const void* img, int64_t img_pitch, int H, int W, int img_dtype,
+                         void* coeffs, void* scratch, size_t scratch_bytes, int wavelet, int J,
+                         int band_dtype, cudaStream_t st);
+
 }  // namespace dwt2

@@ -110,6 +110,48 @@ __device__ __forceinline__ void scale_row(QRow<float>& r, float sa, float sb, fl
     }
 }
 
+// Adds v to every component of a float row (the DC level shift of the first forward level and
+// of the last inverse level); integer rows are never shifted.
+template <typename C>
+__device__ __forceinline__ void add_row(QRow<C>& r, float v) {
+    if constexpr (kPacked<C>) {
+        const float2 w = make_float2(v, v);
+        put2(r.a, __fadd2_rn(v2(r.a), w));
+        put2(r.b, __fadd2_rn(v2(r.b), w));
+        put2(r.c, __fadd2_rn(v2(r.c), w));
+        put2(r.e, __fadd2_rn(v2(r.e), w));
+    } else if constexpr (std::is_same<C, float>::value) {
+#pragma unroll
+        for (int q = 0; q < kQ; ++q) {
+            r.a[q] += v;
+            r.b[q] += v;
+            r.c[q] += v;
+            r.e[q] += v;
+        }
+    }
+}
+// The same with scalar adds (the forward stages, whose arithmetic is scalar).
+__device__ __forceinline__ void add_row_scalar(QRow<float>& r, float v) {
+#pragma unroll
+    for (int q = 0; q < kQ; ++q) {
+        r.a[q] += v;
+        r.b[q] += v;
+        r.c[q] += v;
+        r.e[q] += v;
+    }
+}
+__device__ __forceinline__ void add_row_scalar(QRow<int32_t>&, float) {}
+// The same on the LL component only (the shift of LL_J entering the inverse).
+template <typename C>
+__device__ __forceinline__ void add_ll(QRow<C>& r, float v) {
+    if constexpr (kPacked<C>) {
+        put2(r.a, __fadd2_rn(v2(r.a), make_float2(v, v)));
+    } else if constexpr (std::is_same<C, float>::value) {
+#pragma unroll
+        for (int q = 0; q < kQ; ++q) r.a[q] += v;
+    }
+}
+
 // =============================================================================================
 // Non-separable scheme (Sec. 3, Eq. 5).
 //
@@ -301,83 +343,87 @@ struct InvPredictNS {
 // fused step with P1 / U1:
 //   M_P(P) = M_P(P1) M_P(P0),  M_P(P0) = [1 0 0 0; p 1 0 0; p 0 1 0; p^2 p p 1],
 //   M_U(U) = M_U(U1) M_U(U0),  M_U(U0) = [1 u u u^2; 0 1 0 u; 0 0 1 u; 0 0 0 1].
+// Sec. 3 evaluates the constant parts with the separable scheme, which has the fewest
+// operations: the local steps are a horizontal then a vertical 1-D step, 4 FMAs per quad
+// instead of the 5 of the multiplied-out matrix.  The fused steps are evaluated in the factored
+// form of the plain scheme (the P1* / U1* term applied to P1's / U1's result), also 4 FMAs.
 // The same linear map as the plain scheme; fp32 rounding differs.
 // =============================================================================================
 
-// Local predict on arrival, then the fused P1 step one row later (lag 1):
-//   b' = b + p a,  c' = c + p a,  e' = e + p c + p b + p^2 a            (quad only)
-//   HL = b' + p a[m+1],  LH = c' + p a[n+1],
-//   HH = e' + p^2 a[n+1][m+1] + p b'[n+1] + p c'[m+1]
+// Local predict on arrival (separable: b' = b + p a, t = e + p c, then c' = c + p a,
+// e' = t + p b'), then the fused P1 step, factored like PredictNS (lag 1):
+//   hl = b' + p a[m+1],  LH = c' + p a[n+1],  HH = (e' + p c'[m+1]) + p hl[n+1]
+//      ( = e' + p^2 a[n+1][m+1] + p b'[n+1] + p c'[m+1] ).
+// State carried to the next push: row n's a, hl, c', and e' + p c'[m+1].
 struct AdaptedPredict {
-    float p, pp;
-    QRow<float> x;        // row n: a, b', c', e'
-    float xar[kQ], xcr[kQ];  // row n: a[m+1], c'[m+1]
+    float p;
+    QRow<float> x;  // row n: a, hl (in b), c', t (in e)
     __device__ __forceinline__ void init(float p_) {
         p = p_;
-        pp = p_ * p_;
         zero_row(x);
-#pragma unroll
-        for (int q = 0; q < kQ; ++q) xar[q] = xcr[q] = 0.f;
     }
     __device__ __forceinline__ void push(const QRow<float>& y, QRow<float>& o) {
-        QRow<float> n;  // row n + 1 after the local step
+        QRow<float> n;  // row n + 1: a, hl, c', t
+        float lb[kQ], le[kQ];
 #pragma unroll
-        for (int q = 0; q < kQ; ++q) {
-            n.a[q] = y.a[q];
-            n.b[q] = fmaf(p, y.a[q], y.b[q]);
+        for (int q = 0; q < kQ; ++q) {  // local step, horizontal then vertical
+            lb[q] = fmaf(p, y.a[q], y.b[q]);
+            le[q] = fmaf(p, y.c[q], y.e[q]);
             n.c[q] = fmaf(p, y.a[q], y.c[q]);
-            n.e[q] = fmaf(pp, y.a[q], fmaf(p, y.b[q], fmaf(p, y.c[q], y.e[q])));
+            le[q] = fmaf(p, lb[q], le[q]);
         }
         float yar[kQ], ycr[kQ];
         right_of(y.a, yar);
         right_of(n.c, ycr);
 #pragma unroll
         for (int q = 0; q < kQ; ++q) {
-            o.a[q] = x.a[q];
-            o.b[q] = fmaf(p, xar[q], x.b[q]);
-            o.c[q] = fmaf(p, n.a[q], x.c[q]);
-            o.e[q] = fmaf(p, xcr[q], fmaf(p, n.b[q], fmaf(pp, yar[q], x.e[q])));
+            n.a[q] = y.a[q];
+            n.b[q] = fmaf(p, yar[q], lb[q]);
+            n.e[q] = fmaf(p, ycr[q], le[q]);
         }
-        x = n;
 #pragma unroll
         for (int q = 0; q < kQ; ++q) {
-            xar[q] = yar[q];
-            xcr[q] = ycr[q];
+            o.a[q] = x.a[q];
+            o.b[q] = x.b[q];
+            o.c[q] = fmaf(p, n.a[q], x.c[q]);
+            o.e[q] = fmaf(p, n.b[q], x.e[q]);
         }
+        x = n;
     }
 };
 
-// Local update, then the fused U1 step, both on the row as it arrives (lag 0):
-//   a' = a + u b + u c + u^2 e,  b' = b + u e,  c' = c + u e            (quad only)
-//   LL = a' + u b'[m-1] + u c'[n-1] + u^2 e[n-1][m-1],  HL = b' + u e[n-1],  LH = c' + u e[m-1]
+// Local update (separable: a1 = a + u b, c' = c + u e, then a' = a1 + u c', b' = b + u e), then
+// the fused U1 step, factored like UpdateNS, both on the row as it arrives (lag 0):
+//   LH = c' + u e[m-1],  LL = a' + u b'[m-1] + u LH[n-1],  HL = b' + u e[n-1]
+//      ( LL = a' + u b'[m-1] + u c'[n-1] + u^2 e[n-1][m-1] ).
 struct AdaptedUpdate {
-    float u, uu;
-    float pc[kQ], pe[kQ], pel[kQ];  // row n - 1: c', e, e[m-1]
+    float u;
+    float plh[kQ], pe[kQ];  // row n - 1: LH, e
     __device__ __forceinline__ void init(float u_) {
         u = u_;
-        uu = u_ * u_;
 #pragma unroll
-        for (int q = 0; q < kQ; ++q) pc[q] = pe[q] = pel[q] = 0.f;
+        for (int q = 0; q < kQ; ++q) plh[q] = pe[q] = 0.f;
     }
     __device__ __forceinline__ void push(QRow<float>& r) {
         float a[kQ], b[kQ], c[kQ];
 #pragma unroll
-        for (int q = 0; q < kQ; ++q) {
-            a[q] = fmaf(uu, r.e[q], fmaf(u, r.c[q], fmaf(u, r.b[q], r.a[q])));
-            b[q] = fmaf(u, r.e[q], r.b[q]);
+        for (int q = 0; q < kQ; ++q) {  // local step, horizontal then vertical
+            a[q] = fmaf(u, r.b[q], r.a[q]);
             c[q] = fmaf(u, r.e[q], r.c[q]);
+            a[q] = fmaf(u, c[q], a[q]);
+            b[q] = fmaf(u, r.e[q], r.b[q]);
         }
         float bl[kQ], el[kQ];
         left_of(b, bl);
         left_of(r.e, el);
 #pragma unroll
         for (int q = 0; q < kQ; ++q) {
-            r.a[q] = fmaf(uu, pel[q], fmaf(u, pc[q], fmaf(u, bl[q], a[q])));
+            const float lh = fmaf(u, el[q], c[q]);
+            r.a[q] = fmaf(u, plh[q], fmaf(u, bl[q], a[q]));
             r.b[q] = fmaf(u, pe[q], b[q]);
-            r.c[q] = fmaf(u, el[q], c[q]);
-            pc[q] = c[q];
+            r.c[q] = lh;
+            plh[q] = lh;
             pe[q] = r.e[q];
-            pel[q] = el[q];
         }
     }
 };
@@ -815,7 +861,7 @@ struct FwdPipe<WV_CDF53_INT, MODE> {
     UpdateSep<int32_t> us;
     PredictCol<int32_t> pcol;
     UpdateCol<int32_t> ucol;
-    __device__ __forceinline__ void init() {
+    __device__ __forceinline__ void init(float = -0.f) {  // integer levels take no shift
         if constexpr (MODE == MODE_NONSEP) { pn.init(0.f); un.init(0.f); }
         if constexpr (MODE == MODE_SEP) { ps.init(0.f); us.init(0.f); }
         if constexpr (MODE == MODE_COLS) { pcol.init(0.f); ucol.init(0.f); }
@@ -844,8 +890,10 @@ struct FwdPipe {
     AdaptedPredict pa[kPairs];
     AdaptedUpdate ua[kPairs];
     ConvV<WV> cv;
+    float ll_add;  // added to the finished LL (the DC level shift at the last level, else -0)
     static_assert(MODE != MODE_CONV || ConvV<WV>::kLag == kPairs, "lag of the convolution");
-    __device__ __forceinline__ void init() {
+    __device__ __forceinline__ void init(float ll_add_ = -0.f) {
+        ll_add = ll_add_;
         if constexpr (MODE == MODE_CONV) cv.init();
         const float P[kQ] = {WV == WV_CDF97 ? k97Alpha : -0.5f, k97Gamma};
         const float U[kQ] = {WV == WV_CDF97 ? k97Beta : 0.25f, k97Delta};
@@ -882,11 +930,14 @@ struct FwdPipe {
                 constexpr float sHH = MODE == MODE_COLS ? k97High : k97High * k97High;
 #pragma unroll
                 for (int q = 0; q < kQ; ++q) {
-                    r.a[q] *= sLL;
+                    r.a[q] = fmaf(r.a[q], sLL, ll_add);
                     r.b[q] *= sHL;
                     r.c[q] *= sLH;
                     r.e[q] *= sHH;
                 }
+            } else {
+#pragma unroll
+                for (int q = 0; q < kQ; ++q) r.a[q] += ll_add;
             }
         }
     }

@@ -240,6 +240,8 @@ __global__ void __launch_bounds__(kThreads, persist_min_ctas<WV>())
     int m0 = 0;
     BandRows bands;
     Pipe pipe;
+    constexpr bool kShift = kShiftable<C, MODE>;
+    LevelShift sh{-0.f, -0.f};
     for (int g = 0;; ++g) {
         const int s = g % kS;
         bool ok = mbar_wait(&ring.full[s], (g / kS) & 1, ring.abort, p.status);
@@ -259,7 +261,12 @@ __global__ void __launch_bounds__(kThreads, persist_min_ctas<WV>())
             idle = wq + kHQ >= A.nec;
             if constexpr (kAdj) hw.init(m0, AxisLen{A.nec, A.ndc});
             bands.init<TB, TL>(A, tl.n0, m0, 0);
-            pipe.init();
+            if constexpr (kShift) {
+                sh.init(A.shift, 0);
+                pipe.init(sh.out_add);
+            } else {
+                pipe.init();
+            }
             i = 0;
         }
         if (!idle) {
@@ -271,6 +278,7 @@ __global__ void __launch_bounds__(kThreads, persist_min_ctas<WV>())
                                                          cols, row, ring.shift[s]);
             __syncwarp();
             if (lane == 0) mbar_arrive(&ring.empty[s]);
+            if constexpr (kShift) add_row_scalar(row, sh.in_add);
             if constexpr (kAdj)
                 pipe.push(row, tl.qfirst + i, hw, AxisLen{A.ner, A.ndr}, A.scale);
             else
@@ -353,6 +361,8 @@ __global__ void __launch_bounds__(kThreads, persist_min_ctas<WV>())
     int m0 = 0;
     char* out_p = nullptr;  // the lane's position in the output plane at the tile's next row
     Pipe pipe;
+    constexpr bool kShift = !ADJ && std::is_same<C, float>::value;
+    LevelShift sh{-0.f, -0.f};
     for (int g = 0;; ++g) {
         const int s = g % kS;
         bool ok = mbar_wait(&ring.full[s], (g / kS) & 1, ring.abort, p.status);
@@ -371,6 +381,7 @@ __global__ void __launch_bounds__(kThreads, persist_min_ctas<WV>())
             idle = wq + kHQ >= A.nec;
             if constexpr (ADJ) hw.init(m0, AxisLen{A.nec, A.ndc});
             out_p = reinterpret_cast<char*>(row_ptr<TO>(A.out, 2 * tl.n0, 0) + 2 * m0);
+            if constexpr (kShift) sh.init(A.shift, 0);
             pipe.init();
             i = 0;
         }
@@ -379,12 +390,14 @@ __global__ void __launch_bounds__(kThreads, persist_min_ctas<WV>())
             inv_lane_row<TL, TB, C>(ring.stage(s), cols, row);
             __syncwarp();
             if (lane == 0) mbar_arrive(&ring.empty[s]);
+            if constexpr (kShift) add_ll(row, sh.in_add);
             if constexpr (ADJ)
                 pipe.push(row, tl.qfirst + i, hw, AxisLen{A.ner, A.ndr}, A.scale);
             else
                 pipe.push(row);
             const int qo = tl.qfirst + i - Pipe::kLag;
             if (qo >= tl.n0 && qo < tl.n1) {
+                if constexpr (kShift) add_row(row, sh.out_add);
                 if (store_lane) inv_store_rows_at<TO>(A, row, qo, m0, out_p);
                 out_p += 2 * A.out.pitch;
             }

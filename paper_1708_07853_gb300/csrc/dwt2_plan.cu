@@ -234,6 +234,11 @@ int build_work(dwt2_plan* P, int rows, std::vector<FwdUnit>& fu, std::vector<Inv
                 if (P->direction == DWT2_DIR_INVERSE_ADJOINT) {
                     const Scale4 s = plan_level_scale(P->wavelet, hh, ww);
                     u.a.scale = Scale4{1.f / s.ll, 1.f / s.hl, 1.f / s.lh, 1.f / s.hh};
+                } else if (P->wavelet != WV_CDF53_INT) {
+                    // the DC level shift of the image, as the single-image forward takes it
+                    u.a.shift = ShiftSrc{d.img, d.img_pitch_bytes, 0, d.H, d.W, P->img_dtype,
+                                         (j == 1 ? kShiftIn : 0) | (j == J ? kShiftOut : 0)};
+                    if (!u.a.shift.mode) u.a.shift.ptr = nullptr;
                 }
                 u.a.rpc = rpc;
                 u.item_begin = begin;
@@ -266,8 +271,15 @@ int build_work(dwt2_plan* P, int rows, std::vector<FwdUnit>& fu, std::vector<Inv
                 int rc = plan_prepare_inv_unit(&u, bp, pp, hh, ww, ll_dt, P->band_dtype, out, opitch,
                                                out_dt, status);
                 if (rc) return rc;
-                if (P->direction == DWT2_DIR_FORWARD_ADJOINT)
+                if (P->direction == DWT2_DIR_FORWARD_ADJOINT) {
                     u.a.scale = plan_level_scale(P->wavelet, hh, ww);
+                } else if (P->wavelet != WV_CDF53_INT) {
+                    // the DC level shift of LL_J, as the single-image inverse takes it
+                    u.a.shift = ShiftSrc{cb + bands[0].offset_bytes, bands[0].pitch_bytes, 0,
+                                         bands[0].h, bands[0].w, DT_F32,
+                                         (j == J ? kShiftIn : 0) | (j == 1 ? kShiftOut : 0)};
+                    if (!u.a.shift.mode) u.a.shift.ptr = nullptr;
+                }
                 u.a.rpc = rpc;
                 u.item_begin = begin;
                 u.n_items = n_items;

@@ -14,7 +14,6 @@
 // contents of the previous call; calls whose execution overlaps on the GPU (different streams,
 // or different host threads) race on it and must be ordered by the caller.
 #include <cstdio>
-#include <mutex>
 
 #include "../../include/dwt2.h"
 #include "dwt2_internal.h"
@@ -28,8 +27,6 @@ void set_last_error(const char* msg);
 namespace {
 
 constexpr size_t kStaticScratchBytes = size_t(24) << 20;  // DWT2_STATIC_SCRATCH_BYTES
-constexpr size_t kStatusHeaderBytes = 256;                // cleared by every call
-constexpr int kMaxDevices = 64;
 
 static_assert(kStaticScratchBytes == DWT2_STATIC_SCRATCH_BYTES, "header and library disagree");
 
@@ -37,33 +34,19 @@ static_assert(kStaticScratchBytes == DWT2_STATIC_SCRATCH_BYTES, "header and libr
 // the device address comes from cudaGetSymbolAddress below.
 static __device__ __align__(256) unsigned char g_scratch[kStaticScratchBytes];
 
-std::mutex g_mu;
-void* g_addr[kMaxDevices] = {};
-
-// Device address of g_scratch on the current device, looked up once per device.
+// Device address of g_scratch in the current device's current context.  Looked up on every call
+// (a host-side lookup): a cached address would go stale after cudaDeviceReset, or belong to
+// another context when the caller switches contexts, and the kernels would then write through
+// it.  The first lookup in a context loads the library's device code there.
 int scratch_address(void** out) {
-    int dev = -1;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) {
-        dwt2::set_last_error(cudaGetErrorString(e));
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
+    if (e != cudaSuccess || !p) {
+        dwt2::set_last_error(e != cudaSuccess ? cudaGetErrorString(e)
+                                              : "cudaGetSymbolAddress returned null");
         return DWT2_ECUDA;
     }
-    if (dev < 0 || dev >= kMaxDevices) {
-        dwt2::set_last_error("dwt2_forward_static: device index out of range");
-        return DWT2_EUNSUPPORTED;
-    }
-    std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_addr[dev]) {
-        void* p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_scratch);
-        if (e != cudaSuccess || !p) {
-            dwt2::set_last_error(e != cudaSuccess ? cudaGetErrorString(e)
-                                                  : "cudaGetSymbolAddress returned null");
-            return DWT2_ECUDA;
-        }
-        g_addr[dev] = p;
-    }
-    *out = g_addr[dev];
+    *out = p;
     return DWT2_OK;
 }
 
@@ -84,15 +67,11 @@ DWT2_EXPORT int dwt2_forward_static(const void* img, int64_t img_pitch_bytes, in
         return DWT2_ENOMEM;
     }
     void* ws = nullptr;
-    int rc = scratch_address(&ws);
+    const int rc = scratch_address(&ws);
     if (rc) return rc;
-    // The status word must start at zero; the LL planes are fully written before they are read.
-    cudaError_t e =
-        cudaMemsetAsync(ws, 0, kStatusHeaderBytes, static_cast<cudaStream_t>(stream));
-    if (e != cudaSuccess) {
-        dwt2::set_last_error(cudaGetErrorString(e));
-        return DWT2_ECUDA;
-    }
-    return dwt2_forward(img, img_pitch_bytes, H, W, img_dtype, coeffs, ws, kStaticScratchBytes,
-                        wavelet, levels, band_dtype, stream);
+    // Every argument is checked before anything is queued on the stream; then the status word is
+    // cleared (the LL planes are fully written before they are read).
+    return dwt2::forward_into_scratch(img, img_pitch_bytes, H, W, img_dtype, coeffs, ws,
+                                      kStaticScratchBytes, wavelet, levels, band_dtype,
+                                      static_cast<cudaStream_t>(stream));
 }

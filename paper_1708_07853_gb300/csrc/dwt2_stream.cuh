@@ -89,6 +89,28 @@ struct PlaneOut {
     int64_t bstride;
 };
 
+// DC level shift of the float transforms.  The lifting intermediates of CDF 9/7 reach several
+// times the signal level (the first predict leaves d = (1 + 2 alpha) x ~ -2.2 x on smooth
+// content, its 2-D HH term (1 + 2 alpha)^2 x ~ 4.7 x), and fp32 rounds them at that magnitude.
+// A transform of x - c with c added back to LL_J computes the same coefficients in exact
+// arithmetic (LL has DC gain 1, the high-pass bands vanish on a constant), but its intermediates
+// scale with |x - c|: on [0, 255] content about three times smaller errors.  c is one number per
+// image, sampled from the data so that every tile, launch shape and entry point (single image,
+// uniform batch, plan) uses the same value: the median of a 3 x 3 grid of samples of the source
+// plane (the image for the forward, LL_J for the inverse; non-finite samples count as 0), rounded
+// to an integer.  The median of 9 ignores up to 4 outlying samples.
+enum ShiftType { SHIFT_F32 = 1, SHIFT_BF16 = 2, SHIFT_F16 = 3 };  // the C ABI's dtype codes
+struct ShiftSrc {
+    const void* ptr;  // plane the shift is sampled from; nullptr: no shift
+    int64_t pitch;    // bytes
+    int64_t bstride;  // bytes between the images of a batch
+    int h, w;
+    int dt;           // ShiftType
+    int mode;         // bit 0: subtract c from the level's input; bit 1: add c to its output
+};
+constexpr int kShiftIn = 1;
+constexpr int kShiftOut = 2;
+
 struct FwdArgs {
     const void* in;     // input plane (used by the plain-load path)
     int64_t in_pitch;   // bytes
@@ -101,6 +123,7 @@ struct FwdArgs {
     Scale4 scale;       // MODE_ADJ_INV: the reciprocal band scales applied last
     int tma;            // 1: load the input plane with TMA (16-byte aligned base and pitch)
     int nbatch;         // images in the batch (grid z)
+    ShiftSrc shift;     // DC level shift: kShiftIn at level 1, kShiftOut (onto LL) at level J
 };
 
 struct InvArgs {
@@ -116,6 +139,50 @@ struct InvArgs {
     Scale4 scale;         // adjoint: the band scales applied first
     int tma;              // 1: load the band planes with TMA
     int nbatch;           // images in the batch (grid z)
+    ShiftSrc shift;       // DC level shift: kShiftIn (from LL) at level J, kShiftOut at level 1
+};
+
+// The level shift c of image z (0 when none): see ShiftSrc.
+__device__ __forceinline__ float shift_sample(const char* row, int c, int dt) {
+    float v;
+    if (dt == SHIFT_BF16) v = __bfloat162float(reinterpret_cast<const __nv_bfloat16*>(row)[c]);
+    else if (dt == SHIFT_F16) v = __half2float(reinterpret_cast<const __half*>(row)[c]);
+    else v = reinterpret_cast<const float*>(row)[c];
+    return isfinite(v) ? v : 0.f;
+}
+__device__ __forceinline__ float level_shift(const ShiftSrc& s, int z) {
+    if (s.ptr == nullptr || s.mode == 0 || s.h < 1 || s.w < 1) return 0.f;
+    const char* base = static_cast<const char*>(s.ptr) + int64_t(z) * s.bstride;
+    float v[9];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        const char* row = base + (int64_t(2 * i + 1) * s.h / 6) * s.pitch;
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+            v[3 * i + j] = shift_sample(row, int(int64_t(2 * j + 1) * s.w / 6), s.dt);
+    }
+    // the 5th smallest: a partial selection sort
+#pragma unroll
+    for (int i = 0; i < 5; ++i)
+#pragma unroll
+        for (int j = i + 1; j < 9; ++j) {
+            const float lo = fminf(v[i], v[j]), hi = fmaxf(v[i], v[j]);
+            v[i] = lo;
+            v[j] = hi;
+        }
+    return rintf(v[4]);
+}
+
+// The values a level adds to its input (-c at the first level, else +0) and to its output
+// (+c at the last level, else -0).  x + 0 with the sign that leaves every x unchanged, -0
+// included, so an unshifted level computes exactly what it would without the shift.
+struct LevelShift {
+    float in_add, out_add;
+    __device__ __forceinline__ void init(const ShiftSrc& s, int z) {
+        const float c = level_shift(s, z);
+        in_add = (s.mode & kShiftIn) && c != 0.f ? -c : -0.f;
+        out_add = (s.mode & kShiftOut) && c != 0.f ? c : -0.f;
+    }
 };
 
 template <typename T>
@@ -678,13 +745,20 @@ __device__ __forceinline__ void drain_ring(const Ring<NS>& r, int issued, int* s
         if (!mbar_wait(&r.full[i % NS], (i / NS) & 1, &no_abort, status)) break;
 }
 
+// Forward levels that take the DC level shift: float lifting (every scheme but the convolution,
+// whose only intermediates are the filter outputs) and not the adjoint (a linear map of
+// gradients, with no DC to remove).
+template <typename C, int MODE>
+constexpr bool kShiftable =
+    std::is_same<C, float>::value && MODE != MODE_CONV && MODE != MODE_ADJ_INV;
+
 // =============================================================================================
 // Single-image kernels: one CTA = one tile (kCtaQ quad columns x rpc quad rows + halo) of one
 // level.  MODE_ROWS writes the interleaved plane (the row pass of the two-pass separable
 // comparator); MODE_ADJ_INV is the transpose of the inverse level; every other mode is the
 // forward level.
 // =============================================================================================
-template <int WV, int MODE, typename TI, typename TB, typename TL, bool kPlain>
+template <int WV, int MODE, typename TI, typename TB, typename TL, bool kPlain, bool kShift>
 __global__ void __launch_bounds__(kThreads, min_ctas<WV>())
     k_forward(const __grid_constant__ CUtensorMap tmap, const FwdArgs args) {
     constexpr bool kAdj = MODE == MODE_ADJ_INV;
@@ -750,8 +824,12 @@ __global__ void __launch_bounds__(kThreads, min_ctas<WV>())
 
     BandRows bands;
     if constexpr (MODE != MODE_ROWS) bands.init<TB, TL>(args, n0, m0, z);
+    static_assert(!kShift || kShiftable<C, MODE>, "a level shift on a level that takes none");
+    LevelShift sh{-0.f, -0.f};
+    if constexpr (kShift) sh.init(args.shift, z);
     Pipe pipe;
-    pipe.init();
+    if constexpr (kShift) pipe.init(sh.out_add);
+    else pipe.init();
     RingPos<kS> rp;
 #pragma unroll row_unroll<WV>()
     for (int i = 0; i < nrows; ++i) {
@@ -775,6 +853,7 @@ __global__ void __launch_bounds__(kThreads, min_ctas<WV>())
             fwd_lane_row<TI, C>(reinterpret_cast<const TI*>(ring.stage(s)), cols, row);
         __syncwarp();
         if (lane == 0) mbar_arrive(&ring.empty[s]);
+        if constexpr (kShift) add_row_scalar(row, sh.in_add);
         if constexpr (kAdj)
             pipe.push(row, qfirst + i, hw, rows, args.scale);
         else
@@ -791,7 +870,7 @@ __global__ void __launch_bounds__(kThreads, min_ctas<WV>())
 
 // Inverse level (ADJ = false) or the transpose of the forward level (ADJ = true): four band
 // planes in, the interleaved plane out.
-template <int WV, typename TB, typename TL, typename TO, bool ADJ>
+template <int WV, typename TB, typename TL, typename TO, bool ADJ, bool kShift>
 __global__ void __launch_bounds__(kThreads, min_ctas<WV>())
     k_inverse(const __grid_constant__ CUtensorMap tm_ll, const __grid_constant__ CUtensorMap tm_hl,
               const __grid_constant__ CUtensorMap tm_lh, const __grid_constant__ CUtensorMap tm_hh,
@@ -858,6 +937,9 @@ __global__ void __launch_bounds__(kThreads, min_ctas<WV>())
     const AxisLen rows{args.ner, args.ndr};
 
     char* out_p = reinterpret_cast<char*>(row_ptr<TO>(args.out, 2 * n0, z) + 2 * m0);
+    static_assert(!kShift || (!ADJ && std::is_same<C, float>::value), "no shift on this level");
+    LevelShift sh{-0.f, -0.f};
+    if constexpr (kShift) sh.init(args.shift, z);
     Pipe pipe;
     pipe.init();
     RingPos<kS> rp;
@@ -876,12 +958,14 @@ __global__ void __launch_bounds__(kThreads, min_ctas<WV>())
         inv_lane_row<TL, TB, C>(ring.stage(s), cols, row);
         __syncwarp();
         if (lane == 0) mbar_arrive(&ring.empty[s]);
+        if constexpr (kShift) add_ll(row, sh.in_add);
         if constexpr (ADJ)
             pipe.push(row, qfirst + i, hw, rows, args.scale);
         else
             pipe.push(row);
         const int qo = qfirst + i - Pipe::kLag;
         if (qo >= n0 && qo < n1) {
+            if constexpr (kShift) add_row(row, sh.out_add);
             if (store_lane) inv_store_rows_at<TO>(args, row, qo, m0, out_p);
             out_p += 2 * args.out.pitch;
         }
@@ -965,9 +1049,9 @@ int configure(K kernel, size_t smem) {
     return n;
 }
 
-template <int WV, int MODE, typename TI, typename TB, typename TL, bool kPlain>
+template <int WV, int MODE, typename TI, typename TB, typename TL, bool kPlain, bool kShift>
 cudaError_t launch_forward_k(const CUtensorMap& tm, FwdArgs a, cudaStream_t st) {
-    auto k = k_forward<WV, MODE, TI, TB, TL, kPlain>;
+    auto k = k_forward<WV, MODE, TI, TB, TL, kPlain, kShift>;
     constexpr size_t smem = fwd_smem_bytes<TI, fwd_stages<WV>()>();
     static const int occ = configure(k, smem);
     const LaunchGeom g = pick_geometry(a.ner, a.nec, int64_t(a.H) * a.W * int64_t(sizeof(TI)),
@@ -976,22 +1060,40 @@ cudaError_t launch_forward_k(const CUtensorMap& tm, FwdArgs a, cudaStream_t st) 
     return launch_pdl(k, g.grid, smem, st, tm, a);
 }
 
-// TMA-loading or plain-loading instantiation, by whether the input plane has a tensor map.
+// TMA-loading or plain-loading instantiation, by whether the input plane has a tensor map,
+// and the instantiation with the DC level shift only for the levels that take it (the first and
+// the last), so the others run exactly the code they would without it.
 template <int WV, int MODE, typename TI, typename TB, typename TL>
 cudaError_t launch_forward_t(const CUtensorMap& tm, FwdArgs a, cudaStream_t st) {
-    return a.tma ? launch_forward_k<WV, MODE, TI, TB, TL, false>(tm, a, st)
-                 : launch_forward_k<WV, MODE, TI, TB, TL, true>(tm, a, st);
+    using C = std::conditional_t<WV == WV_CDF53_INT, int32_t, float>;
+    if constexpr (kShiftable<C, MODE>) {
+        if (a.shift.mode != 0)
+            return a.tma ? launch_forward_k<WV, MODE, TI, TB, TL, false, true>(tm, a, st)
+                         : launch_forward_k<WV, MODE, TI, TB, TL, true, true>(tm, a, st);
+    }
+    return a.tma ? launch_forward_k<WV, MODE, TI, TB, TL, false, false>(tm, a, st)
+                 : launch_forward_k<WV, MODE, TI, TB, TL, true, false>(tm, a, st);
 }
 
-template <int WV, typename TB, typename TL, typename TO, bool ADJ = false>
-cudaError_t launch_inverse_t(const CUtensorMap* tm, InvArgs a, cudaStream_t st) {
-    auto k = k_inverse<WV, TB, TL, TO, ADJ>;
+template <int WV, typename TB, typename TL, typename TO, bool ADJ, bool kShift>
+cudaError_t launch_inverse_k(const CUtensorMap* tm, InvArgs a, cudaStream_t st) {
+    auto k = k_inverse<WV, TB, TL, TO, ADJ, kShift>;
     constexpr size_t smem = inv_smem_bytes<TL, TB, inv_stages<WV>()>();
     static const int occ = configure(k, smem);
     const LaunchGeom g = pick_geometry(a.ner, a.nec, int64_t(a.H) * a.W * int64_t(sizeof(TL)),
                                        device_sm_count(), occ, a.nbatch);
     a.rpc = g.rpc;
     return launch_pdl(k, g.grid, smem, st, tm[0], tm[1], tm[2], tm[3], a);
+}
+
+// The inverse level with the DC level shift for the levels that take it (the last inverse level,
+// which takes the shift off LL_J, and the first, which puts it back).
+template <int WV, typename TB, typename TL, typename TO, bool ADJ = false>
+cudaError_t launch_inverse_t(const CUtensorMap* tm, InvArgs a, cudaStream_t st) {
+    if constexpr (!ADJ && WV != WV_CDF53_INT) {
+        if (a.shift.mode != 0) return launch_inverse_k<WV, TB, TL, TO, false, true>(tm, a, st);
+    }
+    return launch_inverse_k<WV, TB, TL, TO, ADJ, false>(tm, a, st);
 }
 
 }  // namespace dwt2

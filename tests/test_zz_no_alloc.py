@@ -19,7 +19,7 @@ from paper_1708_07853_gb300 import inputs as I
 
 pytestmark = pytest.mark.gpu
 
-FLOAT_TOL = 1e-3  # the float bound the other GPU tests use
+DWT2_STATIC_SCRATCH_BYTES = 24 << 20  # include/dwt2.h
 
 
 @pytest.fixture(scope="module")
@@ -39,21 +39,23 @@ def _static_forward(lib, x: torch.Tensor, wavelet: int, levels: int, bdt: int) -
     return c
 
 
-@pytest.mark.parametrize("wavelet,dtype", [(0, torch.int32), (2, torch.float32)])
-def test_static_matches_workspace_entry_point_two_calls(lib, wavelet, dtype):
+@pytest.mark.parametrize("wavelet,dtype,band", [(0, torch.int32, torch.int32),
+                                                 (2, torch.float32, torch.float32),
+                                                 (2, torch.float32, torch.bfloat16)])
+def test_static_matches_workspace_entry_point_two_calls(lib, wavelet, dtype, band):
+    """Both entry points run the same kernels on the same input, so the coefficients must be the
+    same bits; any difference would come from the scratch (an aliased or stale LL plane).  The
+    bf16 case keeps its intermediate LL planes in fp32 in the scratch."""
     # two different images, so the second call cannot pass on the first call's leftovers
     for k, (H, W, lv) in enumerate([(1000, 777, 4), (1537, 2049, 5)]):
         x = I.field(H, W, I.seed_for(9, k))
         t = torch.from_numpy(x.astype(np.int32) if dtype == torch.int32 else x).cuda()
-        bdt = D.TORCH_DT[dtype]
+        bdt = D.TORCH_DT[band]
         got = _static_forward(lib, t, wavelet, lv, bdt)
-        want = D.forward(t, wavelet, lv)
+        want = D.forward(t, wavelet, lv, band_dtype=band)
         torch.cuda.synchronize()
         for g, w in zip(got.band_views(), want.band_views()):
-            if dtype == torch.int32:
-                assert torch.equal(g, w)
-            elif w.numel():
-                assert (g - w).abs().max().item() <= FLOAT_TOL
+            assert torch.equal(g, w)
 
 
 def test_static_rejects_sizes_beyond_its_scratch(lib):
@@ -69,5 +71,31 @@ def test_static_rejects_sizes_beyond_its_scratch(lib):
                                  c5.buffer.data_ptr(), 2, 5, D.DT_F32,
                                  torch.cuda.current_stream().cuda_stream)
     assert rc == 3  # DWT2_ENOMEM
+    assert b"scratch" in lib.dwt2_last_error()
+    torch.cuda.synchronize()
+
+
+def test_static_scratch_limit(lib):
+    """4096 x 4096 int32 fits the built-in scratch at the maximum level count; the first square
+    size whose workspace exceeds the scratch is rejected with DWT2_ENOMEM before any launch."""
+    st = torch.cuda.current_stream().cuda_stream
+    n = 4096
+    x = torch.from_numpy(I.field(n, n, I.seed_for(9, 5)).astype(np.int32)).cuda()
+    lv = D.max_levels(n, n)
+    assert lib.dwt2_workspace_bytes(n, n, lv, 0, D.DT_I32) <= DWT2_STATIC_SCRATCH_BYTES
+    got = _static_forward(lib, x, 0, lv, D.DT_I32)
+    want = D.forward(x, 0, lv)
+    torch.cuda.synchronize()
+    for g, w in zip(got.band_views(), want.band_views()):
+        assert torch.equal(g, w)
+    # the first size above the limit (the workspace grows with the size)
+    m = n
+    while lib.dwt2_workspace_bytes(m, m, 2, 0, D.DT_I32) <= DWT2_STATIC_SCRATCH_BYTES:
+        m += 1
+    y = torch.zeros((m, m), dtype=torch.int32, device="cuda")
+    c = D.alloc_coeffs(m, m, 2, 0, D.DT_I32, "cuda")
+    rc = lib.dwt2_forward_static(y.data_ptr(), m * 4, m, m, D.DT_I32, c.buffer.data_ptr(), 0, 2,
+                                 D.DT_I32, st)
+    assert rc == 3, rc  # DWT2_ENOMEM
     assert b"scratch" in lib.dwt2_last_error()
     torch.cuda.synchronize()
