@@ -12,8 +12,8 @@ launches on.  Clocks and throttle reasons are sampled with nvidia-smi during the
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
---impl reference times the CPU oracle (fp64, one host thread) on a bounded crop of the same
-workload and prints the same JSON line with "impl": "reference".
+--impl reference times the CPU oracle (fp64, all host cores) on the same workload and prints the
+same JSON line with "impl": "reference".
 """
 from __future__ import annotations
 
@@ -195,32 +195,81 @@ def job_rate(units_per_rank: int, world: int, ms: float) -> float:
     return world * units_per_rank / (ms * 1e-3) / 1e9
 
 
+def host_cpu():
+    """(usable host cores, CPU model from lscpu)."""
+    try:
+        cores = len(os.sched_getaffinity(0))
+    except AttributeError:  # pragma: no cover - Linux has it
+        cores = os.cpu_count() or 1
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return cores, model
+
+
+def oracle_forward_seconds(O, img: np.ndarray, threads: int, reps: int):
+    """Median wall time of `reps` oracle forwards (CDF 9/7 fp64, LEVELS levels) of img."""
+    O.set_threads(threads)
+    try:
+        ts = []
+        for _ in range(reps):
+            t = time.perf_counter()
+            O.forward(img, "cdf97", LEVELS)
+            ts.append(time.perf_counter() - t)
+    finally:
+        O.set_threads(1)
+    return float(np.median(ts))
+
+
+# Longest the reference arm may take (warm-up + timed steps) before it times a crop instead.
+REFERENCE_BUDGET_S = 180.0
+
+
 def run_reference(args, rank: int, world: int):
+    """The oracle over all host cores on the workload image, one full forward per step."""
     if rank != 0:
         return
     from oracle import oracle as O
     from paper_1708_07853_gb300 import inputs as I
 
     O.build()
-    side = 1024 if args.steps + args.warmup <= 300 else 512
-    full = I.field(H, W, I.seed_for(1))
-    crop = full[:side, :side].astype(np.float64)
+    cores, model = host_cpu()
+    img = I.field(H, W, I.seed_for(1)).astype(np.float64)
+    est = oracle_forward_seconds(O, img, cores, 1)  # one probe run, untimed
+    side = H
+    if est * (args.steps + args.warmup) > REFERENCE_BUDGET_S:  # too many steps: a crop
+        side = int(H * np.sqrt(REFERENCE_BUDGET_S / (est * (args.steps + args.warmup))))
+        side = max(256, side // 256 * 256)
+        img = np.ascontiguousarray(img[:side, :side])
+    O.set_threads(cores)
     times = []
-    for i in range(args.warmup + args.steps):
-        t = time.perf_counter()
-        O.forward(crop, "cdf97", LEVELS)
-        if i >= args.warmup:
-            times.append(time.perf_counter() - t)
-    ms = 1e3 * float(np.mean(times))
+    try:
+        for i in range(args.warmup + args.steps):
+            t = time.perf_counter()
+            O.forward(img, "cdf97", LEVELS)
+            if i >= args.warmup:
+                times.append(time.perf_counter() - t)
+    finally:
+        O.set_threads(1)
+    ms = 1e3 * float(np.median(times))
     gpix = side * side / (ms * 1e-3) / 1e9
-    line = {"impl": "reference", "metric": METRIC, "value": gpix, "unit": "Gpixel/s",
-            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": CONFIG,
-            "cpu_baseline": {"kind": "oracle", "value": gpix, "unit": "Gpixel/s", "cores": 1,
-                             "sample": f"{side}x{side} top-left crop of the workload image, "
-                                       f"CDF 9/7 fp64, {LEVELS} levels, one host thread"},
-            "e2e": {"value": gpix, "unit": "Gpixel/s", "h2d_bytes_per_step": 0,
+    sample = (f"{'the full' if side == H else f'a {side}x{side} top-left crop of the'} "
+              f"{H}x{W} workload image per step, CDF 9/7 fp64, {LEVELS} levels, "
+              f"{cores} host threads (median of {args.steps})")
+    line = {"impl": "reference", "metric": METRIC, "value": round(gpix, 5), "unit": "Gpixel/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(ms, 3), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": dict(CONFIG, parallelism="host cores"),
+            "cpu_baseline": {"kind": "oracle", "value": round(gpix, 5), "unit": "Gpixel/s",
+                             "cores": cores, "cpu_model": model, "sample": sample},
+            "e2e": {"value": round(gpix, 5), "unit": "Gpixel/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -543,6 +592,7 @@ def main():
         return run_only(args, D, dev, x_f32, x_i32, flush, stream)
 
     def run_case(fn, steps, warmup):
+        """Median CUDA-event time (ms) of `steps` calls, L2 flushed before each."""
         for _ in range(warmup):
             fn()
         evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
@@ -553,7 +603,7 @@ def main():
             fn()
             e.record(stream)
         torch.cuda.synchronize()
-        return float(np.mean([s.elapsed_time(e) for s, e in evs]))  # ms
+        return float(np.median([s.elapsed_time(e) for s, e in evs]))  # ms
 
     cases = {}
 
@@ -572,6 +622,13 @@ def main():
     sampler = ClockSampler(dev.index if dev.index is not None else 0)
     sampler.start()
     time.sleep(0.3)  # let the sampler start delivering
+    # about a second of back-to-back transforms first, so that the timed steps do not start on
+    # clocks still ramping up from idle
+    t_warm = time.time()
+    while time.time() - t_warm < 1.0:
+        for _ in range(50):
+            fwd97()
+        torch.cuda.synchronize()
     for _ in range(args.warmup):
         fwd97()
     barrier()
@@ -622,6 +679,12 @@ def main():
     cases["fwd_cdf97_conv"] = summarise(run_case(
         lambda: D.forward(x_f32, "cdf97", LEVELS, scheme="conv", out=cc, workspace=wsc),
         args.steps, args.warmup))
+    # the non-separable kernel against both separable comparators (time ratios, > 1: faster)
+    comparison = {
+        f"{wv}_nonsep_speedup_vs_{sc}": round(
+            cases[f"fwd_{wv}_{sc}"]["ms"] / cases[f"fwd_{wv}_{ref}"]["ms"], 3)
+        for wv, ref in (("cdf97", "f32_nonsep"), ("cdf53_int", "nonsep"))
+        for sc in ("sep_fused", "sep_twopass")}
     correct_inv = bool(torch.equal(D.inverse(ci, out=out_i, workspace=wsi), x_i32))
     clocks = sampler.summary(t0, t1)  # the headline window (extended into these cases if short)
     sampler.stop()
@@ -703,12 +766,17 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         from oracle import oracle as O
         O.build()
-        t = time.perf_counter()
-        O.forward(field.astype(np.float64), "cdf97", LEVELS)
-        dt = time.perf_counter() - t
-        cpu = {"value": round(npix / dt / 1e9, 5), "unit": "Gpixel/s", "cores": 1,
-               "kind": "oracle", "sample": "one full 8192x8192 forward, CDF 9/7 fp64, 5 levels, "
-                                           "one host thread", "seconds": round(dt, 2)}
+        cores, model = host_cpu()
+        img = field.astype(np.float64)
+        t_all = oracle_forward_seconds(O, img, cores, 3)
+        t_one = oracle_forward_seconds(O, img, 1, 3)
+        cpu = {"value": round(npix / t_all / 1e9, 5), "unit": "Gpixel/s", "cores": cores,
+               "cpu_model": model, "kind": "oracle",
+               "sample": f"full 8192x8192 forward, CDF 9/7 fp64, 5 levels, {cores} host "
+                         f"threads, median of 3", "seconds": round(t_all, 3),
+               "single_thread": {"value": round(npix / t_one / 1e9, 5), "unit": "Gpixel/s",
+                                 "seconds": round(t_one, 3), "sample": "the same, one thread, "
+                                                                       "median of 3"}}
 
     line = {"metric": METRIC, "value": round(gpix_main, 2), "unit": "Gpixel/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -719,6 +787,7 @@ def main():
             "hbm_gb_s": cases["fwd_cdf97_f32_nonsep"]["gb_s"],
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": args.steps * LEVELS, "clocks": clocks, "cases": cases,
+            "comparison": comparison,
             "workloads": workloads,
             "device_status": status, "int53_roundtrip_exact": correct_inv}
     if rank == 0:
