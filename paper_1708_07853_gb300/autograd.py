@@ -8,11 +8,15 @@ kernels, from the coarsest level down (W^T) or from the finest up (W^-T).
 Coefficients travel as one flat float32 tensor per image, laid out exactly as dwt2_layout
 describes (fp32 storage makes every band, and the padding between rows and bands, a whole
 number of floats).  `band_views` gives the LL / HL / LH / HH planes as views into it; the
-padding entries are zero in forward outputs and in gradients.  All images of a call go through
-the uniform-batch entry points: one launch per level covers every image.
+padding entries are zero in forward outputs and in gradients.  The kernels write the bands
+only, so outputs are allocated uninitialised and just their padding entries are zeroed, from an
+index cached per layout (empty when the widths are multiples of 4 and the band sizes multiples of
+256 bytes, as for 1024 x 1024 images).  All images of a call go through the uniform-batch entry
+points: one launch per level covers every image.
 """
 from __future__ import annotations
 
+import numpy as np
 import torch
 
 from . import dwt2 as D
@@ -21,6 +25,34 @@ from . import dwt2 as D
 def coeff_floats(H: int, W: int, levels: int) -> int:
     _, nbytes = D.layout(H, W, levels, D.DT_F32)
     return nbytes // 4
+
+
+_PAD = {}
+
+
+def padding_index(H: int, W: int, levels: int, device) -> torch.Tensor:
+    """Positions of the flat coefficient layout that belong to no band (row padding and the gaps
+    that align each band to 256 bytes), as a cached int64 tensor on device."""
+    key = (H, W, levels, str(device))
+    if key not in _PAD:
+        lay, nbytes = D.layout(H, W, levels, D.DT_F32)
+        pad = np.ones(nbytes // 4, dtype=bool)
+        for b in lay:
+            if b.h and b.w:
+                o, p = b.offset_bytes // 4, b.pitch_bytes // 4
+                pad[(o + np.arange(b.h)[:, None] * p + np.arange(b.w)[None, :]).ravel()] = False
+        _PAD[key] = torch.from_numpy(np.nonzero(pad)[0]).to(device)
+    return _PAD[key]
+
+
+def _new_coeffs(n_img: int, H: int, W: int, levels: int, device) -> torch.Tensor:
+    """Uninitialised flat coefficients whose padding entries are zero (the kernels then write
+    every band entry)."""
+    out = torch.empty((n_img, coeff_floats(H, W, levels)), dtype=torch.float32, device=device)
+    pad = padding_index(H, W, levels, device)
+    if pad.numel():
+        out[:, pad] = 0.0
+    return out
 
 
 def band_views(c: torch.Tensor, H: int, W: int, levels: int):
@@ -55,7 +87,7 @@ class DWT2Fn(torch.autograd.Function):
         H, W = x.shape[-2:]
         xs = _images(x.contiguous())
         n = coeff_floats(H, W, levels)
-        out = torch.zeros((xs.shape[0], n), dtype=torch.float32, device=x.device)
+        out = _new_coeffs(xs.shape[0], H, W, levels, x.device)
         D.forward_batch(xs, wavelet, levels, D.DT_F32, out=out)
         ctx.meta = (H, W, wavelet, levels, x.shape)
         return out.reshape(*x.shape[:-2], n)
@@ -83,7 +115,7 @@ class IDWT2Fn(torch.autograd.Function):
     def backward(ctx, gx: torch.Tensor):
         H, W, wavelet, levels, cshape = ctx.meta
         gxs = _images(gx.contiguous())
-        gc = torch.zeros((gxs.shape[0], cshape[-1]), dtype=torch.float32, device=gx.device)
+        gc = _new_coeffs(gxs.shape[0], H, W, levels, gx.device)
         D.inverse_adjoint_batch(gxs, wavelet, levels, out=gc)
         return gc.reshape(cshape), None, None, None, None
 

@@ -84,16 +84,27 @@ __device__ __forceinline__ void warp_done(int* counter, int lane) {
     if (lane == 0) atomicAdd(counter, 1);
 }
 
+// Consumer warps per CTA of the persistent kernels: the narrow CTA (180-quad tiles).  The plans'
+// uneven images leave many tiles partly filled, and with it the 512-image batch ran faster on
+// GB300: int 5/3 0.983 against 1.036 ms, 9/7 1.164 against 1.181 ms.  The inverse data flow
+// with 16-bit bands keeps the wide CTA, whose band loads stay 16-byte aligned (see
+// inv_tma_x_aligned).
+constexpr int kPersistFwdNW = 3;
+template <typename TB, typename TL>
+constexpr int persist_inv_nw() {
+    return inv_narrow_nw<TB, TL>();
+}
+
 // Geometry of one tile.
 struct Tile {
     int qx0, n0, n1, nrows, qfirst;
 };
 
-template <int kVH, typename Args>
+template <int kVH, int NW, typename Args>
 __device__ __forceinline__ Tile tile_of(const Args& a, int local, int strips) {
     Tile t;
     const int rb = local / strips, strip = local - rb * strips;
-    t.qx0 = strip * kCtaQ;
+    t.qx0 = strip * cta_q<NW>();
     t.n0 = rb * a.rpc;
     t.n1 = min(t.n0 + a.rpc, a.ner);
     t.nrows = t.n1 - t.n0 + 2 * kVH;
@@ -135,7 +146,7 @@ constexpr int kPersistStages = 8;
 
 // Producer side shared by both kernel shapes: claim the next ticket; returns -1 when the work is
 // exhausted.  Waits for the ticket's dependency.
-template <typename Unit>
+template <int NW, typename Unit>
 __device__ __forceinline__ int claim(const PersistArgs<Unit>& p, volatile int* abort_flag,
                                      int lane, bool& ok) {
     int t = 0;
@@ -148,7 +159,7 @@ __device__ __forceinline__ int claim(const PersistArgs<Unit>& p, volatile int* a
     const int dep = p.units[u].dep;
     if (dep >= 0) {
         int good = 1;
-        if (lane == 0) good = wait_count(&p.done[dep], kNW * p.units[dep].n_items, abort_flag, p.status);
+        if (lane == 0) good = wait_count(&p.done[dep], NW * p.units[dep].n_items, abort_flag, p.status);
         good = __shfl_sync(kFull, good, 0);
         if (!good) {
             ok = false;
@@ -174,8 +185,10 @@ __device__ __forceinline__ void post_sentinel(const Ring<NS>& ring, int g, int l
 }
 
 template <int WV, int MODE, typename TI, typename TB, typename TL>
-__global__ void __launch_bounds__(kThreads, persist_min_ctas<WV>())
+__global__ void __launch_bounds__(cta_threads<kPersistFwdNW>(), persist_min_ctas<WV>())
     k_forward_persistent(const PersistArgs<FwdUnit> p) {
+    constexpr int kNW = kPersistFwdNW;
+    static_assert(fwd_tma_x_aligned<kNW, TI>(), "TMA x coordinates of this CTA width misaligned");
     constexpr bool kAdj = MODE == MODE_ADJ_INV;
     using Pipe = std::conditional_t<kAdj, AdjInvPipe<WV>, FwdPipe<WV, MODE_NONSEP>>;
     using C = typename Pipe::C;
@@ -184,7 +197,7 @@ __global__ void __launch_bounds__(kThreads, persist_min_ctas<WV>())
     extern __shared__ __align__(128) uint8_t smem_raw[];
     const Ring<kS> ring = make_ring<kS>(smem_raw, size_t(2) * kSRow * sizeof(TI));
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    init_ring(ring);
+    init_ring<kNW>(ring);
     __syncthreads();
 
     if (warp == kNW) {  // ------------------------------------------------------ producer
@@ -193,14 +206,14 @@ __global__ void __launch_bounds__(kThreads, persist_min_ctas<WV>())
         bool bulk_used = false;  // TMA or bulk copies (async, tracked by the stage barriers)
         for (;;) {
             bool ok;
-            const int t = claim(p, ring.abort, lane, ok);
+            const int t = claim<kNW>(p, ring.abort, lane, ok);
             if (t < 0) {
                 if (ok) post_sentinel(ring, g, lane, p.status);
                 break;
             }
             const FwdUnit& U = p.units[__ldg(&p.item_unit[t])];
             pargs = U.a;
-            const Tile tl = tile_of<kVH>(pargs, t - __ldg(&U.item_begin), __ldg(&U.strips));
+            const Tile tl = tile_of<kVH, kNW>(pargs, t - __ldg(&U.item_begin), __ldg(&U.strips));
             const int xs = 2 * tl.qx0 - kXL;
             bulk_used |= pargs.tma != 0 || (kPersistBulk && !kAdj);
             bool alive = true;
@@ -253,7 +266,7 @@ __global__ void __launch_bounds__(kThreads, persist_min_ctas<WV>())
             unit = __ldg(&p.item_unit[t]);
             const FwdUnit* U = &p.units[unit];
             A = U->a;
-            tl = tile_of<kVH>(A, t - __ldg(&U->item_begin), __ldg(&U->strips));
+            tl = tile_of<kVH, kNW>(A, t - __ldg(&U->item_begin), __ldg(&U->strips));
             const int wq = tl.qx0 - kHQ + warp * kWarpOut;
             m0 = wq + kQ * lane;
             const int xs = 2 * tl.qx0 - kXL;
@@ -278,7 +291,7 @@ __global__ void __launch_bounds__(kThreads, persist_min_ctas<WV>())
                                                          cols, row, ring.shift[s]);
             __syncwarp();
             if (lane == 0) mbar_arrive(&ring.empty[s]);
-            if constexpr (kShift) add_row_scalar(row, sh.in_add);
+            if constexpr (kShift) add_row(row, sh.in_add);
             if constexpr (kAdj)
                 pipe.push(row, tl.qfirst + i, hw, AxisLen{A.ner, A.ndr}, A.scale);
             else
@@ -296,8 +309,11 @@ __global__ void __launch_bounds__(kThreads, persist_min_ctas<WV>())
 }
 
 template <int WV, typename TB, typename TL, typename TO, bool ADJ>
-__global__ void __launch_bounds__(kThreads, persist_min_ctas<WV>())
+__global__ void __launch_bounds__(cta_threads<persist_inv_nw<TB, TL>()>(), persist_min_ctas<WV>())
     k_inverse_persistent(const PersistArgs<InvUnit> p) {
+    constexpr int kNW = persist_inv_nw<TB, TL>();
+    static_assert(inv_tma_x_aligned<kNW, TB>() && inv_tma_x_aligned<kNW, TL>(),
+                  "TMA x coordinates of this CTA width misaligned");
     using Pipe = std::conditional_t<ADJ, AdjFwdPipe<WV>, InvPipe<WV>>;
     using C = typename Pipe::C;
     constexpr int kVH = vhalo<Pipe, ADJ>();
@@ -306,7 +322,7 @@ __global__ void __launch_bounds__(kThreads, persist_min_ctas<WV>())
     extern __shared__ __align__(128) uint8_t smem_raw[];
     const Ring<kS> ring = make_ring<kS>(smem_raw, kStageBytes);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    init_ring(ring);
+    init_ring<kNW>(ring);
     __syncthreads();
 
     if (warp == kNW) {  // ------------------------------------------------------ producer
@@ -315,14 +331,14 @@ __global__ void __launch_bounds__(kThreads, persist_min_ctas<WV>())
         bool tma_used = false;
         for (;;) {
             bool ok;
-            const int t = claim(p, ring.abort, lane, ok);
+            const int t = claim<kNW>(p, ring.abort, lane, ok);
             if (t < 0) {
                 if (ok) post_sentinel(ring, g, lane, p.status);
                 break;
             }
             const InvUnit& U = p.units[__ldg(&p.item_unit[t])];
             pargs = U.a;
-            const Tile tl = tile_of<kVH>(pargs, t - __ldg(&U.item_begin), __ldg(&U.strips));
+            const Tile tl = tile_of<kVH, kNW>(pargs, t - __ldg(&U.item_begin), __ldg(&U.strips));
             const int xb = tl.qx0 - kXLB;
             const CUtensorMap* maps[4] = {&U.tm[0], &U.tm[1], &U.tm[2], &U.tm[3]};
             tma_used |= pargs.tma != 0;
@@ -374,7 +390,7 @@ __global__ void __launch_bounds__(kThreads, persist_min_ctas<WV>())
             unit = __ldg(&p.item_unit[t]);
             const InvUnit* U = &p.units[unit];
             A = U->a;
-            tl = tile_of<kVH>(A, t - __ldg(&U->item_begin), __ldg(&U->strips));
+            tl = tile_of<kVH, kNW>(A, t - __ldg(&U->item_begin), __ldg(&U->strips));
             const int wq = tl.qx0 - kHQ + warp * kWarpOut;
             m0 = wq + kQ * lane;
             cols.init(m0, tl.qx0 - kXLB, A.W, !ADJ, (2 * wq < 0) || (2 * wq + 2 * kWarpQ > A.W));

@@ -9,13 +9,13 @@ template <int WV, int MODE, typename TI, typename TB, typename TL>
 cudaError_t go(const PersistArgs<FwdUnit>& p, int ctas_per_sm, cudaStream_t st, int* occ_out) {
     auto k = k_forward_persistent<WV, MODE, TI, TB, TL>;
     constexpr size_t smem = fwd_smem_bytes<TI, kPersistStages>();
-    static const int occ = configure(k, smem);
+    static const int occ = configure(k, cta_threads<kPersistFwdNW>(), smem);
     if (occ_out) {
         *occ_out = occ;
         return cudaSuccess;
     }
     const int c = (ctas_per_sm > 0 && ctas_per_sm < occ) ? ctas_per_sm : occ;
-    k<<<device_sm_count() * c, kThreads, smem, st>>>(p);
+    k<<<device_sm_count() * c, cta_threads<kPersistFwdNW>(), smem, st>>>(p);
     return cudaGetLastError();
 }
 

@@ -9,13 +9,13 @@ template <int WV, typename TB, typename TL, typename TO, bool ADJ>
 cudaError_t go(const PersistArgs<InvUnit>& p, int ctas_per_sm, cudaStream_t st, int* occ_out) {
     auto k = k_inverse_persistent<WV, TB, TL, TO, ADJ>;
     constexpr size_t smem = inv_smem_bytes<TL, TB, kPersistStages>();
-    static const int occ = configure(k, smem);
+    static const int occ = configure(k, cta_threads<persist_inv_nw<TB, TL>()>(), smem);
     if (occ_out) {
         *occ_out = occ;
         return cudaSuccess;
     }
     const int c = (ctas_per_sm > 0 && ctas_per_sm < occ) ? ctas_per_sm : occ;
-    k<<<device_sm_count() * c, kThreads, smem, st>>>(p);
+    k<<<device_sm_count() * c, cta_threads<persist_inv_nw<TB, TL>()>(), smem, st>>>(p);
     return cudaGetLastError();
 }
 

@@ -1,6 +1,6 @@
 // dwt2_plan.cu -- batched plans: many images (any sizes), all levels, one persistent launch.
 //
-// dwt2_plan_create builds the work list (one unit per image and level; tiles of kCtaQ quad columns
+// dwt2_plan_create builds the work list (one unit per image and level; tiles of plan_cta_q quad columns
 // by a per-level number of quad rows), the TMA tensor maps and argument blocks of every unit in
 // plan-owned device memory, and captures [memset of the tile counters, persistent kernel] into a CUDA graph;
 // dwt2_plan_execute replays it.  rows_per_tile (and the CTAs per SM) come from an autotuner that
@@ -97,6 +97,15 @@ int check_plan_args(const dwt2_image_desc* imgs, int n, int wavelet, int J, int 
     return DWT2_OK;
 }
 
+// Quad columns of a tile: the strip of the persistent kernel the plan launches (its CTA width
+// depends on the data flow and, for the inverse flow, on the band type).
+int plan_cta_q(const dwt2_plan* P) {
+    if (P->fwd_flow) return cta_q<kPersistFwdNW>();
+    if (P->band_dtype == DT_BF16 || P->band_dtype == DT_F16)
+        return cta_q<persist_inv_nw<__nv_bfloat16, float>()>();
+    return cta_q<persist_inv_nw<float, float>()>();
+}
+
 // Upper bound on the quad rows per tile at level j, for `rows` at level 1: halved at every level
 // (a level has half the rows and half the strips of the one before), at least 4.
 int level_rows(int rows, int j) { return std::max(4, rows >> (j - 1)); }
@@ -120,13 +129,14 @@ std::vector<int> plan_level_rows(const dwt2_plan* P, int rows, int resident) {
         one_size = one_size && h[i] == h[0] && w[i] == w[0];
     }
     const int64_t slots = std::max(1, resident);
+    const int cq = plan_cta_q(P);
     auto tiles_of = [&](int r, int* longest) {
         int64_t tiles = 0;
         *longest = 1;
         for (int i = 0; i < P->n; ++i) {
             const int ner = (h[i] + 1) / 2, nec = (w[i] + 1) / 2;
             const int rpc = std::max(1, std::min(r, ner));
-            tiles += int64_t((nec + kCtaQ - 1) / kCtaQ) * ((ner + rpc - 1) / rpc);
+            tiles += int64_t((nec + cq - 1) / cq) * ((ner + rpc - 1) / rpc);
             *longest = std::max(*longest, rpc);
         }
         return tiles;
@@ -156,13 +166,13 @@ std::vector<int> plan_level_rows(const dwt2_plan* P, int rows, int resident) {
 
 // Default level-1 rows per tile: about four tiles per resident CTA over the whole batch, so that
 // the tail of the ticket queue is short, within [8, 256] quad rows.
-int default_rows(const dwt2_image_desc* imgs, int n, int J, int resident) {
+int default_rows(const dwt2_image_desc* imgs, int n, int J, int resident, int cq) {
     double quad_rows_x_strips = 0;
     for (int i = 0; i < n; ++i) {
         int h = imgs[i].H, w = imgs[i].W;
         for (int j = 0; j < J; ++j) {
             const int ner = (h + 1) / 2, nec = (w + 1) / 2;
-            quad_rows_x_strips += double(ner) * ((nec + kCtaQ - 1) / kCtaQ) * double(1 << j);
+            quad_rows_x_strips += double(ner) * ((nec + cq - 1) / cq) * double(1 << j);
             h = ner;
             w = nec;
         }
@@ -212,7 +222,7 @@ int build_work(dwt2_plan* P, int rows, std::vector<FwdUnit>& fu, std::vector<Inv
             const dwt2_band& bhh = bands[1 + 3 * (J - j) + 2];
             const int ner = (hh + 1) / 2, nec = (ww + 1) / 2;
             const int rpc = std::max(1, std::min(lrows[j], ner));
-            const int strips = (nec + kCtaQ - 1) / kCtaQ;
+            const int strips = (nec + plan_cta_q(P) - 1) / plan_cta_q(P);
             const int n_items = strips * ((ner + rpc - 1) / rpc);
             const int dep_level = P->fwd_flow ? j - 1 : j + 1;
             const int dep = (dep_level >= 1 && dep_level <= J) ? unit_of[size_t(i) * (J + 1) + dep_level]
@@ -389,7 +399,8 @@ std::string tune_key(const dwt2_plan* P) {
     std::string name(prop.name);
     std::replace(name.begin(), name.end(), ' ', '_');
     k << name << "|dir" << P->direction << "|wv" << P->wavelet << "|bt" << P->band_dtype << "|L"
-      << P->levels << "|n" << P->n << "|px2^" << int(std::lround(std::log2(double(std::max<int64_t>(px, 1)))));
+      << P->levels << "|n" << P->n << "|px2^" << int(std::lround(std::log2(double(std::max<int64_t>(px, 1)))))
+      << "|q" << plan_cta_q(P);  // the tile width: a cache from another CTA width does not apply
     return k.str();
 }
 
@@ -500,7 +511,7 @@ DWT2_EXPORT int dwt2_plan_create(const dwt2_image_desc* imgs, int n, int wavelet
         }
     }
     P->ctas_per_sm = occ;
-    P->rows_per_tile = default_rows(imgs, n, levels, occ * device_sm_count());
+    P->rows_per_tile = default_rows(imgs, n, levels, occ * device_sm_count(), plan_cta_q(P));
     bool tuned = false;
     std::string key;
     if (tune_cache && *tune_cache) {

@@ -4,7 +4,8 @@
 // results with vector stores.  One HBM read of the input and one write of the output per level.
 //
 // Geometry (all in polyphase quads; a quad is 2 x 2 pixels):
-//   CTA   = a strip of kCtaQ output quad columns (4 warps x 30 lanes x kQ) x rpc quad rows;
+//   CTA   = a strip of cta_q<NW>() output quad columns (NW = 3 or 4 consumer warps x 30 lanes
+//           x kQ) x rpc quad rows, plus one producer warp;
 //   warp  = a window of 32 x kQ quad columns (kQ adjacent quads per lane); lanes 0 and 31 are halo
 //           (they compute but never store: the lifting reaches 2 quads to each side);
 //   rows  = the CTA streams its rpc rows plus halo quad rows above and below (one per lifting
@@ -20,20 +21,34 @@
 
 namespace dwt2 {
 
-constexpr int kNW = 4;                   // consumer warps per CTA
 constexpr int kHQ = kQ;                  // halo quads on each side of a warp window (one lane)
 constexpr int kWarpQ = 32 * kQ;          // quads in a warp window
 constexpr int kWarpOut = kWarpQ - 2 * kHQ;  // output quads per warp (30 lanes)
-constexpr int kCtaQ = kNW * kWarpOut;    // output quads per CTA strip
-constexpr int kThreads = 32 * (kNW + 1);
+// Consumer warps per CTA: 4 (a 240-quad strip, 5 warps with the producer) or 3 (a 180-quad strip,
+// 4 warps).  At 80 registers an SM holds 24 warps: four 5-warp CTAs (16 consumer warps) or six
+// 4-warp CTAs (18).  The wide CTA is faster on planes it divides well (8192^2 9/7 forward 1.5%,
+// inverse 5%, int 5/3 forward 3% on GB300); the narrow one where the wide strips leave warps
+// idle: a 1024-pixel row is 512 quads, 2 strips of 240 and one of 32 (9 of 12 warp windows
+// busy) but 3 strips of 180 (9 of 9), and the batched 3-level transforms of 192 such images ran
+// 21% faster with it (pick_nw chooses per launch).  The stage rows are sized for the wide CTA.
+constexpr int kMaxNW = 4;
+template <int NW>
+constexpr int cta_q() {  // output quads per CTA strip
+    return NW * kWarpOut;
+}
+template <int NW>
+constexpr int cta_threads() {
+    return 32 * (NW + 1);
+}
+constexpr int kMaxCtaQ = cta_q<kMaxNW>();
 // Resident CTAs per SM the kernels are compiled for.  Measured on GB300: holding the cheap
 // wavelets (integer and float CDF 5/3) to 64 registers for 6 CTAs per SM was 7% faster with an
 // 8-stage ring (their 12-stage ring now holds them to 4 CTAs per SM by shared memory, which is
 // faster still).  The CDF 9/7 kernels are left free (78-80 registers, 4 CTAs per SM): bound to
 // 5 CTAs per SM (72 registers, no spills) the forward measured 6% and the inverse 9% slower.
-template <int WV>
-constexpr int min_ctas() {
-    return WV == 2 ? 1 : 6;
+template <int WV, int NW>
+constexpr int min_ctas() {  // the 5/3 kernels at 64 registers (6 wide or 8 narrow CTAs per SM)
+    return WV == 2 ? 1 : (NW == 3 ? 8 : 6);
 }
 // Consumer row loop unrolled by 2 for the 5/3 wavelets: the compiler then renames the row
 // pipeline's registers instead of rotating them (int 5/3 forward 4.7% faster on GB300).  The 9/7
@@ -72,14 +87,34 @@ constexpr int vhalo() {
 // as 256-wide boxes (every TMA destination starts on a 128-byte boundary).
 constexpr int kXL = 8;
 constexpr int kBoxW = 256;
-constexpr int kBoxes = (kXL + 2 * kCtaQ + 2 * kHQ + kBoxW - 1) / kBoxW;
+constexpr int kBoxes = (kXL + 2 * kMaxCtaQ + 2 * kHQ + kBoxW - 1) / kBoxW;
 constexpr int kSRow = kBoxes * kBoxW;
 // Inverse: a stage holds one row of each band, quad columns [qx0 - kXLB, +kBRow).
 constexpr int kXLB = 8;
-constexpr int kBBoxes = (kXLB + kCtaQ + kHQ + kBoxW - 1) / kBoxW;
+constexpr int kBBoxes = (kXLB + kMaxCtaQ + kHQ + kBoxW - 1) / kBoxW;
 constexpr int kBRow = kBBoxes * kBoxW;
-static_assert(kSRow >= kXL + 2 * kCtaQ + 2 * kHQ, "forward stage row too short");
-static_assert(kBRow >= kXLB + kCtaQ + kHQ, "inverse stage row too short");
+static_assert(kSRow >= kXL + 2 * kMaxCtaQ + 2 * kHQ, "forward stage row too short");
+static_assert(kBRow >= kXLB + kMaxCtaQ + kHQ, "inverse stage row too short");
+
+// A TMA copy must start on a 16-byte boundary in x.  The forward loads x = 2 qx0 - kXL + kBoxW b
+// input elements, the inverse x = qx0 - kXLB + kBoxW b band elements, qx0 a multiple of the CTA
+// strip: every term must be a multiple of 16 bytes.  The narrow strip (180 quads) fails this for
+// 16-bit bands in the inverse (odd strips would start 8 bytes off), so those keep the wide CTA.
+template <int NW, typename T>
+constexpr bool fwd_tma_x_aligned() {
+    return (2 * cta_q<NW>() * sizeof(T)) % 16 == 0 && (kXL * sizeof(T)) % 16 == 0 &&
+           (kBoxW * sizeof(T)) % 16 == 0;
+}
+template <int NW, typename T>
+constexpr bool inv_tma_x_aligned() {
+    return (cta_q<NW>() * sizeof(T)) % 16 == 0 && (kXLB * sizeof(T)) % 16 == 0 &&
+           (kBoxW * sizeof(T)) % 16 == 0;
+}
+// The narrowest CTA whose inverse band loads stay aligned: band type TB, LL type TL.
+template <typename TB, typename TL>
+constexpr int inv_narrow_nw() {
+    return inv_tma_x_aligned<3, TB>() && inv_tma_x_aligned<3, TL>() ? 3 : kMaxNW;
+}
 
 // A plane (or a batch of equally shaped planes): image z, row r starts at
 // ptr + z * bstride + r * pitch (bytes).
@@ -724,13 +759,14 @@ __device__ __forceinline__ Ring<NS> make_ring(uint8_t* smem_raw, size_t stage_by
     return r;
 }
 
-// Thread 0 initialises the barriers; every thread must call __syncthreads() afterwards.
-template <int NS>
+// Thread 0 initialises the barriers (the empty barriers take one arrival per consumer warp);
+// every thread must call __syncthreads() afterwards.
+template <int NW, int NS>
 __device__ __forceinline__ void init_ring(const Ring<NS>& r) {
     if (threadIdx.x == 0) {
         for (int s = 0; s < NS; ++s) {
             mbar_init(&r.full[s], 1);
-            mbar_init(&r.empty[s], kNW);
+            mbar_init(&r.empty[s], NW);
         }
         *r.abort = 0;
         fence_barrier_init();
@@ -753,14 +789,18 @@ constexpr bool kShiftable =
     std::is_same<C, float>::value && MODE != MODE_CONV && MODE != MODE_ADJ_INV;
 
 // =============================================================================================
-// Single-image kernels: one CTA = one tile (kCtaQ quad columns x rpc quad rows + halo) of one
+// Single-image kernels: one CTA = one tile (cta_q<NW>() quad columns x rpc quad rows + halo) of one
 // level.  MODE_ROWS writes the interleaved plane (the row pass of the two-pass separable
 // comparator); MODE_ADJ_INV is the transpose of the inverse level; every other mode is the
 // forward level.
 // =============================================================================================
-template <int WV, int MODE, typename TI, typename TB, typename TL, bool kPlain, bool kShift>
-__global__ void __launch_bounds__(kThreads, min_ctas<WV>())
+template <int WV, int MODE, typename TI, typename TB, typename TL, bool kPlain, bool kShift,
+          int NW>
+__global__ void __launch_bounds__(cta_threads<NW>(), min_ctas<WV, NW>())
     k_forward(const __grid_constant__ CUtensorMap tmap, const FwdArgs args) {
+    constexpr int kNW = NW;
+    constexpr int kCtaQ = cta_q<NW>();
+    static_assert(fwd_tma_x_aligned<NW, TI>(), "TMA x coordinates of this CTA width misaligned");
     constexpr bool kAdj = MODE == MODE_ADJ_INV;
     using Pipe = std::conditional_t<kAdj, AdjInvPipe<WV>, FwdPipe<WV, kAdj ? MODE_NONSEP : MODE>>;
     using C = typename Pipe::C;
@@ -778,7 +818,7 @@ __global__ void __launch_bounds__(kThreads, min_ctas<WV>())
     const int qfirst = n0 - kVH;
     const int xs = 2 * qx0 - kXL;
 
-    init_ring(ring);
+    init_ring<kNW>(ring);
     if (!kPlain && warp == kNW && lane == 0) prefetch_tensormap(&tmap);
     __syncthreads();
     // Everything above overlaps the previous level's tail; nothing below may touch global memory
@@ -853,7 +893,7 @@ __global__ void __launch_bounds__(kThreads, min_ctas<WV>())
             fwd_lane_row<TI, C>(reinterpret_cast<const TI*>(ring.stage(s)), cols, row);
         __syncwarp();
         if (lane == 0) mbar_arrive(&ring.empty[s]);
-        if constexpr (kShift) add_row_scalar(row, sh.in_add);
+        if constexpr (kShift) add_row(row, sh.in_add);
         if constexpr (kAdj)
             pipe.push(row, qfirst + i, hw, rows, args.scale);
         else
@@ -870,11 +910,15 @@ __global__ void __launch_bounds__(kThreads, min_ctas<WV>())
 
 // Inverse level (ADJ = false) or the transpose of the forward level (ADJ = true): four band
 // planes in, the interleaved plane out.
-template <int WV, typename TB, typename TL, typename TO, bool ADJ, bool kShift>
-__global__ void __launch_bounds__(kThreads, min_ctas<WV>())
+template <int WV, typename TB, typename TL, typename TO, bool ADJ, bool kShift, int NW>
+__global__ void __launch_bounds__(cta_threads<NW>(), min_ctas<WV, NW>())
     k_inverse(const __grid_constant__ CUtensorMap tm_ll, const __grid_constant__ CUtensorMap tm_hl,
               const __grid_constant__ CUtensorMap tm_lh, const __grid_constant__ CUtensorMap tm_hh,
               const InvArgs args) {
+    constexpr int kNW = NW;
+    constexpr int kCtaQ = cta_q<NW>();
+    static_assert(inv_tma_x_aligned<NW, TB>() && inv_tma_x_aligned<NW, TL>(),
+                  "TMA x coordinates of this CTA width misaligned");
     using Pipe = std::conditional_t<ADJ, AdjFwdPipe<WV>, InvPipe<WV>>;
     using C = typename Pipe::C;
     constexpr size_t kStageBytes = size_t(kBRow) * (sizeof(TL) + 3 * sizeof(TB));
@@ -892,7 +936,7 @@ __global__ void __launch_bounds__(kThreads, min_ctas<WV>())
     const int qfirst = n0 - kVH;
     const int xb = qx0 - kXLB;
 
-    init_ring(ring);
+    init_ring<kNW>(ring);
     if (args.tma && warp == kNW && lane == 0) {
         prefetch_tensormap(&tm_ll);
         prefetch_tensormap(&tm_hl);
@@ -989,10 +1033,10 @@ struct LaunchGeom {
 // data of a few MB (served from L2 after the previous level wrote it), where the per-row latency
 // of a CTA, not bytes, sets the time.
 inline LaunchGeom pick_geometry(int ner, int nec, int64_t plane_bytes, int sms, int ctas_per_sm,
-                                int nbatch) {
+                                int nbatch, int cta_quads) {
     constexpr int64_t kRowCost = 8;  // halo rows + pipeline fill, in rows
     const int n = std::max(1, nbatch);
-    const int strips = (nec + kCtaQ - 1) / kCtaQ;
+    const int strips = (nec + cta_quads - 1) / cta_quads;
     const int64_t slots = int64_t(std::max(1, sms)) * std::max(1, ctas_per_sm);
     const int min_rows = plane_bytes * n < (int64_t(24) << 20) ? 2 : 16;
     const int rb_max = std::max(1, (ner + min_rows - 1) / min_rows);
@@ -1019,10 +1063,11 @@ inline LaunchGeom pick_geometry(int ner, int nec, int64_t plane_bytes, int sms, 
 // Launch with programmatic stream serialization (the kernels wait for their predecessor with
 // griddepcontrol.wait before touching global memory).
 template <typename K, typename... Args>
-cudaError_t launch_pdl(K kernel, dim3 grid, size_t smem, cudaStream_t st, Args... args) {
+cudaError_t launch_pdl(K kernel, dim3 grid, int threads, size_t smem, cudaStream_t st,
+                       Args... args) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = grid;
-    cfg.blockDim = dim3(kThreads, 1, 1);
+    cfg.blockDim = dim3(threads, 1, 1);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = st;
     cudaLaunchAttribute attr[1];
@@ -1039,51 +1084,79 @@ int device_sm_count();
 // (the kernels need no L1 beyond the default; without this the driver may pick a smaller carveout
 // and fit fewer CTAs per SM), then returns the resident CTAs per SM.
 template <typename K>
-int configure(K kernel, size_t smem) {
+int configure(K kernel, int threads, size_t smem) {
     cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
     cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
                          int(cudaSharedmemCarveoutMaxShared));
     int n = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, kThreads, smem) != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, threads, smem) != cudaSuccess)
         n = 1;
     return n;
 }
 
-template <int WV, int MODE, typename TI, typename TB, typename TL, bool kPlain, bool kShift>
+// Consumer warps per CTA for a plane of nec quad columns: the narrow CTA where its strips keep at
+// least 10% more of the warp windows busy than the wide CTA's, else the wide one.
+inline int pick_nw(int nec) {
+    auto busy = [nec](int q) {
+        const int strips = (nec + q - 1) / q;
+        return double(nec) / double(int64_t(strips) * q);
+    };
+    return busy(cta_q<3>()) >= busy(cta_q<4>()) + 0.1 ? 3 : 4;
+}
+
+template <int WV, int MODE, typename TI, typename TB, typename TL, bool kPlain, bool kShift,
+          int NW>
 cudaError_t launch_forward_k(const CUtensorMap& tm, FwdArgs a, cudaStream_t st) {
-    auto k = k_forward<WV, MODE, TI, TB, TL, kPlain, kShift>;
+    auto k = k_forward<WV, MODE, TI, TB, TL, kPlain, kShift, NW>;
     constexpr size_t smem = fwd_smem_bytes<TI, fwd_stages<WV>()>();
-    static const int occ = configure(k, smem);
+    static const int occ = configure(k, cta_threads<NW>(), smem);
     const LaunchGeom g = pick_geometry(a.ner, a.nec, int64_t(a.H) * a.W * int64_t(sizeof(TI)),
-                                       device_sm_count(), occ, a.nbatch);
+                                       device_sm_count(), occ, a.nbatch, cta_q<NW>());
     a.rpc = g.rpc;
-    return launch_pdl(k, g.grid, smem, st, tm, a);
+    return launch_pdl(k, g.grid, cta_threads<NW>(), smem, st, tm, a);
 }
 
 // TMA-loading or plain-loading instantiation, by whether the input plane has a tensor map,
 // and the instantiation with the DC level shift only for the levels that take it (the first and
 // the last), so the others run exactly the code they would without it.
-template <int WV, int MODE, typename TI, typename TB, typename TL>
-cudaError_t launch_forward_t(const CUtensorMap& tm, FwdArgs a, cudaStream_t st) {
+template <int WV, int MODE, typename TI, typename TB, typename TL, int NW>
+cudaError_t launch_forward_nw(const CUtensorMap& tm, FwdArgs a, cudaStream_t st) {
     using C = std::conditional_t<WV == WV_CDF53_INT, int32_t, float>;
     if constexpr (kShiftable<C, MODE>) {
         if (a.shift.mode != 0)
-            return a.tma ? launch_forward_k<WV, MODE, TI, TB, TL, false, true>(tm, a, st)
-                         : launch_forward_k<WV, MODE, TI, TB, TL, true, true>(tm, a, st);
+            return a.tma ? launch_forward_k<WV, MODE, TI, TB, TL, false, true, NW>(tm, a, st)
+                         : launch_forward_k<WV, MODE, TI, TB, TL, true, true, NW>(tm, a, st);
     }
-    return a.tma ? launch_forward_k<WV, MODE, TI, TB, TL, false, false>(tm, a, st)
-                 : launch_forward_k<WV, MODE, TI, TB, TL, true, false>(tm, a, st);
+    return a.tma ? launch_forward_k<WV, MODE, TI, TB, TL, false, false, NW>(tm, a, st)
+                 : launch_forward_k<WV, MODE, TI, TB, TL, true, false, NW>(tm, a, st);
+}
+
+// ... and the CTA width by the plane's width (the separable comparators keep the wide CTA).
+template <int WV, int MODE, typename TI, typename TB, typename TL>
+cudaError_t launch_forward_t(const CUtensorMap& tm, FwdArgs a, cudaStream_t st) {
+    if constexpr (MODE == MODE_NONSEP || MODE == MODE_ADJ_INV) {
+        if (pick_nw(a.nec) == 3) return launch_forward_nw<WV, MODE, TI, TB, TL, 3>(tm, a, st);
+    }
+    return launch_forward_nw<WV, MODE, TI, TB, TL, kMaxNW>(tm, a, st);
+}
+
+template <int WV, typename TB, typename TL, typename TO, bool ADJ, bool kShift, int NW>
+cudaError_t launch_inverse_k(const CUtensorMap* tm, InvArgs a, cudaStream_t st) {
+    auto k = k_inverse<WV, TB, TL, TO, ADJ, kShift, NW>;
+    constexpr size_t smem = inv_smem_bytes<TL, TB, inv_stages<WV>()>();
+    static const int occ = configure(k, cta_threads<NW>(), smem);
+    const LaunchGeom g = pick_geometry(a.ner, a.nec, int64_t(a.H) * a.W * int64_t(sizeof(TL)),
+                                       device_sm_count(), occ, a.nbatch, cta_q<NW>());
+    a.rpc = g.rpc;
+    return launch_pdl(k, g.grid, cta_threads<NW>(), smem, st, tm[0], tm[1], tm[2], tm[3], a);
 }
 
 template <int WV, typename TB, typename TL, typename TO, bool ADJ, bool kShift>
-cudaError_t launch_inverse_k(const CUtensorMap* tm, InvArgs a, cudaStream_t st) {
-    auto k = k_inverse<WV, TB, TL, TO, ADJ, kShift>;
-    constexpr size_t smem = inv_smem_bytes<TL, TB, inv_stages<WV>()>();
-    static const int occ = configure(k, smem);
-    const LaunchGeom g = pick_geometry(a.ner, a.nec, int64_t(a.H) * a.W * int64_t(sizeof(TL)),
-                                       device_sm_count(), occ, a.nbatch);
-    a.rpc = g.rpc;
-    return launch_pdl(k, g.grid, smem, st, tm[0], tm[1], tm[2], tm[3], a);
+cudaError_t launch_inverse_s(const CUtensorMap* tm, InvArgs a, cudaStream_t st) {
+    if constexpr (inv_narrow_nw<TB, TL>() == 3) {
+        if (pick_nw(a.nec) == 3) return launch_inverse_k<WV, TB, TL, TO, ADJ, kShift, 3>(tm, a, st);
+    }
+    return launch_inverse_k<WV, TB, TL, TO, ADJ, kShift, kMaxNW>(tm, a, st);
 }
 
 // The inverse level with the DC level shift for the levels that take it (the last inverse level,
@@ -1091,9 +1164,9 @@ cudaError_t launch_inverse_k(const CUtensorMap* tm, InvArgs a, cudaStream_t st) 
 template <int WV, typename TB, typename TL, typename TO, bool ADJ = false>
 cudaError_t launch_inverse_t(const CUtensorMap* tm, InvArgs a, cudaStream_t st) {
     if constexpr (!ADJ && WV != WV_CDF53_INT) {
-        if (a.shift.mode != 0) return launch_inverse_k<WV, TB, TL, TO, false, true>(tm, a, st);
+        if (a.shift.mode != 0) return launch_inverse_s<WV, TB, TL, TO, false, true>(tm, a, st);
     }
-    return launch_inverse_k<WV, TB, TL, TO, ADJ, false>(tm, a, st);
+    return launch_inverse_s<WV, TB, TL, TO, ADJ, false>(tm, a, st);
 }
 
 }  // namespace dwt2
