@@ -673,19 +673,31 @@ __device__ __forceinline__ float tu_right(int k, AxisLen a) {
                : 0.f;
 }
 
-// Per-lane horizontal weights of the lane's kQ quads (quad columns m0 .. m0 + kQ - 1).
+// Per-lane horizontal weights of the lane's kQ quads (quad columns m0 .. m0 + kQ - 1).  ones:
+// every weight of every lane of the warp is 1 (a warp away from the plane's left and right
+// edges), so its rows away from the top and bottom edges can take the steps without weights.
 struct LaneW {
     float p_own[kQ], p_left[kQ], u_own[kQ], u_right[kQ];
+    bool ones;
     __device__ __forceinline__ void init(int m0, AxisLen cols) {
+        bool one = true;
 #pragma unroll
         for (int q = 0; q < kQ; ++q) {
             p_own[q] = tp_own(m0 + q, cols);
             p_left[q] = tp_left(m0 + q, cols);
             u_own[q] = tu_own(m0 + q, cols);
             u_right[q] = tu_right(m0 + q, cols);
+            one = one && p_own[q] == 1.f && p_left[q] == 1.f && u_own[q] == 1.f &&
+                  u_right[q] == 1.f;
         }
+        ones = __all_sync(0xffffffffu, one);
     }
 };
+// Rows n of an axis whose transposed-step weights are all 1 (tp_own, tp_left, tu_own, tu_right),
+// with a margin of kPairs rows for the pipelines' row offsets.
+__device__ __forceinline__ bool interior_row(int n, AxisLen rows, int margin) {
+    return n >= 1 + margin && n + margin < rows.nd - 1;
+}
 
 // Transpose of the fused update: U*^T (into g_c from g_a, into g_e from g_b; reads row n + 1),
 // then U^T (into g_b from g_a, into g_e from the new g_c; reads quad m + 1).  Predict-shaped,
@@ -702,8 +714,27 @@ struct AdjUpdate {
 #pragma unroll
         for (int q = 0; q < kQ; ++q) xar[q] = 0.f;
     }
+    template <bool kFast = false>
     __device__ __forceinline__ void push(const QRow<float>& y, int yn, QRow<float>& o,
                                          const LaneW& hw, AxisLen rows) {
+        if constexpr (kFast) {  // all weights 1: the bits the general form gives with them
+            float gc[kQ], gcr[kQ];
+#pragma unroll
+            for (int q = 0; q < kQ; ++q) gc[q] = fmaf(u, x.a[q], fmaf(u, y.a[q], x.c[q]));
+            right_of(gc, gcr);
+#pragma unroll
+            for (int q = 0; q < kQ; ++q) {
+                const float ge = fmaf(u, x.b[q], fmaf(u, y.b[q], x.e[q]));
+                o.a[q] = x.a[q];
+                o.b[q] = x.b[q] + u * (x.a[q] + xar[q]);
+                o.c[q] = gc[q];
+                o.e[q] = ge + u * (gc[q] + gcr[q]);
+            }
+            x = y;
+            xn = yn;
+            right_of(y.a, xar);
+            return;
+        }
         // the step's constant folded into the row weights: two FMAs per vertical term, as in
         // the forward steps.  (Folding it into the lane weights too would hold their products
         // in registers for the whole loop: 8 more, one CTA per SM fewer.)
@@ -737,7 +768,28 @@ struct AdjPredict {
 #pragma unroll
         for (int q = 0; q < kQ; ++q) pc[q] = pe[q] = 0.f;
     }
+    template <bool kFast = false>
     __device__ __forceinline__ void push(QRow<float>& r, int n, const LaneW& hw, AxisLen rows) {
+        if constexpr (kFast) {  // all weights 1
+            float ga[kQ], gb[kQ], gbl[kQ], gel[kQ];
+#pragma unroll
+            for (int q = 0; q < kQ; ++q) {
+                ga[q] = fmaf(p, r.c[q], fmaf(p, pc[q], r.a[q]));
+                gb[q] = fmaf(p, r.e[q], fmaf(p, pe[q], r.b[q]));
+            }
+            left_of(gb, gbl);
+            left_of(r.e, gel);
+#pragma unroll
+            for (int q = 0; q < kQ; ++q) {
+                const float gc = r.c[q] + p * (r.e[q] + gel[q]);
+                pc[q] = r.c[q];
+                pe[q] = r.e[q];
+                r.a[q] = ga[q] + p * (gb[q] + gbl[q]);
+                r.b[q] = gb[q];
+                r.c[q] = gc;
+            }
+            return;
+        }
         const float wo = p * tp_own(n, rows), wl = p * tp_left(n, rows);
         float ga[kQ], gb[kQ], gbl[kQ], gel[kQ];
 #pragma unroll
@@ -792,12 +844,23 @@ struct AdjFwdPipe {
             r.c[q] *= s.lh;
             r.e[q] *= s.hh;
         }
+        // rows n - kPairs .. n take part in this push; away from every edge no weight is needed
+        if (hw.ones && interior_row(n, rows, kPairs)) {
 #pragma unroll
-        for (int k = 0; k < kPairs; ++k) {
-            QRow<float> t;
-            tu[k].push(r, n - k, t, hw, rows);
-            tp[k].push(t, n - k - 1, hw, rows);
-            r = t;
+            for (int k = 0; k < kPairs; ++k) {
+                QRow<float> t;
+                tu[k].template push<true>(r, n - k, t, hw, rows);
+                tp[k].template push<true>(t, n - k - 1, hw, rows);
+                r = t;
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < kPairs; ++k) {
+                QRow<float> t;
+                tu[k].push(r, n - k, t, hw, rows);
+                tp[k].push(t, n - k - 1, hw, rows);
+                r = t;
+            }
         }
     }
 };
@@ -820,12 +883,22 @@ struct AdjInvPipe {
     }
     __device__ __forceinline__ void push(QRow<float>& r, int n, const LaneW& hw, AxisLen rows,
                                          const Scale4& inv_s) {
+        if (hw.ones && interior_row(n, rows, kPairs)) {
 #pragma unroll
-        for (int k = 0; k < kPairs; ++k) {
-            QRow<float> t;
-            tp[k].push(r, n - k, hw, rows);
-            tu[k].push(r, n - k, t, hw, rows);
-            r = t;
+            for (int k = 0; k < kPairs; ++k) {
+                QRow<float> t;
+                tp[k].template push<true>(r, n - k, hw, rows);
+                tu[k].template push<true>(r, n - k, t, hw, rows);
+                r = t;
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < kPairs; ++k) {
+                QRow<float> t;
+                tp[k].push(r, n - k, hw, rows);
+                tu[k].push(r, n - k, t, hw, rows);
+                r = t;
+            }
         }
 #pragma unroll
         for (int q = 0; q < kQ; ++q) {

@@ -1094,9 +1094,12 @@ int configure(K kernel, int threads, size_t smem) {
     return n;
 }
 
-// Consumer warps per CTA for a plane of nec quad columns: the narrow CTA where its strips keep at
-// least 10% more of the warp windows busy than the wide CTA's, else the wide one.
-inline int pick_nw(int nec) {
+// Consumer warps per CTA for a launch over planes of nec quad columns and `bytes` of input in all:
+// the narrow CTA where its strips keep at least 10 points more of the warp windows busy than the
+// wide CTA's, on launches of 24 MB or more.  Smaller launches are latency-bound, and the wide CTA
+// was faster there (levels 4 and 5 of an 8192^2 forward: 0.1412 against 0.1423 ms in all).
+inline int pick_nw(int nec, int64_t bytes) {
+    if (bytes < (int64_t(24) << 20)) return 4;
     auto busy = [nec](int q) {
         const int strips = (nec + q - 1) / q;
         return double(nec) / double(int64_t(strips) * q);
@@ -1135,7 +1138,8 @@ cudaError_t launch_forward_nw(const CUtensorMap& tm, FwdArgs a, cudaStream_t st)
 template <int WV, int MODE, typename TI, typename TB, typename TL>
 cudaError_t launch_forward_t(const CUtensorMap& tm, FwdArgs a, cudaStream_t st) {
     if constexpr (MODE == MODE_NONSEP || MODE == MODE_ADJ_INV) {
-        if (pick_nw(a.nec) == 3) return launch_forward_nw<WV, MODE, TI, TB, TL, 3>(tm, a, st);
+        if (pick_nw(a.nec, int64_t(a.H) * a.W * int64_t(sizeof(TI)) * a.nbatch) == 3)
+            return launch_forward_nw<WV, MODE, TI, TB, TL, 3>(tm, a, st);
     }
     return launch_forward_nw<WV, MODE, TI, TB, TL, kMaxNW>(tm, a, st);
 }
@@ -1154,7 +1158,9 @@ cudaError_t launch_inverse_k(const CUtensorMap* tm, InvArgs a, cudaStream_t st) 
 template <int WV, typename TB, typename TL, typename TO, bool ADJ, bool kShift>
 cudaError_t launch_inverse_s(const CUtensorMap* tm, InvArgs a, cudaStream_t st) {
     if constexpr (inv_narrow_nw<TB, TL>() == 3) {
-        if (pick_nw(a.nec) == 3) return launch_inverse_k<WV, TB, TL, TO, ADJ, kShift, 3>(tm, a, st);
+        const int64_t bytes = int64_t(a.H) * a.W * int64_t(sizeof(TL)) * a.nbatch;
+        if (pick_nw(a.nec, bytes) == 3)
+            return launch_inverse_k<WV, TB, TL, TO, ADJ, kShift, 3>(tm, a, st);
     }
     return launch_inverse_k<WV, TB, TL, TO, ADJ, kShift, kMaxNW>(tm, a, st);
 }
