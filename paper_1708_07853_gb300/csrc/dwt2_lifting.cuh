@@ -41,6 +41,11 @@ constexpr float k97Delta = 0.443506852043971f;
 constexpr float k97K = 1.230174104914001f;
 constexpr float k97Low = 1.0f / k97K;
 constexpr float k97High = k97K / 2.0f;
+// 2-D band scales of a 9/7 level (per axis low 1/K, high K/2)
+constexpr float k97sLL = k97Low * k97Low;
+constexpr float k97sHL = k97Low * k97High;
+constexpr float k97sLH = k97High * k97Low;
+constexpr float k97sHH = k97High * k97High;
 
 template <typename C>
 struct QRow {
@@ -991,10 +996,10 @@ struct FwdPipe {
             }
             if constexpr (WV == WV_CDF97) {
                 // per axis: low * 1/K, high * K/2 (COLS: vertical axis only)
-                constexpr float sLL = MODE == MODE_COLS ? k97Low : k97Low * k97Low;
-                constexpr float sHL = MODE == MODE_COLS ? k97Low : k97Low * k97High;
-                constexpr float sLH = MODE == MODE_COLS ? k97High : k97High * k97Low;
-                constexpr float sHH = MODE == MODE_COLS ? k97High : k97High * k97High;
+                constexpr float sLL = MODE == MODE_COLS ? k97Low : k97sLL;
+                constexpr float sHL = MODE == MODE_COLS ? k97Low : k97sHL;
+                constexpr float sLH = MODE == MODE_COLS ? k97High : k97sLH;
+                constexpr float sHH = MODE == MODE_COLS ? k97High : k97sHH;
 #pragma unroll
                 for (int q = 0; q < kQ; ++q) {
                     r.a[q] = fmaf(r.a[q], sLL, ll_add);
