@@ -128,12 +128,18 @@ constexpr int persist_min_ctas() {
     return WV == 2 ? 1 : 4;
 }
 
-// Plain-load path of the persistent kernels: 16-byte cp.async chunks issued by all producer
-// lanes and elementwise reads of the shifted stages.  The single-image kernels' bulk copies and
-// vector reads each made the 512-image batch about 1% slower here (its unaligned images are
-// mostly small, so their rows are short).
-constexpr bool kPersistBulk = false;
-constexpr bool kPersistVec = false;
+// Plain-load path of the persistent kernels, per wavelet.  The integer 5/3 takes the single-image
+// kernels' loader, one bulk copy per row and vector reads of the shifted stages: the 512-image
+// batch measured 0.965 against 0.982 ms on GB300.  The 9/7 keeps 16-byte cp.async chunks and
+// elementwise reads, with which it measured 1.165 against 1.179 ms.
+template <int WV>
+constexpr bool persist_bulk() {
+    return WV == WV_CDF53_INT;
+}
+template <int WV>
+constexpr bool persist_vec() {
+    return WV == WV_CDF53_INT;
+}
 
 // Ring depth of the persistent kernels: 8 stages for every wavelet (the single-image depths, 6
 // for the 9/7 forward and 12 for the 5/3, made the 512-image batch 1.4% and 0.4% slower).
@@ -215,7 +221,7 @@ __global__ void __launch_bounds__(cta_threads<kPersistFwdNW>(), persist_min_ctas
             pargs = U.a;
             const Tile tl = tile_of<kVH, kNW>(pargs, t - __ldg(&U.item_begin), __ldg(&U.strips));
             const int xs = 2 * tl.qx0 - kXL;
-            bulk_used |= pargs.tma != 0 || (kPersistBulk && !kAdj);
+            bulk_used |= pargs.tma != 0 || (persist_bulk<WV>() && !kAdj);
             bool alive = true;
             for (int i = 0; i < tl.nrows; ++i, ++g) {
                 const int s = g % kS;
@@ -227,7 +233,7 @@ __global__ void __launch_bounds__(cta_threads<kPersistFwdNW>(), persist_min_ctas
                     }
                 }
                 if (lane == 0) ring.meta[s] = t;
-                fwd_produce_row<TI, kSRow / 32, LOAD_RUNTIME, kPersistBulk>(
+                fwd_produce_row<TI, kSRow / 32, LOAD_RUNTIME, persist_bulk<WV>()>(
                                                 pargs, &U.tm, kAdj, tl.qfirst + i, xs,
                                                 reinterpret_cast<TI*>(ring.stage(s)),
                                                 &ring.full[s], lane, 0, &ring.shift[s]);
@@ -287,7 +293,7 @@ __global__ void __launch_bounds__(cta_threads<kPersistFwdNW>(), persist_min_ctas
             if (A.tma)
                 fwd_lane_row<TI, C>(reinterpret_cast<const TI*>(ring.stage(s)), cols, row);
             else
-                fwd_lane_row_shifted<TI, C, kPersistVec>(reinterpret_cast<const TI*>(ring.stage(s)),
+                fwd_lane_row_shifted<TI, C, persist_vec<WV>()>(reinterpret_cast<const TI*>(ring.stage(s)),
                                                          cols, row, ring.shift[s]);
             __syncwarp();
             if (lane == 0) mbar_arrive(&ring.empty[s]);
