@@ -118,7 +118,9 @@ def test_adjoint_batches_equal_single_image(wavelet):
 
 
 def test_large_batch_and_status():
-    """192 images of 1024 x 1024 (the autograd workload's per-call batch), 3 levels of 9/7."""
+    """192 images of 1024 x 1024 (the autograd workload's per-call batch), 3 levels of 9/7.
+    Launches of this size take the narrow CTA (180-quad strips), single 1024^2 images the wide
+    one: every direction must give the single-image bits."""
     N, H, W, levels = 192, 1024, 1024, 3
     x = _batch(N, H, W, torch.float32, 25)
     ws = D.new_workspace(D.workspace_bytes_batch(N, H, W, levels, "cdf97", D.DT_F32), "cuda")
@@ -129,4 +131,32 @@ def test_large_batch_and_status():
         _same(_coeffs_row(c, k, H, W, "cdf97", levels, D.DT_F32), D.forward(x[k], "cdf97", levels))
     y = D.inverse_batch(c, H, W, "cdf97", levels)
     torch.cuda.synchronize()
-    assert (y - x).abs().max().item() <= 2e-3
+    assert (y - x).abs().max().item() <= FLOAT_TOL
+    for k in (0, N - 1):
+        assert torch.equal(y[k], D.inverse(_coeffs_row(c, k, H, W, "cdf97", levels, D.DT_F32)))
+    # the adjoints of the same batch
+    gc = D.inverse_adjoint_batch(y, "cdf97", levels)
+    gy = D.forward_adjoint_batch(gc, H, W, "cdf97", levels)
+    torch.cuda.synchronize()
+    for k in (0, N - 1):
+        ck = _coeffs_row(gc, k, H, W, "cdf97", levels, D.DT_F32)
+        _same(ck, D.inverse_adjoint(y[k], "cdf97", levels))
+        assert torch.equal(gy[k], D.forward_adjoint(ck))
+
+
+def test_large_int_batch_unaligned_width():
+    """64 int32 images of 1000 x 998 (odd band widths, plain loads at level 1 as the pitch is
+    not a multiple of 16 bytes), 4 levels of the reversible 5/3: narrow CTAs in the batch, wide
+    ones for the single image, the same bits, and an exact round trip."""
+    N, H, W, levels = 64, 1000, 998, 4
+    x = _batch(N, H, W, torch.int32, 26)
+    c = D.forward_batch(x, "cdf53_int", levels)
+    y = D.inverse_batch(c, H, W, "cdf53_int", levels)
+    torch.cuda.synchronize()
+    assert torch.equal(y, x)
+    for k in (0, N - 1):
+        _same(_coeffs_row(c, k, H, W, "cdf53_int", levels, D.DT_I32),
+              D.forward(x[k].contiguous(), "cdf53_int", levels))
+    want = O.forward(x[N - 1].cpu().numpy().astype(np.int64), "cdf53_int", levels)
+    for gv, w in zip(gpu_bands(_coeffs_row(c, N - 1, H, W, "cdf53_int", levels, D.DT_I32)), want):
+        assert np.array_equal(gv, w)
