@@ -908,6 +908,101 @@ __global__ void __launch_bounds__(cta_threads<NW>(), min_ctas<WV, NW>())
     }
 }
 
+// =============================================================================================
+// Direct forward level for small planes (a few MB, in L2 after the previous level wrote them).
+// The streaming kernel's fixed costs -- a producer warp, the stage ring and its barriers, the TMA
+// latency of the first rows and the pipeline fill -- dominate there, and every level costs a
+// few microseconds whatever its size.  Here each warp is one 60-quad window of kDirectRows output
+// quad rows: it loads the kDirectRows + 2 kLag input quad rows it needs straight from global
+// memory (L2) into registers, all at once, then pushes them through the same FwdPipe and stores
+// through the same band rows as the streaming kernel, so the results are the same bits.  The
+// halo rows are loaded and computed again by the windows above and below.
+// =============================================================================================
+constexpr int kDirectRows = 2;     // output quad rows per warp
+constexpr int kDirectWarps = 4;    // warps (windows) per CTA
+// Largest input (bytes, all images of a launch) a level takes the direct kernel for.
+constexpr int64_t kDirectMaxBytes = int64_t(4) << 20;
+
+// refl for the direct kernels, whose rows and columns are mostly inside the plane already.
+__device__ __forceinline__ int refl_in(int i, int n) {
+    return unsigned(i) < unsigned(n) ? i : refl(i, n);
+}
+
+// A lane's 2 kQ pixels of pixel row r of the plane: aligned vector loads where the window lies
+// inside the plane, else elementwise from the columns col (mirrored at the edges).
+template <typename TI, typename C>
+__device__ __forceinline__ void direct_load_row(const char* base, int64_t pitch, int r,
+                                                const int (&col)[2 * kQ], bool vec,
+                                                C (&v)[2 * kQ]) {
+    const TI* row = reinterpret_cast<const TI*>(base + int64_t(r) * pitch);
+    if (vec) {
+        ldN<2 * kQ>(row + col[0], v);
+    } else {
+#pragma unroll
+        for (int k = 0; k < 2 * kQ; ++k) v[k] = to_c(ldcg(row + col[k]));
+    }
+}
+
+template <int WV, typename TI, typename TB, typename TL, bool kShift>
+__global__ void __launch_bounds__(32 * kDirectWarps) k_forward_direct(const FwdArgs args) {
+    using Pipe = FwdPipe<WV, MODE_NONSEP>;
+    using C = typename Pipe::C;
+    constexpr int kLag = Pipe::kLag;
+    constexpr int kRows = kDirectRows + 2 * kLag;  // input quad rows per warp
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int z = blockIdx.z;
+    // grid x runs over row blocks (a tall plane may have more than 65535 of them), y over strips
+    const int wq = (blockIdx.y * kDirectWarps + warp) * kWarpOut - kHQ;  // first quad of the window
+    const int m0 = wq + kQ * lane;
+    const int n0 = blockIdx.x * kDirectRows;
+    const int n1 = min(n0 + kDirectRows, args.ner);
+    const bool store_lane = lane >= 1 && lane <= 30;
+    grid_dependency_wait();  // the input plane is the previous level's output
+    allow_dependent_launch();
+    if (wq + kHQ >= args.nec) return;  // a window wholly beyond the plane: the warp has no work
+
+    const char* base = static_cast<const char*>(args.in) + int64_t(z) * args.in_bstride;
+    const bool edge = (2 * wq < 0) || (2 * wq + 2 * kWarpQ > args.W);
+    const bool vec = !edge && (reinterpret_cast<uintptr_t>(base) % (4 * sizeof(TI))) == 0 &&
+                     args.in_pitch % int64_t(4 * sizeof(TI)) == 0;
+    int col[2 * kQ];
+#pragma unroll
+    for (int k = 0; k < 2 * kQ; ++k) col[k] = refl_in(2 * m0 + k, args.W);
+    QRow<C> rows[kRows];
+#pragma unroll
+    for (int i = 0; i < kRows; ++i) {
+        const int q = n0 - kLag + i;
+        C v0[2 * kQ], v1[2 * kQ];
+        direct_load_row<TI, C>(base, args.in_pitch, refl_in(2 * q, args.H), col, vec, v0);
+        direct_load_row<TI, C>(base, args.in_pitch, refl_in(2 * q + 1, args.H), col, vec, v1);
+#pragma unroll
+        for (int k = 0; k < kQ; ++k) {
+            rows[i].a[k] = v0[2 * k];
+            rows[i].b[k] = v0[2 * k + 1];
+            rows[i].c[k] = v1[2 * k];
+            rows[i].e[k] = v1[2 * k + 1];
+        }
+    }
+    LevelShift sh{-0.f, -0.f};
+    if constexpr (kShift) sh.init(args.shift, z);
+    Pipe pipe;
+    if constexpr (kShift) pipe.init(sh.out_add);
+    else pipe.init();
+    BandRows bands;
+    bands.init<TB, TL>(args, n0, m0, z);
+#pragma unroll
+    for (int i = 0; i < kRows; ++i) {
+        QRow<C> row = rows[i];
+        if constexpr (kShift) add_row(row, sh.in_add);
+        pipe.push(row);
+        const int qo = n0 - kLag + i - kLag;
+        if (i >= 2 * kLag && qo < n1) {
+            if (store_lane) fwd_store_bands<TB, TL>(args, bands, row, qo, m0);
+            bands.next(args);
+        }
+    }
+}
+
 // Inverse level (ADJ = false) or the transpose of the forward level (ADJ = true): four band
 // planes in, the interleaved plane out.
 template <int WV, typename TB, typename TL, typename TO, bool ADJ, bool kShift, int NW>
@@ -1009,6 +1104,101 @@ __global__ void __launch_bounds__(cta_threads<NW>(), min_ctas<WV, NW>())
             pipe.push(row);
         const int qo = qfirst + i - Pipe::kLag;
         if (qo >= n0 && qo < n1) {
+            if constexpr (kShift) add_row(row, sh.out_add);
+            if (store_lane) inv_store_rows_at<TO>(args, row, qo, m0, out_p);
+            out_p += 2 * args.out.pitch;
+        }
+    }
+}
+
+// =============================================================================================
+// Direct inverse level for small planes: the inverse counterpart of k_forward_direct.  Each warp
+// loads the band rows of kDirectRows + 2 kLag extended quad rows (mirrored rows and columns,
+// as the streaming kernel's stages hold them) straight from global memory into registers and
+// pushes them through the same InvPipe.
+// =============================================================================================
+// A lane's kQ values of band row r (false ok: a row outside the band, zeros); columns m0 + j,
+// or the mirrored columns col[j] at the plane's edges.
+template <typename T, typename C>
+__device__ __forceinline__ void direct_load_band(const char* row, bool ok, int m0, bool vec,
+                                                 bool edge, const int (&col)[kQ], bool zero,
+                                                 C (&v)[kQ]) {
+    const T* p = reinterpret_cast<const T*>(row);
+    if (!ok || zero) {
+#pragma unroll
+        for (int j = 0; j < kQ; ++j) v[j] = C(0);
+    } else if (vec) {
+        ldN<kQ>(p + m0, v);
+    } else {
+#pragma unroll
+        for (int j = 0; j < kQ; ++j) v[j] = to_c(ldcg(p + (edge ? col[j] : m0 + j)));
+    }
+}
+
+template <int WV, typename TB, typename TL, typename TO, bool kShift>
+__global__ void __launch_bounds__(32 * kDirectWarps) k_inverse_direct(const InvArgs args) {
+    using Pipe = InvPipe<WV>;
+    using C = typename Pipe::C;
+    constexpr int kLag = Pipe::kLag;
+    constexpr int kRows = kDirectRows + 2 * kLag;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int z = blockIdx.z;
+    const int wq = (blockIdx.y * kDirectWarps + warp) * kWarpOut - kHQ;
+    const int m0 = wq + kQ * lane;
+    const int n0 = blockIdx.x * kDirectRows;
+    const int n1 = min(n0 + kDirectRows, args.ner);
+    const bool store_lane = lane >= 1 && lane <= 30;
+    grid_dependency_wait();
+    allow_dependent_launch();
+    if (wq + kHQ >= args.nec) return;
+
+    // columns: LL / LH hold the even pixel columns 2m, HL / HH the odd ones 2m + 1
+    const bool edge = (2 * wq < 0) || (2 * wq + 2 * kWarpQ > args.W);
+    const bool odd_zero = args.W <= 1;
+    int ce[kQ], co[kQ];
+#pragma unroll
+    for (int j = 0; j < kQ; ++j) {
+        ce[j] = refl_in(2 * (m0 + j), args.W) >> 1;
+        co[j] = odd_zero ? 0 : (refl_in(2 * (m0 + j) + 1, args.W) - 1) >> 1;
+    }
+    const char* base[4];
+    bool vec = !edge;
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+        base[b] = static_cast<const char*>(args.band[b]) + int64_t(z) * args.band_bstride[b];
+        const int64_t esz = b == 0 ? sizeof(TL) : sizeof(TB);
+        vec = vec && (reinterpret_cast<uintptr_t>(base[b]) % (kQ * esz)) == 0 &&
+              args.band_pitch[b] % (kQ * esz) == 0;
+    }
+    QRow<C> rows[kRows];
+#pragma unroll
+    for (int i = 0; i < kRows; ++i) {
+        const int q = n0 - kLag + i;
+        const int re = refl_in(2 * q, args.H) >> 1;                              // LL / HL row
+        const int ro = args.H > 1 ? (refl_in(2 * q + 1, args.H) - 1) >> 1 : -1;  // LH / HH row
+        const bool ok_o = ro >= 0;
+        const int roc = ok_o ? ro : 0;
+        direct_load_band<TL, C>(base[0] + int64_t(re) * args.band_pitch[0], true, m0, vec, edge,
+                                ce, false, rows[i].a);
+        direct_load_band<TB, C>(base[1] + int64_t(re) * args.band_pitch[1], true, m0, vec, edge,
+                                co, odd_zero, rows[i].b);
+        direct_load_band<TB, C>(base[2] + int64_t(roc) * args.band_pitch[2], ok_o, m0, vec, edge,
+                                ce, false, rows[i].c);
+        direct_load_band<TB, C>(base[3] + int64_t(roc) * args.band_pitch[3], ok_o, m0, vec, edge,
+                                co, odd_zero, rows[i].e);
+    }
+    LevelShift sh{-0.f, -0.f};
+    if constexpr (kShift) sh.init(args.shift, z);
+    char* out_p = reinterpret_cast<char*>(row_ptr<TO>(args.out, 2 * n0, z) + 2 * m0);
+    Pipe pipe;
+    pipe.init();
+#pragma unroll
+    for (int i = 0; i < kRows; ++i) {
+        QRow<C> row = rows[i];
+        if constexpr (kShift) add_ll(row, sh.in_add);
+        pipe.push(row);
+        const int qo = n0 - 2 * kLag + i;
+        if (i >= 2 * kLag && qo < n1) {
             if constexpr (kShift) add_row(row, sh.out_add);
             if (store_lane) inv_store_rows_at<TO>(args, row, qo, m0, out_p);
             out_p += 2 * args.out.pitch;
@@ -1134,9 +1324,29 @@ cudaError_t launch_forward_nw(const CUtensorMap& tm, FwdArgs a, cudaStream_t st)
                  : launch_forward_k<WV, MODE, TI, TB, TL, true, false, NW>(tm, a, st);
 }
 
+template <int WV, typename TI, typename TB, typename TL, bool kShift>
+cudaError_t launch_forward_direct(FwdArgs a, cudaStream_t st) {
+    auto k = k_forward_direct<WV, TI, TB, TL, kShift>;
+    const int windows = (a.nec + kWarpOut - 1) / kWarpOut;
+    const dim3 grid((a.ner + kDirectRows - 1) / kDirectRows,
+                    (windows + kDirectWarps - 1) / kDirectWarps, std::max(1, a.nbatch));
+    a.rpc = kDirectRows;
+    return launch_pdl(k, grid, 32 * kDirectWarps, 0, st, a);
+}
+
 // ... and the CTA width by the plane's width (the separable comparators keep the wide CTA).
+// Small planes of the non-separable forward take the direct kernel.
 template <int WV, int MODE, typename TI, typename TB, typename TL>
 cudaError_t launch_forward_t(const CUtensorMap& tm, FwdArgs a, cudaStream_t st) {
+    if constexpr (MODE == MODE_NONSEP) {
+        if (int64_t(a.H) * a.W * int64_t(sizeof(TI)) * std::max(1, a.nbatch) <= kDirectMaxBytes) {
+            using C = std::conditional_t<WV == WV_CDF53_INT, int32_t, float>;
+            if constexpr (kShiftable<C, MODE>) {
+                if (a.shift.mode != 0) return launch_forward_direct<WV, TI, TB, TL, true>(a, st);
+            }
+            return launch_forward_direct<WV, TI, TB, TL, false>(a, st);
+        }
+    }
     if constexpr (MODE == MODE_NONSEP || MODE == MODE_ADJ_INV) {
         if (pick_nw(a.nec, int64_t(a.H) * a.W * int64_t(sizeof(TI)) * a.nbatch) == 3)
             return launch_forward_nw<WV, MODE, TI, TB, TL, 3>(tm, a, st);
@@ -1167,8 +1377,27 @@ cudaError_t launch_inverse_s(const CUtensorMap* tm, InvArgs a, cudaStream_t st) 
 
 // The inverse level with the DC level shift for the levels that take it (the last inverse level,
 // which takes the shift off LL_J, and the first, which puts it back).
+template <int WV, typename TB, typename TL, typename TO, bool kShift>
+cudaError_t launch_inverse_direct(InvArgs a, cudaStream_t st) {
+    auto k = k_inverse_direct<WV, TB, TL, TO, kShift>;
+    const int windows = (a.nec + kWarpOut - 1) / kWarpOut;
+    const dim3 grid((a.ner + kDirectRows - 1) / kDirectRows,
+                    (windows + kDirectWarps - 1) / kDirectWarps, std::max(1, a.nbatch));
+    a.rpc = kDirectRows;
+    return launch_pdl(k, grid, 32 * kDirectWarps, 0, st, a);
+}
+
+// Small output planes of the inverse take the direct kernel.
 template <int WV, typename TB, typename TL, typename TO, bool ADJ = false>
 cudaError_t launch_inverse_t(const CUtensorMap* tm, InvArgs a, cudaStream_t st) {
+    if constexpr (!ADJ) {
+        if (int64_t(a.H) * a.W * int64_t(sizeof(TL)) * std::max(1, a.nbatch) <= kDirectMaxBytes) {
+            if constexpr (WV != WV_CDF53_INT) {
+                if (a.shift.mode != 0) return launch_inverse_direct<WV, TB, TL, TO, true>(a, st);
+            }
+            return launch_inverse_direct<WV, TB, TL, TO, false>(a, st);
+        }
+    }
     if constexpr (!ADJ && WV != WV_CDF53_INT) {
         if (a.shift.mode != 0) return launch_inverse_s<WV, TB, TL, TO, false, true>(tm, a, st);
     }

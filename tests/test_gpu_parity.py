@@ -103,6 +103,33 @@ def test_float_all_levels(wavelet, H, W):
         assert np.abs(r2 - want_x).max() <= FLOAT_TOL, ("inv", wavelet, H, W, lv)
 
 
+# Planes of more than 4 MB (all images of a launch together) take the streaming kernels; smaller
+# ones, every case above, the direct kernels.  Ragged shapes just above that size, with aligned
+# (TMA) and unaligned (plain-load) rows, for the streaming kernels' edges.
+STREAM_RAGGED = [(1201, 1003), (2049, 613), (517, 2311)]
+
+
+@pytest.mark.parametrize("wavelet", ["cdf53_int", "cdf97"])
+@pytest.mark.parametrize("H,W", STREAM_RAGGED)
+@pytest.mark.parametrize("pad", [0, 1])
+def test_streaming_ragged_above_direct_size(wavelet, H, W, pad):
+    rng = np.random.default_rng(H + 3 * W + pad)
+    is_int = wavelet == "cdf53_int"
+    dt = torch.int32 if is_int else torch.float32
+    x = (rng.integers(-(2 ** 15), 2 ** 15 + 1, (H, W)).astype(np.int32) if is_int
+         else rng.uniform(0, 255, (H, W)).astype(np.float32))
+    for lv in (1, 3):
+        c = D.forward(to_gpu(x, dt, pad), wavelet, lv)
+        want = O.forward(x.astype(np.int64 if is_int else np.float64), wavelet, lv)
+        assert_bands(gpu_bands(c), want, 0 if is_int else FLOAT_TOL, ("fwd", wavelet, H, W, lv))
+        out = torch.zeros((H, W + pad), dtype=dt, device="cuda")[:, :W]
+        r = D.inverse(c, out=out).cpu().numpy()
+        if is_int:
+            assert (r == x).all(), ("inv", H, W, lv)
+        else:
+            assert np.abs(r - x).max() <= FLOAT_TOL, ("roundtrip", H, W, lv)
+
+
 def test_cdf53_float_one_level_exact_config_512():
     """512 x 512 integer field in [0, 255], float CDF 5/3, one level: exact in fp32."""
     x = I.field(512, 512, I.seed_for(0))
