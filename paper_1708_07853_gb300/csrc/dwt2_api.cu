@@ -35,6 +35,20 @@ int device_sm_count() {
     return n;
 }
 
+// L2 bytes a level may ask to keep for the next one: its LL output, stored evict_last, if the
+// planes of all images of the launch fit in three quarters of the device's L2 (the LL_1 of an
+// 8192^2 fp32 image, 64 MiB, does) and the next level streams (the direct kernels of small
+// planes read from L2 anyway).
+static int64_t l2_keep_budget() {
+    static int64_t n = [] {
+        int dev = 0, v = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&v, cudaDevAttrL2CacheSize, dev) != cudaSuccess) v = 0;
+        return int64_t(v) / 4 * 3;
+    }();
+    return n;
+}
+
 static size_t esize(int dt) { return dt == DT_BF16 || dt == DT_F16 ? 2 : 4; }
 static int64_t align_up(int64_t v, int64_t a) { return (v + a - 1) / a * a; }
 static bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
@@ -323,6 +337,7 @@ static int forward_impl(const void* img, int64_t img_pitch, int H, int W, int im
     int in_dt = img_dtype;
     // float lifting takes the DC level shift; the adjoint and the convolution scheme do not
     const bool shifted = wavelet != WV_CDF53_INT && !adjoint && scheme != DWT2_SCHEME_CONV;
+    bool in_kept = false;  // the previous level stored this level's input evict_last
     for (int j = 1; j <= J; ++j) {
         const int h = L.h[j - 1], w = L.w[j - 1];
         FwdArgs a = level_args(in, in_pitch, in_bstride, h, w, bt.N, status);
@@ -334,6 +349,12 @@ static int forward_impl(const void* img, int64_t img_pitch, int H, int W, int im
         a.hh = {cb + bhh.offset_bytes, bhh.pitch_bytes, cbs};
         if (j == J) a.ll = {cb + L.band[0].offset_bytes, L.band[0].pitch_bytes, cbs};
         else a.ll = {wb + wp.off[(j - 1) % 2], wp.pitch[(j - 1) % 2], region};
+        // LL_j stays in L2 for level j + 1 when it fits and that level streams
+        const bool next_direct = scheme == DWT2_SCHEME_NONSEP && !adjoint &&
+                                 takes_direct(L.h[j], L.w[j], esize(ll_dt), bt.N);
+        a.ll_keep = keeps_ll_in_l2(wavelet) && j < J && !next_direct &&
+                    a.ll.pitch * int64_t(L.h[j]) * bt.N <= l2_keep_budget();
+        a.in_kept = in_kept;
 
         cudaError_t e;
         if (scheme == DWT2_SCHEME_SEP_TWOPASS) {
@@ -350,6 +371,7 @@ static int forward_impl(const void* img, int64_t img_pitch, int H, int W, int im
             if (e != cudaSuccess) return cuda_fail(e, "row pass");
             FwdArgs c = level_args(wb + wp.off[2], wp.pitch[2], 0, h, w, 1, status);
             c.ll = a.ll;
+            c.ll_keep = a.ll_keep;
             c.hl = a.hl;
             c.lh = a.lh;
             c.hh = a.hh;
@@ -384,6 +406,7 @@ static int forward_impl(const void* img, int64_t img_pitch, int H, int W, int im
         in_pitch = a.ll.pitch;
         in_bstride = a.ll.bstride;
         in_dt = ll_dt;
+        in_kept = a.ll_keep != 0;
     }
     return DWT2_OK;
 }
@@ -415,6 +438,7 @@ static int inverse_impl(const void* coeffs, void* img, int64_t img_pitch, int H,
     const int ll_dt = wavelet == WV_CDF53_INT ? DT_I32 : DT_F32;
 
     const bool shifted = wavelet != WV_CDF53_INT && !adjoint;
+    bool ll_kept = false;  // the previous level stored this level's LL evict_last
     for (int j = J; j >= 1; --j) {
         const int h = L.h[j - 1], w = L.w[j - 1];
         InvArgs a;
@@ -456,6 +480,13 @@ static int inverse_impl(const void* coeffs, void* img, int64_t img_pitch, int H,
         const size_t vbytes = 4 * esize(out_dt);
         a.out_vec = aligned(a.out.ptr, vbytes) && a.out.pitch % int64_t(vbytes) == 0 &&
                     a.out.bstride % int64_t(vbytes) == 0;
+        // LL_(j-1) stays in L2 for level j - 1 when it fits and that level streams
+        const bool next_direct =
+            j > 1 && !adjoint && takes_direct(L.h[j - 2], L.w[j - 2], esize(ll_dt), bt.N);
+        a.out_keep = keeps_ll_in_l2(wavelet) && j > 1 && !next_direct &&
+                     a.out.pitch * int64_t(h) * bt.N <= l2_keep_budget();
+        a.ll_kept = ll_kept;
+        ll_kept = a.out_keep != 0;
 
         // TMA needs all four band planes non-empty (h, w >= 2); the plain-load path covers the
         // rest (and planes whose base, pitch or batch stride TMA cannot address).

@@ -101,6 +101,33 @@ __device__ __forceinline__ void tma_load_3d(void* smem_dst, const CUtensorMap* m
         : "memory");
 }
 
+// The same with an L2 eviction priority (a createpolicy operand) for the loaded lines.
+__device__ __forceinline__ void tma_load_3d_hint(void* smem_dst, const CUtensorMap* map,
+                                                 uint64_t* bar, int x, int y, int z,
+                                                 uint64_t policy) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        ".L2::cache_hint [%0], [%1, {%2, %3, %4}], [%5], %6;" ::"r"(smem_u32(smem_dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar)),
+        "l"(policy)
+        : "memory");
+}
+
+// L2 eviction policies (createpolicy, the whole access range).  A level whose LL output the next
+// level reads stores it evict_last, so that it stays in L2 while the level streams its input and
+// detail bands through; the next level reads it back with evict_normal, which returns the lines
+// to the normal priority once they are used.
+__device__ __forceinline__ uint64_t l2_evict_last() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+__device__ __forceinline__ uint64_t l2_evict_normal() {
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_normal.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+
 // Bulk (non-tensor) copy of `bytes` bytes from global to shared memory, completing on an
 // mbarrier (transaction bytes).  Both addresses 16-byte aligned, bytes a multiple of 16.
 __device__ __forceinline__ void bulk_copy_g2s(void* smem_dst, const void* src, uint32_t bytes,
@@ -243,6 +270,33 @@ __device__ __forceinline__ void st4(T* p, C v0, C v1, C v2, C v3) {
         *reinterpret_cast<uint4*>(p) = *reinterpret_cast<const uint4*>(t);
     else
         *reinterpret_cast<uint2*>(p) = *reinterpret_cast<const uint2*>(t);
+}
+
+// Vector stores to global memory with an L2 eviction policy (from createpolicy).
+template <typename T, typename C>
+__device__ __forceinline__ void st2_hint(T* p, C v0, C v1, uint64_t pol) {
+    T t[2] = {from_c<T>(v0), from_c<T>(v1)};
+    if constexpr (sizeof(T) == 4) {
+        const uint2 u = *reinterpret_cast<const uint2*>(t);
+        asm volatile("st.global.L2::cache_hint.v2.b32 [%0], {%1, %2}, %3;" ::"l"(p), "r"(u.x),
+                     "r"(u.y), "l"(pol));
+    } else {
+        const uint32_t u = *reinterpret_cast<const uint32_t*>(t);
+        asm volatile("st.global.L2::cache_hint.b32 [%0], %1, %2;" ::"l"(p), "r"(u), "l"(pol));
+    }
+}
+template <typename T, typename C>
+__device__ __forceinline__ void st4_hint(T* p, C v0, C v1, C v2, C v3, uint64_t pol) {
+    T t[4] = {from_c<T>(v0), from_c<T>(v1), from_c<T>(v2), from_c<T>(v3)};
+    if constexpr (sizeof(T) == 4) {
+        const uint4 u = *reinterpret_cast<const uint4*>(t);
+        asm volatile("st.global.L2::cache_hint.v4.b32 [%0], {%1, %2, %3, %4}, %5;" ::"l"(p),
+                     "r"(u.x), "r"(u.y), "r"(u.z), "r"(u.w), "l"(pol));
+    } else {
+        const uint2 u = *reinterpret_cast<const uint2*>(t);
+        asm volatile("st.global.L2::cache_hint.v2.b32 [%0], {%1, %2}, %3;" ::"l"(p), "r"(u.x),
+                     "r"(u.y), "l"(pol));
+    }
 }
 
 // ------------------------------------------------------------------ warp neighbour exchange

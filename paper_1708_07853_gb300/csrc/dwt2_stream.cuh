@@ -159,6 +159,8 @@ struct FwdArgs {
     int tma;            // 1: load the input plane with TMA (16-byte aligned base and pitch)
     int nbatch;         // images in the batch (grid z)
     ShiftSrc shift;     // DC level shift: kShiftIn at level 1, kShiftOut (onto LL) at level J
+    int ll_keep;        // 1: store LL evict_last (the next level reads it back from L2)
+    int in_kept;        // 1: the input was stored evict_last; read it back with evict_normal
 };
 
 struct InvArgs {
@@ -175,6 +177,8 @@ struct InvArgs {
     int tma;              // 1: load the band planes with TMA
     int nbatch;           // images in the batch (grid z)
     ShiftSrc shift;       // DC level shift: kShiftIn (from LL) at level J, kShiftOut at level 1
+    int out_keep;         // 1: store the output (the next level's LL) evict_last
+    int ll_kept;          // 1: LL was stored evict_last; read it back with evict_normal
 };
 
 // The level shift c of image z (0 when none): see ShiftSrc.
@@ -232,6 +236,21 @@ template <int N, typename T, typename C>
 __device__ __forceinline__ void putN(T* p, const C (&v)[N], int c0, int width, bool vec) {
     if (vec && c0 + N - 1 < width) {
         stN<N>(p, v);
+    } else {
+#pragma unroll
+        for (int k = 0; k < N; ++k)
+            if (c0 + k >= 0 && c0 + k < width) p[k] = from_c<T>(v[k]);
+    }
+}
+
+// putN with an L2 eviction policy on the vector stores (the clipped edge stores are plain).
+template <int N, typename T, typename C>
+__device__ __forceinline__ void putN_hint(T* p, const C (&v)[N], int c0, int width, bool vec,
+                                          uint64_t pol) {
+    static_assert(N == 2 || N == 4, "vector width");
+    if (vec && c0 + N - 1 < width) {
+        if constexpr (N == 2) st2_hint(p, v[0], v[1], pol);
+        else st4_hint(p, v[0], v[1], v[2], v[3], pol);
     } else {
 #pragma unroll
         for (int k = 0; k < N; ++k)
@@ -384,7 +403,8 @@ enum Loader { LOAD_RUNTIME = 0, LOAD_TMA = 1, LOAD_PLAIN = 2 };
 template <typename TI, int kUnrollPlain = 1, int kLoader = LOAD_RUNTIME, bool kBulk = true>
 __device__ __forceinline__ void fwd_produce_row(const FwdArgs& a, const CUtensorMap* tm, bool adj,
                                                 int q, int xs, TI* dst, uint64_t* full, int lane,
-                                                int z, volatile int* shift_slot) {
+                                                int z, volatile int* shift_slot,
+                                                const uint64_t* l2_pol = nullptr) {
     const int r0 = adj ? 2 * q : refl(2 * q, a.H);
     const int r1 = adj ? 2 * q + 1 : refl(2 * q + 1, a.H);
     const bool use_tma = kLoader == LOAD_TMA || (kLoader == LOAD_RUNTIME && a.tma);
@@ -393,8 +413,14 @@ __device__ __forceinline__ void fwd_produce_row(const FwdArgs& a, const CUtensor
             mbar_arrive_expect_tx(full, 2 * kSRow * sizeof(TI));
 #pragma unroll
             for (int b = 0; b < kBoxes; ++b) {
-                tma_load_3d(dst + b * kBoxW, tm, full, xs + b * kBoxW, r0, z);
-                tma_load_3d(dst + kSRow + b * kBoxW, tm, full, xs + b * kBoxW, r1, z);
+                if (l2_pol) {
+                    tma_load_3d_hint(dst + b * kBoxW, tm, full, xs + b * kBoxW, r0, z, *l2_pol);
+                    tma_load_3d_hint(dst + kSRow + b * kBoxW, tm, full, xs + b * kBoxW, r1, z,
+                                     *l2_pol);
+                } else {
+                    tma_load_3d(dst + b * kBoxW, tm, full, xs + b * kBoxW, r0, z);
+                    tma_load_3d(dst + kSRow + b * kBoxW, tm, full, xs + b * kBoxW, r1, z);
+                }
             }
         }
     } else if constexpr (kLoader != LOAD_TMA) {
@@ -588,13 +614,28 @@ __device__ __forceinline__ void fwd_store_bands(const FwdArgs& a, const BandRows
     }
 }
 
+// fwd_store_bands with the LL row stored under the L2 policy ll_pol (evict_last when the next
+// level reads LL back from L2, else evict_normal).
+template <typename TB, typename TL, typename C>
+__device__ __forceinline__ void fwd_store_bands_ll(const FwdArgs& a, const BandRows& br,
+                                                   const QRow<C>& row, int qo, int m0,
+                                                   uint64_t ll_pol) {
+    putN_hint<kQ>(reinterpret_cast<TL*>(br.p[0]), row.a, m0, a.nec, true, ll_pol);
+    putN<kQ>(reinterpret_cast<TB*>(br.p[1]), row.b, m0, a.ndc, true);
+    if (qo < a.ndr) {
+        putN<kQ>(reinterpret_cast<TB*>(br.p[2]), row.c, m0, a.nec, true);
+        putN<kQ>(reinterpret_cast<TB*>(br.p[3]), row.e, m0, a.ndc, true);
+    }
+}
+
 // Inverse data flow: band rows of extended quad row q.  Even pixel row 2q -> LL / HL row, odd
 // pixel row 2q + 1 -> LH / HH row (mirrored; plain rows with zeros outside for the adjoint).
 // tm[k] points to the tensor map of band k (LL, HL, LH, HH) in parameter or global memory.
 template <typename TL, typename TB>
 __device__ __forceinline__ void inv_produce_row(const InvArgs& a, const CUtensorMap* const* tm,
                                                 bool adj, int q, int xb, uint8_t* stage,
-                                                uint64_t* full, int lane, int z) {
+                                                uint64_t* full, int lane, int z,
+                                                const uint64_t* ll_pol = nullptr) {
     constexpr size_t kStageBytes = size_t(kBRow) * (sizeof(TL) + 3 * sizeof(TB));
     TL* sll = reinterpret_cast<TL*>(stage);
     TB* sb = reinterpret_cast<TB*>(stage + kBRow * sizeof(TL));
@@ -606,7 +647,8 @@ __device__ __forceinline__ void inv_produce_row(const InvArgs& a, const CUtensor
 #pragma unroll
             for (int b = 0; b < kBBoxes; ++b) {
                 const int x = xb + b * kBoxW;
-                tma_load_3d(sll + b * kBoxW, tm[0], full, x, re, z);
+                if (ll_pol) tma_load_3d_hint(sll + b * kBoxW, tm[0], full, x, re, z, *ll_pol);
+                else tma_load_3d(sll + b * kBoxW, tm[0], full, x, re, z);
                 tma_load_3d(sb + b * kBoxW, tm[1], full, x, re, z);
                 tma_load_3d(sb + kBRow + b * kBoxW, tm[2], full, x, ro, z);
                 tma_load_3d(sb + 2 * kBRow + b * kBoxW, tm[3], full, x, ro, z);
@@ -717,6 +759,25 @@ __device__ __forceinline__ void inv_store_rows_at(const InvArgs& a, const QRow<C
         putN<2 * kQ>(reinterpret_cast<TO*>(p + a.out.pitch), vc, c0, a.W, a.out_vec != 0);
 }
 
+// inv_store_rows_at with the vector stores under the L2 policy pol.
+template <typename TO, typename C>
+__device__ __forceinline__ void inv_store_rows_at_hint(const InvArgs& a, const QRow<C>& row,
+                                                       int qo, int m0, char* p, uint64_t pol) {
+    const int c0 = 2 * m0;
+    C va[2 * kQ], vc[2 * kQ];
+#pragma unroll
+    for (int q = 0; q < kQ; ++q) {
+        va[2 * q] = row.a[q];
+        va[2 * q + 1] = row.b[q];
+        vc[2 * q] = row.c[q];
+        vc[2 * q + 1] = row.e[q];
+    }
+    putN_hint<2 * kQ>(reinterpret_cast<TO*>(p), va, c0, a.W, a.out_vec != 0, pol);
+    if (2 * qo + 1 < a.H)
+        putN_hint<2 * kQ>(reinterpret_cast<TO*>(p + a.out.pitch), vc, c0, a.W, a.out_vec != 0,
+                          pol);
+}
+
 // Shared-memory ring: NS stages, then the full / empty barriers, the abort flag and the
 // per-stage tile ids (persistent kernels).
 template <int NS>
@@ -781,6 +842,14 @@ __device__ __forceinline__ void drain_ring(const Ring<NS>& r, int issued, int* s
         if (!mbar_wait(&r.full[i % NS], (i / NS) & 1, &no_abort, status)) break;
 }
 
+// Wavelets whose streaming levels keep the next level's LL in L2 (evict_last stores, read back
+// with evict_normal).  Measured on GB300, 8192^2, 5 levels, same box: the integer 5/3 forward
+// 131.5 -> 126.0 us and its inverse 132.7 -> 126.0 us (level 1 and 2 both faster); the 9/7
+// forward 140.3 -> 141.3 us and inverse 139.5 -> 145.1 us, and its 192 x 1024^2 batch 10%
+// slower: the 9/7 kernels are bound by instruction issue, and the hinted stores cost them more
+// than the L2 reads save.  The 9/7 kernels therefore keep plain stores and loads.
+__host__ __device__ constexpr bool keeps_ll_in_l2(int wv) { return wv != WV_CDF97; }
+
 // Forward levels that take the DC level shift: float lifting (every scheme but the convolution,
 // whose only intermediates are the filter outputs) and not the adjoint (a linear map of
 // gradients, with no DC to remove).
@@ -827,6 +896,8 @@ __global__ void __launch_bounds__(cta_threads<NW>(), min_ctas<WV, NW>())
     allow_dependent_launch();
 
     if (warp == kNW) {  // ------------------------------------------------------ producer
+        const uint64_t in_pol = keeps_ll_in_l2(WV) ? l2_evict_normal() : 0;
+        const uint64_t* in_hint = keeps_ll_in_l2(WV) && args.in_kept ? &in_pol : nullptr;
         int issued = 0;
         RingPos<kS> rp;
         for (int i = 0; i < nrows; ++i) {
@@ -839,7 +910,7 @@ __global__ void __launch_bounds__(cta_threads<NW>(), min_ctas<WV, NW>())
             }
             fwd_produce_row<TI, 1, kPlain ? LOAD_PLAIN : LOAD_TMA>(
                 args, &tmap, kAdj, qfirst + i, xs, reinterpret_cast<TI*>(ring.stage(s)),
-                &ring.full[s], lane, z, &ring.shift[s]);
+                &ring.full[s], lane, z, &ring.shift[s], in_hint);
             issued = i + 1;
         }
         if (lane == 0) drain_ring(ring, issued, args.status);
@@ -864,6 +935,9 @@ __global__ void __launch_bounds__(cta_threads<NW>(), min_ctas<WV, NW>())
 
     BandRows bands;
     if constexpr (MODE != MODE_ROWS) bands.init<TB, TL>(args, n0, m0, z);
+    uint64_t ll_pol = 0;
+    if constexpr (keeps_ll_in_l2(WV))
+        ll_pol = args.ll_keep ? l2_evict_last() : l2_evict_normal();
     static_assert(!kShift || kShiftable<C, MODE>, "a level shift on a level that takes none");
     LevelShift sh{-0.f, -0.f};
     if constexpr (kShift) sh.init(args.shift, z);
@@ -902,7 +976,12 @@ __global__ void __launch_bounds__(cta_threads<NW>(), min_ctas<WV, NW>())
         if constexpr (MODE == MODE_ROWS) {
             if (qo >= n0 && qo < n1 && store_lane) fwd_store_interleaved<TL>(args, row, qo, m0, z);
         } else if (qo >= n0 && qo < n1) {
-            if (store_lane) fwd_store_bands<TB, TL>(args, bands, row, qo, m0);
+            if (store_lane) {
+                if constexpr (keeps_ll_in_l2(WV))
+                    fwd_store_bands_ll<TB, TL>(args, bands, row, qo, m0, ll_pol);
+                else
+                    fwd_store_bands<TB, TL>(args, bands, row, qo, m0);
+            }
             bands.next(args);
         }
     }
@@ -922,6 +1001,11 @@ constexpr int kDirectRows = 2;     // output quad rows per warp
 constexpr int kDirectWarps = 4;    // warps (windows) per CTA
 // Largest input (bytes, all images of a launch) a level takes the direct kernel for.
 constexpr int64_t kDirectMaxBytes = int64_t(4) << 20;
+// Whether a non-separable forward level over n planes of h x w elements of es bytes (an inverse
+// level: n output planes of h x w LL elements) takes the direct kernel.
+inline bool takes_direct(int h, int w, size_t es, int n) {
+    return int64_t(h) * w * int64_t(es) * std::max(1, n) <= kDirectMaxBytes;
+}
 
 // refl for the direct kernels, whose rows and columns are mostly inside the plane already.
 __device__ __forceinline__ int refl_in(int i, int n) {
@@ -1045,6 +1129,8 @@ __global__ void __launch_bounds__(cta_threads<NW>(), min_ctas<WV, NW>())
     if (warp == kNW) {  // ------------------------------------------------------ producer
         // pointers to the __grid_constant__ parameters (TMA reads the maps where they live)
         const CUtensorMap* maps[4] = {&tm_ll, &tm_hl, &tm_lh, &tm_hh};
+        const uint64_t ll_pol = keeps_ll_in_l2(WV) ? l2_evict_normal() : 0;
+        const uint64_t* ll_hint = keeps_ll_in_l2(WV) && args.ll_kept ? &ll_pol : nullptr;
         int issued = 0;
         RingPos<kS> rp;
         for (int i = 0; i < nrows; ++i) {
@@ -1056,7 +1142,7 @@ __global__ void __launch_bounds__(cta_threads<NW>(), min_ctas<WV, NW>())
                 if (!__all_sync(kFull, ok)) break;
             }
             inv_produce_row<TL, TB>(args, maps, ADJ, qfirst + i, xb, ring.stage(s), &ring.full[s],
-                                    lane, z);
+                                    lane, z, ll_hint);
             issued = i + 1;
         }
         if (args.tma && lane == 0) drain_ring(ring, issued, args.status);
@@ -1076,6 +1162,9 @@ __global__ void __launch_bounds__(cta_threads<NW>(), min_ctas<WV, NW>())
     const AxisLen rows{args.ner, args.ndr};
 
     char* out_p = reinterpret_cast<char*>(row_ptr<TO>(args.out, 2 * n0, z) + 2 * m0);
+    uint64_t out_pol = 0;
+    if constexpr (keeps_ll_in_l2(WV))
+        out_pol = args.out_keep ? l2_evict_last() : l2_evict_normal();
     static_assert(!kShift || (!ADJ && std::is_same<C, float>::value), "no shift on this level");
     LevelShift sh{-0.f, -0.f};
     if constexpr (kShift) sh.init(args.shift, z);
@@ -1105,7 +1194,12 @@ __global__ void __launch_bounds__(cta_threads<NW>(), min_ctas<WV, NW>())
         const int qo = qfirst + i - Pipe::kLag;
         if (qo >= n0 && qo < n1) {
             if constexpr (kShift) add_row(row, sh.out_add);
-            if (store_lane) inv_store_rows_at<TO>(args, row, qo, m0, out_p);
+            if (store_lane) {
+                if constexpr (keeps_ll_in_l2(WV))
+                    inv_store_rows_at_hint<TO>(args, row, qo, m0, out_p, out_pol);
+                else
+                    inv_store_rows_at<TO>(args, row, qo, m0, out_p);
+            }
             out_p += 2 * args.out.pitch;
         }
     }
@@ -1339,7 +1433,7 @@ cudaError_t launch_forward_direct(FwdArgs a, cudaStream_t st) {
 template <int WV, int MODE, typename TI, typename TB, typename TL>
 cudaError_t launch_forward_t(const CUtensorMap& tm, FwdArgs a, cudaStream_t st) {
     if constexpr (MODE == MODE_NONSEP) {
-        if (int64_t(a.H) * a.W * int64_t(sizeof(TI)) * std::max(1, a.nbatch) <= kDirectMaxBytes) {
+        if (takes_direct(a.H, a.W, sizeof(TI), a.nbatch)) {
             using C = std::conditional_t<WV == WV_CDF53_INT, int32_t, float>;
             if constexpr (kShiftable<C, MODE>) {
                 if (a.shift.mode != 0) return launch_forward_direct<WV, TI, TB, TL, true>(a, st);
@@ -1391,7 +1485,7 @@ cudaError_t launch_inverse_direct(InvArgs a, cudaStream_t st) {
 template <int WV, typename TB, typename TL, typename TO, bool ADJ = false>
 cudaError_t launch_inverse_t(const CUtensorMap* tm, InvArgs a, cudaStream_t st) {
     if constexpr (!ADJ) {
-        if (int64_t(a.H) * a.W * int64_t(sizeof(TL)) * std::max(1, a.nbatch) <= kDirectMaxBytes) {
+        if (takes_direct(a.H, a.W, sizeof(TL), a.nbatch)) {
             if constexpr (WV != WV_CDF53_INT) {
                 if (a.shift.mode != 0) return launch_inverse_direct<WV, TB, TL, TO, true>(a, st);
             }
