@@ -329,6 +329,45 @@ def run_only(args, D, dev, x_f32, x_i32, flush, stream):
                       "status": D.check_status(ws)}), flush=True)
 
 
+def run_levels_table(args, D, dev, x_f32, x_i32, flush, stream):
+    """Per-level times of the 8192 x 8192 forward and inverse transforms: the median of K calls
+    of the J-level transform for J = 1 .. LEVELS, L2 flushed before each call; level j's time is
+    the J = j median minus the J = j - 1 one (PDL lets a level overlap the previous one's tail,
+    so a level's share is what adding it costs the transform)."""
+    def med(fn):
+        for _ in range(args.warmup):
+            fn()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(args.steps)]
+        for s0, e0 in evs:
+            flush()
+            s0.record(stream)
+            fn()
+            e0.record(stream)
+        torch.cuda.synchronize()
+        return 1e3 * float(np.median([a.elapsed_time(b) for a, b in evs]))  # us
+
+    report = {}
+    for wv, x in (("cdf97", x_f32), ("cdf53_int", x_i32), ("cdf53", x_f32)):
+        bdt = D.TORCH_DT[x.dtype]
+        out = torch.empty_like(x)
+        fwd, inv = [], []
+        for lv in range(1, LEVELS + 1):
+            c = D.alloc_coeffs(H, W, lv, wv, bdt, dev)
+            ws = D.new_workspace(D.workspace_bytes(H, W, lv, wv, bdt), dev)
+            fwd.append(med(lambda: D.forward(x, wv, lv, out=c, workspace=ws)))
+            inv.append(med(lambda: D.inverse(c, out=out, workspace=ws)))
+            del c, ws
+        per = lambda t: [round(t[0], 1)] + [round(t[k] - t[k - 1], 1) for k in range(1, len(t))]
+        report[wv] = {"forward_level_us": per(fwd), "forward_total_us": round(fwd[-1], 1),
+                      "inverse_level_us": per(inv), "inverse_total_us": round(inv[-1], 1),
+                      "level_bytes": [2 * x.element_size() * (H >> j) * (W >> j)
+                                      for j in range(LEVELS)]}
+    print(json.dumps({"levels_table": f"{H}x{W}, 1..{LEVELS} levels, median of {args.steps} "
+                                      "calls per transform, L2 flushed before each",
+                      "report": report}), flush=True)
+
+
 def storage_bytes(h: int, w: int, levels: int, in_es: int, band_es: int, ll_es: int = 4) -> int:
     """Algorithmic bytes of a forward with band storage band_es: per level one read of the
     input plane and one write of the four bands (LL planes fp32)."""
@@ -545,6 +584,8 @@ def main():
                              "inv_cdf53_int", "twopass_cdf97", "sepfused_cdf97", "adapted_cdf97",
                              "conv_cdf97", "plan_cdf97", "plan_cdf53_int"],
                     help="run one case only (for profiler captures); prints a short line")
+    ap.add_argument("--levels-table", action="store_true",
+                    help="8192x8192: per-level forward and inverse times of each wavelet")
     ap.add_argument("--levels", type=int, default=0,
                     help="with --only: decomposition levels instead of the case's own")
     args = ap.parse_args()
@@ -590,6 +631,8 @@ def main():
 
     if args.only:
         return run_only(args, D, dev, x_f32, x_i32, flush, stream)
+    if args.levels_table:
+        return run_levels_table(args, D, dev, x_f32, x_i32, flush, stream)
 
     def run_case(fn, steps, warmup):
         """Median CUDA-event time (ms) of `steps` calls, L2 flushed before each."""
