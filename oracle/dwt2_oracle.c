@@ -33,6 +33,14 @@
  *            factorisation of Eq. 2), followed by scaling low-pass by 1/K and high-pass by K/2,
  *            which gives the low-pass a DC gain of 1 and the high-pass a Nyquist gain of 1.
  *   Reversible CDF 5/3: d = x_o - floor((x_e + x_e') / 2), s = x_e + floor((d' + d + 2) / 4).
+ *   Deslauriers-Dubuc 9/7 and 13/7 (interpolating wavelets, no scaling): the predict is the
+ *            cubic interpolation of the odd sample from its four even neighbours,
+ *            d[m] = x[2m+1] - (9/16 (s[m] + s[m+1]) - 1/16 (s[m-1] + s[m+2])), so the high
+ *            pass vanishes on cubics; the update is half the predict's transpose,
+ *            s[m] += 1/4 (d[m-1] + d[m]) for 9/7 (two vanishing moments of the low pass at
+ *            Nyquist) and s[m] += 9/32 (d[m-1] + d[m]) - 1/32 (d[m-2] + d[m+1]) for 13/7 (four).
+ *            Each step has an inner tap pair (distance 1 in the interleaved signal) and an outer
+ *            one (distance 3); the CDF wavelets have no outer pair.
  * ---------------------------------------------------------------------------------------- */
 static const double C53_P = -0.5;
 static const double C53_U = 0.25;
@@ -44,10 +52,12 @@ static const double C97_K = 1.230174104914001;
 
 typedef struct {
     int npairs;
-    double p[2], u[2];
+    double p[2], u[2];   /* inner tap pair of each predict / update */
+    double p3[2], u3[2]; /* outer tap pair (0 for the CDF wavelets) */
 } lifting_t;
 
 static int get_lifting(int wavelet, lifting_t* L) {
+    L->p3[0] = L->p3[1] = L->u3[0] = L->u3[1] = 0.0;
     switch (wavelet) {
     case ORC_CDF53_INT: /* coefficients only used for their structure; arithmetic is integer */
     case ORC_CDF53:
@@ -61,6 +71,14 @@ static int get_lifting(int wavelet, lifting_t* L) {
         L->u[0] = C97_BETA;
         L->p[1] = C97_GAMMA;
         L->u[1] = C97_DELTA;
+        return 0;
+    case ORC_DD97:
+    case ORC_DD137:
+        L->npairs = 1;
+        L->p[0] = -9.0 / 16.0;
+        L->p3[0] = 1.0 / 16.0;
+        L->u[0] = wavelet == ORC_DD97 ? 0.25 : 9.0 / 32.0;
+        L->u3[0] = wavelet == ORC_DD97 ? 0.0 : -1.0 / 32.0;
         return 0;
     default:
         return -1;
@@ -108,14 +126,23 @@ static long refl_any(long i, long n) {
  *             that has already been extended far enough).
  * A line of length 1 has no odd sample and passes through.
  * ---------------------------------------------------------------------------------------- */
-static void line_step_f(double* v, long n, long s, int parity, double coef, int mirror) {
+static void line_step_f(double* v, long n, long s, int parity, double coef, double coef3,
+                        int mirror) {
     if (n < 2) return;
     for (long i = parity; i < n; i += 2) {
         long l = i - 1, r = i + 1;
-        if (!mirror && (l < 0 || r >= n)) continue;
-        l = refl1(l, n);
-        r = refl1(r, n);
-        v[i * s] += coef * (v[l * s] + v[r * s]);
+        if (coef3 == 0.0) {
+            if (!mirror && (l < 0 || r >= n)) continue;
+            l = refl1(l, n);
+            r = refl1(r, n);
+            v[i * s] += coef * (v[l * s] + v[r * s]);
+        } else {
+            /* the outer pair at distance 3 (Deslauriers-Dubuc): reflections of any depth */
+            long l3 = i - 3, r3 = i + 3;
+            if (!mirror && (l3 < 0 || r3 >= n)) continue;
+            v[i * s] += coef * (v[refl_any(l, n) * s] + v[refl_any(r, n) * s]) +
+                        coef3 * (v[refl_any(l3, n) * s] + v[refl_any(r3, n) * s]);
+        }
     }
 }
 
@@ -153,13 +180,14 @@ static void line_step_adj_f(double* g, long n, long s, int parity, double coef) 
  * is still computed by one thread in the same order, so the results do not depend on it. */
 enum { AX_ROWS = 0, AX_COLS = 1 };
 
-static void plane_step_f(double* x, long H, long W, int axis, int parity, double coef, int mirror) {
+static void plane_step_f(double* x, long H, long W, int axis, int parity, double coef,
+                         double coef3, int mirror) {
     if (axis == AX_ROWS) {
 #pragma omp parallel for schedule(static)
-        for (long r = 0; r < H; ++r) line_step_f(x + r * W, W, 1, parity, coef, mirror);
+        for (long r = 0; r < H; ++r) line_step_f(x + r * W, W, 1, parity, coef, coef3, mirror);
     } else {
 #pragma omp parallel for schedule(static)
-        for (long c = 0; c < W; ++c) line_step_f(x + c, H, W, parity, coef, mirror);
+        for (long c = 0; c < W; ++c) line_step_f(x + c, H, W, parity, coef, coef3, mirror);
     }
 }
 
@@ -192,7 +220,7 @@ static void plane_step_adj_f(double* g, long H, long W, int axis, int parity, do
  * ---------------------------------------------------------------------------------------- */
 typedef struct {
     int axis, parity;
-    double coef;
+    double coef, coef3; /* inner and outer tap pair */
 } step2d_t;
 
 static int level_steps(int wavelet, int scheme, step2d_t* st) {
@@ -201,18 +229,18 @@ static int level_steps(int wavelet, int scheme, step2d_t* st) {
     int n = 0;
     if (scheme == ORC_SEP_EQ3) {
         for (int k = 0; k < L.npairs; ++k) {
-            st[n++] = (step2d_t){AX_ROWS, 1, L.p[k]};
-            st[n++] = (step2d_t){AX_COLS, 1, L.p[k]};
-            st[n++] = (step2d_t){AX_ROWS, 0, L.u[k]};
-            st[n++] = (step2d_t){AX_COLS, 0, L.u[k]};
+            st[n++] = (step2d_t){AX_ROWS, 1, L.p[k], L.p3[k]};
+            st[n++] = (step2d_t){AX_COLS, 1, L.p[k], L.p3[k]};
+            st[n++] = (step2d_t){AX_ROWS, 0, L.u[k], L.u3[k]};
+            st[n++] = (step2d_t){AX_COLS, 0, L.u[k], L.u3[k]};
         }
     } else if (scheme == ORC_SEP_ROWS || scheme == ORC_SEP_COLS) {
         int first = scheme == ORC_SEP_ROWS ? AX_ROWS : AX_COLS;
         for (int pass = 0; pass < 2; ++pass) {
             int axis = pass == 0 ? first : 1 - first;
             for (int k = 0; k < L.npairs; ++k) {
-                st[n++] = (step2d_t){axis, 1, L.p[k]};
-                st[n++] = (step2d_t){axis, 0, L.u[k]};
+                st[n++] = (step2d_t){axis, 1, L.p[k], L.p3[k]};
+                st[n++] = (step2d_t){axis, 0, L.u[k], L.u3[k]};
             }
         }
     } else {
@@ -294,7 +322,8 @@ static void join_i(const int64_t* LL, const int64_t* HL, const int64_t* LH, cons
  * Separable level, forward (Eq. 3), in place on an interleaved h x w plane.
  * extension_form = 1: extend by 8 samples of whole-sample symmetric extension on each side of
  * every axis longer than 1 (8 is even, so sample parity is kept, and exceeds the reach of the
- * longest wavelet, 4 samples), lift with no boundary rule, crop.
+ * longest wavelet: 4 samples for CDF 9/7, 6 for Deslauriers-Dubuc 13/7), lift with no boundary
+ * rule, crop.
  * ---------------------------------------------------------------------------------------- */
 #define EXT 8
 
@@ -304,7 +333,7 @@ static int sep_level_fwd_f(double* x, long h, long w, int wavelet, int scheme, i
     if (ns < 0) return -1;
     if (!ext) {
         for (int k = 0; k < ns; ++k)
-            plane_step_f(x, h, w, st[k].axis, st[k].parity, st[k].coef, 1);
+            plane_step_f(x, h, w, st[k].axis, st[k].parity, st[k].coef, st[k].coef3, 1);
         return 0;
     }
     long eh = h > 1 ? EXT : 0, ew = w > 1 ? EXT : 0;
@@ -315,7 +344,7 @@ static int sep_level_fwd_f(double* x, long h, long w, int wavelet, int scheme, i
         for (long c = 0; c < W2; ++c)
             y[r * W2 + c] = x[refl_any(r - eh, h) * w + refl_any(c - ew, w)];
     for (int k = 0; k < ns; ++k)
-        plane_step_f(y, H2, W2, st[k].axis, st[k].parity, st[k].coef, 0);
+        plane_step_f(y, H2, W2, st[k].axis, st[k].parity, st[k].coef, st[k].coef3, 0);
     for (long r = 0; r < h; ++r)
         for (long c = 0; c < w; ++c) x[r * w + c] = y[(r + eh) * W2 + (c + ew)];
     free(y);
@@ -350,7 +379,7 @@ static int sep_level_inv_f(double* x, long h, long w, int wavelet, int scheme) {
     int ns = level_steps(wavelet, scheme, st);
     if (ns < 0) return -1;
     for (int k = ns - 1; k >= 0; --k)
-        plane_step_f(x, h, w, st[k].axis, st[k].parity, -st[k].coef, 1);
+        plane_step_f(x, h, w, st[k].axis, st[k].parity, -st[k].coef, -st[k].coef3, 1);
     return 0;
 }
 
@@ -624,6 +653,113 @@ static void scale_quad_f(quad_f_t* q, long h, long w, int wavelet, int divide) {
 }
 
 /* ------------------------------------------------------------------------------------------
+ * The spatial steps of Eq. 5 for lifting steps with more taps (the Deslauriers-Dubuc wavelets):
+ * the same matrices, with P, P*, U, U* and the products PP*, UU* written as tap lists.  P reads
+ * the even samples m + off of an odd sample m (offsets 0, +1 and, with the outer pair, -1, +2);
+ * U reads the odd samples m + off of an even sample m (offsets -1, 0 and -2, +1).  The
+ * whole-sample extension of an axis of length len, stated on band indices: even position 2k
+ * is band index refl(2k) / 2, odd position 2k + 1 is (refl(2k + 1) - 1) / 2.  sign = -1 undoes
+ * the step (the same matrix entries with the off-diagonal blocks negated and the product
+ * term kept, as in the two-tap inverses above).
+ * ---------------------------------------------------------------------------------------- */
+typedef struct {
+    int n;
+    long off[4];
+    double c[4];
+} taps_t;
+
+static taps_t predict_taps(double p, double p3) {
+    taps_t t = {2, {0, 1, 0, 0}, {p, p, 0.0, 0.0}};
+    if (p3 != 0.0) {
+        t.n = 4;
+        t.off[2] = -1;
+        t.off[3] = 2;
+        t.c[2] = t.c[3] = p3;
+    }
+    return t;
+}
+
+static taps_t update_taps(double u, double u3) {
+    taps_t t = {2, {-1, 0, 0, 0}, {u, u, 0.0, 0.0}};
+    if (u3 != 0.0) {
+        t.n = 4;
+        t.off[2] = -2;
+        t.off[3] = 1;
+        t.c[2] = t.c[3] = u3;
+    }
+    return t;
+}
+
+static long ev_(long k, long len) { return refl_any(2 * k, len) / 2; }
+static long od_(long k, long len) { return (refl_any(2 * k + 1, len) - 1) / 2; }
+
+static void nonsep_predict_taps_f(quad_f_t* q, taps_t P, double sign) {
+    geom_t g = q->g;
+    long h = g.ner + g.ndr, w = g.nec + g.ndc;
+    quad_f_t o = {g, dup_f(q->a, g.ner * g.nec), dup_f(q->b, g.ner * g.ndc),
+                  dup_f(q->c, g.ndr * g.nec), dup_f(q->e, g.ndr * g.ndc)};
+    for (long n = 0; n < g.ner; ++n)
+        for (long m = 0; m < g.ndc; ++m) {
+            double v = 0.0;
+            for (int k = 0; k < P.n; ++k) v += P.c[k] * A_(&o, n, ev_(m + P.off[k], w));
+            B_(q, n, m) = B_(&o, n, m) + sign * v;
+        }
+    for (long n = 0; n < g.ndr; ++n)
+        for (long m = 0; m < g.nec; ++m) {
+            double v = 0.0;
+            for (int k = 0; k < P.n; ++k) v += P.c[k] * A_(&o, ev_(n + P.off[k], h), m);
+            C_(q, n, m) = C_(&o, n, m) + sign * v;
+        }
+    for (long n = 0; n < g.ndr; ++n)
+        for (long m = 0; m < g.ndc; ++m) {
+            double vh = 0.0, vv = 0.0, va = 0.0;
+            for (int k = 0; k < P.n; ++k) {
+                vh += P.c[k] * C_(&o, n, ev_(m + P.off[k], w)); /* P  (LH) */
+                vv += P.c[k] * B_(&o, ev_(n + P.off[k], h), m); /* P* (HL) */
+                for (int l = 0; l < P.n; ++l)                    /* P* P (LL) */
+                    va += P.c[k] * P.c[l] * A_(&o, ev_(n + P.off[k], h), ev_(m + P.off[l], w));
+            }
+            E_(q, n, m) = E_(&o, n, m) + sign * (vh + vv) + va;
+        }
+    free(o.a); free(o.b); free(o.c); free(o.e);
+}
+
+static void nonsep_update_taps_f(quad_f_t* q, taps_t U, double sign) {
+    geom_t g = q->g;
+    long h = g.ner + g.ndr, w = g.nec + g.ndc;
+    quad_f_t o = {g, dup_f(q->a, g.ner * g.nec), dup_f(q->b, g.ner * g.ndc),
+                  dup_f(q->c, g.ndr * g.nec), dup_f(q->e, g.ndr * g.ndc)};
+    for (long n = 0; n < g.ner; ++n)
+        for (long m = 0; m < g.nec; ++m) {
+            double vh = 0.0, vv = 0.0, va = 0.0;
+            for (int k = 0; k < U.n; ++k) {
+                if (g.ndc) vh += U.c[k] * B_(&o, n, od_(m + U.off[k], w)); /* U  (HL) */
+                if (g.ndr) vv += U.c[k] * C_(&o, od_(n + U.off[k], h), m); /* U* (LH) */
+                if (g.ndr && g.ndc)                                         /* U* U (HH) */
+                    for (int l = 0; l < U.n; ++l)
+                        va += U.c[k] * U.c[l] *
+                              E_(&o, od_(n + U.off[k], h), od_(m + U.off[l], w));
+            }
+            A_(q, n, m) = A_(&o, n, m) + sign * (vh + vv) + va;
+        }
+    if (g.ndr)
+        for (long n = 0; n < g.ner; ++n)
+            for (long m = 0; m < g.ndc; ++m) {
+                double v = 0.0;
+                for (int k = 0; k < U.n; ++k) v += U.c[k] * E_(&o, od_(n + U.off[k], h), m);
+                B_(q, n, m) = B_(&o, n, m) + sign * v;
+            }
+    if (g.ndc)
+        for (long n = 0; n < g.ndr; ++n)
+            for (long m = 0; m < g.nec; ++m) {
+                double v = 0.0;
+                for (int k = 0; k < U.n; ++k) v += U.c[k] * E_(&o, n, od_(m + U.off[k], w));
+                C_(q, n, m) = C_(&o, n, m) + sign * v;
+            }
+    free(o.a); free(o.b); free(o.c); free(o.e);
+}
+
+/* ------------------------------------------------------------------------------------------
  * Adapted non-separable scheme (Sec. 3, Fig. 3).  With P = P0 + P1, P0 = p (the constant
  * monomial) and P1 = p z, the spatial predict matrix of Eq. 5 factors as
  * M_P(P) = M_P(P1) M_P(P0): every factor is one of the commuting 1-D steps d += P0 s,
@@ -748,8 +884,13 @@ static int level_fwd_f(const double* x, long h, long w, int wavelet, int scheme,
         quad_f_t q = {geom_of(h, w), LL, HL, LH, HH};
         split_f(x, h, w, ORC_CDF53, LL, HL, LH, HH); /* plain split, no scaling */
         for (int k = 0; k < L.npairs; ++k) {
-            nonsep_predict_f(&q, L.p[k]);
-            nonsep_update_f(&q, L.u[k]);
+            if (L.p3[k] != 0.0 || L.u3[k] != 0.0) {
+                nonsep_predict_taps_f(&q, predict_taps(L.p[k], L.p3[k]), 1.0);
+                nonsep_update_taps_f(&q, update_taps(L.u[k], L.u3[k]), 1.0);
+            } else {
+                nonsep_predict_f(&q, L.p[k]);
+                nonsep_update_f(&q, L.u[k]);
+            }
         }
         scale_quad_f(&q, h, w, wavelet, 0);
         return 0;
@@ -789,8 +930,13 @@ static int level_inv_f(const double* LL, const double* HL, const double* LH, con
                       dup_f(LH, g.ndr * g.nec), dup_f(HH, g.ndr * g.ndc)};
         scale_quad_f(&q, h, w, wavelet, 1);
         for (int k = L.npairs - 1; k >= 0; --k) {
-            nonsep_update_inv_f(&q, L.u[k]);
-            nonsep_predict_inv_f(&q, L.p[k]);
+            if (L.p3[k] != 0.0 || L.u3[k] != 0.0) {
+                nonsep_update_taps_f(&q, update_taps(L.u[k], L.u3[k]), -1.0);
+                nonsep_predict_taps_f(&q, predict_taps(L.p[k], L.p3[k]), -1.0);
+            } else {
+                nonsep_update_inv_f(&q, L.u[k]);
+                nonsep_predict_inv_f(&q, L.p[k]);
+            }
         }
         join_f(q.a, q.b, q.c, q.e, h, w, ORC_CDF53, 0, x);
         free(q.a); free(q.b); free(q.c); free(q.e);
@@ -920,9 +1066,13 @@ int64_t orc_coeff_count(int H, int W, int levels) {
 }
 
 static int valid_scheme(int wavelet, int scheme) {
-    if (wavelet < ORC_CDF53_INT || wavelet > ORC_CDF97) return 0;
+    if (wavelet < ORC_CDF53_INT || wavelet > ORC_DD137) return 0;
     return scheme >= ORC_SEP_EQ3 && scheme <= ORC_NONSEP_EQ5;
 }
+
+/* The adjoints, the adapted scheme and the step-by-step entry points are stated for the CDF
+ * wavelets (two-tap steps). */
+static int is_cdf(int wavelet) { return wavelet >= ORC_CDF53_INT && wavelet <= ORC_CDF97; }
 
 /* The adapted scheme is defined for the float wavelets' forward transform (its constant /
  * neighbour split of a floor term would change the integer result). */
@@ -1011,7 +1161,7 @@ int orc_inverse(const void* coeffs, int H, int W, int wavelet, int levels, int s
 int orc_forward_adjoint(const double* g_coeffs, int H, int W, int wavelet, int levels,
                         double* g_img) {
     layout_t Lo;
-    if (!g_coeffs || !g_img || wavelet == ORC_CDF53_INT || !valid_scheme(wavelet, 0) ||
+    if (!g_coeffs || !g_img || wavelet == ORC_CDF53_INT || !is_cdf(wavelet) ||
         make_layout(H, W, levels, &Lo))
         return -1;
     double* cur = dup_f(g_coeffs + Lo.off_ll, Lo.h[levels] * Lo.w[levels]);
@@ -1033,7 +1183,7 @@ int orc_forward_adjoint(const double* g_coeffs, int H, int W, int wavelet, int l
 int orc_inverse_adjoint(const double* g_img, int H, int W, int wavelet, int levels,
                         double* g_coeffs) {
     layout_t Lo;
-    if (!g_coeffs || !g_img || wavelet == ORC_CDF53_INT || !valid_scheme(wavelet, 0) ||
+    if (!g_coeffs || !g_img || wavelet == ORC_CDF53_INT || !is_cdf(wavelet) ||
         make_layout(H, W, levels, &Lo))
         return -1;
     double* cur = dup_f(g_img, (long)H * W);
@@ -1053,7 +1203,8 @@ int orc_inverse_adjoint(const double* g_img, int H, int W, int wavelet, int leve
 
 int orc_nonsep_steps(const double* img, int H, int W, int wavelet, int nsteps, double* out) {
     lifting_t L;
-    if (!img || !out || H < 1 || W < 1 || wavelet == ORC_CDF53_INT || get_lifting(wavelet, &L) ||
+    if (!img || !out || H < 1 || W < 1 || wavelet == ORC_CDF53_INT || !is_cdf(wavelet) ||
+        get_lifting(wavelet, &L) ||
         nsteps < 0 || nsteps > 2 * L.npairs)
         return -1;
     geom_t g = geom_of(H, W);
@@ -1072,7 +1223,8 @@ int orc_nonsep_steps(const double* img, int H, int W, int wavelet, int nsteps, d
 
 int orc_adapted_steps(const double* img, int H, int W, int wavelet, int nsteps, double* out) {
     lifting_t L;
-    if (!img || !out || H < 1 || W < 1 || wavelet == ORC_CDF53_INT || get_lifting(wavelet, &L) ||
+    if (!img || !out || H < 1 || W < 1 || wavelet == ORC_CDF53_INT || !is_cdf(wavelet) ||
+        get_lifting(wavelet, &L) ||
         nsteps < 0 || nsteps > 4 * L.npairs)
         return -1;
     geom_t g = geom_of(H, W);
@@ -1088,7 +1240,8 @@ int orc_adapted_steps(const double* img, int H, int W, int wavelet, int nsteps, 
 
 int orc_adapted_apply(double* abce, int H, int W, int wavelet, int k0, int k1) {
     lifting_t L;
-    if (!abce || H < 1 || W < 1 || wavelet == ORC_CDF53_INT || get_lifting(wavelet, &L) ||
+    if (!abce || H < 1 || W < 1 || wavelet == ORC_CDF53_INT || !is_cdf(wavelet) ||
+        get_lifting(wavelet, &L) ||
         k0 < 0 || k1 < k0 || k1 > 4 * L.npairs)
         return -1;
     geom_t g = geom_of(H, W);

@@ -17,7 +17,12 @@
  *     an axis of length 1 passes through unchanged.
  *
  * Wavelets: ORC_CDF53_INT (reversible integer CDF 5/3, exact int64, floor division),
- *           ORC_CDF53     (CDF 5/3 in fp64), ORC_CDF97 (CDF 9/7 in fp64).
+ *           ORC_CDF53     (CDF 5/3 in fp64), ORC_CDF97 (CDF 9/7 in fp64),
+ *           ORC_DD97, ORC_DD137 (Deslauriers-Dubuc 9/7 and 13/7 in fp64: four-tap predict,
+ *           two- or four-tap update, no scaling).  The Deslauriers-Dubuc wavelets have the
+ *           forward and inverse transforms of the separable and non-separable schemes; the
+ *           adjoints, the adapted scheme and the step-by-step entry points are for the CDF
+ *           wavelets only.
  * All functions return 0 on success and a negative value on invalid arguments.
  */
 #ifndef DWT2_ORACLE_H
@@ -28,7 +33,7 @@
 extern "C" {
 #endif
 
-enum { ORC_CDF53_INT = 0, ORC_CDF53 = 1, ORC_CDF97 = 2 };
+enum { ORC_CDF53_INT = 0, ORC_CDF53 = 1, ORC_CDF97 = 2, ORC_DD97 = 3, ORC_DD137 = 4 };
 
 /* Schemes: how one level is evaluated.
  *   ORC_SEP_EQ3      separable lifting, steps P_h, P_v, U_h, U_v per lifting pair (Eq. 3)

@@ -19,7 +19,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "dwt2_oracle.c")
 _LIB = os.path.join(_HERE, "liboracle.so")
 
-WAVELETS = {"cdf53_int": 0, "cdf53": 1, "cdf97": 2}
+WAVELETS = {"cdf53_int": 0, "cdf53": 1, "cdf97": 2, "dd97": 3, "dd137": 4}
 SCHEMES = {"eq3": 0, "rows": 1, "cols": 2, "eq5": 3, "adapted": 4}
 
 
