@@ -283,6 +283,8 @@ def run_only(args, D, dev, x_f32, x_i32, flush, stream):
         "inv_cdf97": ("cdf97", x_f32, LEVELS, True, "nonsep"),
         "fwd_cdf53_int": ("cdf53_int", x_i32, LEVELS, False, "nonsep"),
         "inv_cdf53_int": ("cdf53_int", x_i32, LEVELS, True, "nonsep"),
+        "fwd_dd137": ("dd137", x_f32, LEVELS, False, "nonsep"),
+        "inv_dd137": ("dd137", x_f32, LEVELS, True, "nonsep"),
         "twopass_cdf97": ("cdf97", x_f32, LEVELS, False, "sep_twopass"),
         "sepfused_cdf97": ("cdf97", x_f32, LEVELS, False, "sep_fused"),
         "adapted_cdf97": ("cdf97", x_f32, LEVELS, False, "adapted"),
@@ -581,7 +583,7 @@ def main():
                          "storage against the fp64 oracle, and the time of each")
     ap.add_argument("--only", default=None,
                     choices=["fwd_l1_cdf97", "fwd_cdf97", "inv_cdf97", "fwd_cdf53_int",
-                             "inv_cdf53_int", "twopass_cdf97", "sepfused_cdf97", "adapted_cdf97",
+                             "inv_cdf53_int", "fwd_dd137", "inv_dd137", "twopass_cdf97", "sepfused_cdf97", "adapted_cdf97",
                              "conv_cdf97", "plan_cdf97", "plan_cdf53_int"],
                     help="run one case only (for profiler captures); prints a short line")
     ap.add_argument("--levels-table", action="store_true",
@@ -706,6 +708,15 @@ def main():
         lambda: D.inverse(c97, out=out_f, workspace=ws97), args.steps, args.warmup))
     cases["inv_cdf53_int_nonsep"] = summarise(run_case(
         lambda: D.inverse(ci, out=out_i, workspace=wsi), args.steps, args.warmup))
+    # the Deslauriers-Dubuc wavelets (four-tap steps) through the same non-separable kernels
+    for wv in ("dd97", "dd137"):
+        cd, wsd, _ = make(wv, x_f32)
+        cases[f"fwd_{wv}_f32_nonsep"] = summarise(run_case(
+            lambda: D.forward(x_f32, wv, LEVELS, out=cd, workspace=wsd), args.steps,
+            args.warmup))
+        cases[f"inv_{wv}_f32_nonsep"] = summarise(run_case(
+            lambda: D.inverse(cd, out=out_f, workspace=wsd), args.steps, args.warmup))
+        del cd, wsd
     for scheme in ("sep_fused", "sep_twopass"):
         for wv, x in (("cdf97", x_f32), ("cdf53_int", x_i32)):
             c, ws, _ = make(wv, x, scheme)

@@ -29,6 +29,16 @@
  *                       Daubechies-Sweldens factorisation, then low-pass * 1/K and high-pass
  *                       * K/2 per axis (low-pass DC gain 1, high-pass Nyquist gain 1), i.e.
  *                       LL / K^2, HL / 2, LH / 2, HH * K^2 / 4.
+ *       DWT2_DD97_F32   Deslauriers-Dubuc 9/7 in fp32 (the interpolating wavelet with a
+ *                       four-tap predict): d[m] = x_o - (9/16 (s[m] + s[m+1]) - 1/16 (s[m-1] +
+ *                       s[m+2])), the cubic interpolation of the odd sample, then
+ *                       s[m] += 1/4 (d[m-1] + d[m]); no scaling.
+ *       DWT2_DD137_F32  Deslauriers-Dubuc 13/7 in fp32: the same predict, then
+ *                       s[m] += 9/32 (d[m-1] + d[m]) - 1/32 (d[m-2] + d[m+1]); no scaling.
+ *     The Deslauriers-Dubuc wavelets run the non-separable scheme of Eq. 5 (their spatial steps
+ *     with these P, U) in dwt2_forward, dwt2_inverse, the uniform batch entry points and
+ *     dwt2_forward_static; the separable comparators, the adjoints and the batched plans return
+ *     DWT2_EUNSUPPORTED for them.
  *   - All arithmetic of the float wavelets is fp32.  DWT2_BF16 / DWT2_F16 are storage types
  *     only: values are widened on load and rounded to nearest-even on store.  With 16-bit
  *     band storage the intermediate LL planes (workspace) and the final LL_J stay fp32.
@@ -58,7 +68,9 @@ extern "C" {
 typedef enum {
     DWT2_CDF53_INT = 0,
     DWT2_CDF53_F32 = 1,
-    DWT2_CDF97_F32 = 2
+    DWT2_CDF97_F32 = 2,
+    DWT2_DD97_F32 = 3,
+    DWT2_DD137_F32 = 4
 } dwt2_wavelet;
 
 /* Element types.  DWT2_I32 is the only type of the integer wavelet; the float wavelets take

@@ -201,7 +201,7 @@ static MapResult make_map(CUtensorMap* m, const void* base, int64_t pitch, int64
 
 // ------------------------------------------------------------------------------ validation
 static int check_types(int wavelet, int img_dtype, int band_dtype) {
-    if (wavelet < WV_CDF53_INT || wavelet > WV_CDF97) return DWT2_EINVAL;
+    if (wavelet < WV_CDF53_INT || wavelet > WV_DD137) return DWT2_EINVAL;
     if (img_dtype < DT_I32 || img_dtype > DT_F16 || band_dtype < DT_I32 || band_dtype > DT_F16)
         return DWT2_EINVAL;
     if (wavelet == WV_CDF53_INT)
@@ -243,6 +243,8 @@ static cudaError_t launch_fwd(int wavelet, int mode, int ti, int tb, bool tma,
     switch (wavelet) {
     case WV_CDF53_INT: return launch_fwd_i53(mode, tm, a, s);
     case WV_CDF53: return launch_fwd_f53(mode, ti, tb, tm, a, s);
+    case WV_DD97:
+    case WV_DD137: return launch_fwd_dd(wavelet, mode, ti, tb, tm, a, s);
     default: return launch_fwd_f97(mode, ti, tb, tm, a, s);
     }
 }
@@ -305,9 +307,11 @@ static int forward_impl(const void* img, int64_t img_pitch, int H, int W, int im
                         Batch bt = Batch{1, 0, 0}, bool clear_status = false) {
     int rc = check_types(wavelet, img_dtype, band_dtype);
     if (rc) return rc;
-    if (adjoint && (wavelet == WV_CDF53_INT || img_dtype != DT_F32 || band_dtype != DT_F32))
+    if (adjoint && (wavelet == WV_CDF53_INT || is_dd(wavelet) || img_dtype != DT_F32 ||
+                    band_dtype != DT_F32))
         return DWT2_EUNSUPPORTED;
     if (scheme < DWT2_SCHEME_NONSEP || scheme > DWT2_SCHEME_CONV) return DWT2_EINVAL;
+    if (is_dd(wavelet) && scheme != DWT2_SCHEME_NONSEP) return DWT2_EUNSUPPORTED;
     if (scheme != DWT2_SCHEME_NONSEP && (img_dtype != band_dtype || bt.N != 1))
         return DWT2_EUNSUPPORTED;
     if ((scheme == DWT2_SCHEME_ADAPTED || scheme == DWT2_SCHEME_CONV) &&
@@ -419,7 +423,8 @@ static int inverse_impl(const void* coeffs, void* img, int64_t img_pitch, int H,
                         Batch bt = Batch{1, 0, 0}) {
     int rc = check_types(wavelet, img_dtype, band_dtype);
     if (rc) return rc;
-    if (adjoint && (wavelet == WV_CDF53_INT || img_dtype != DT_F32 || band_dtype != DT_F32))
+    if (adjoint && (wavelet == WV_CDF53_INT || is_dd(wavelet) || img_dtype != DT_F32 ||
+                    band_dtype != DT_F32))
         return DWT2_EUNSUPPORTED;
     Layout L;
     if ((rc = make_layout(H, W, J, band_dtype, &L))) return rc;
@@ -627,7 +632,7 @@ DWT2_EXPORT int dwt2_layout(int H, int W, int levels, int band_dtype, dwt2_band*
 DWT2_EXPORT size_t dwt2_workspace_bytes_scheme(int H, int W, int levels, int wavelet,
                                                int band_dtype, int scheme) {
     Layout L;
-    if (make_layout(H, W, levels, band_dtype, &L) || wavelet < 0 || wavelet > 2 ||
+    if (make_layout(H, W, levels, band_dtype, &L) || wavelet < 0 || wavelet > WV_DD137 ||
         scheme < DWT2_SCHEME_NONSEP || scheme > DWT2_SCHEME_CONV)
         return 0;
     return size_t(plan_workspace(H, W, levels, wavelet, scheme).bytes);
@@ -700,7 +705,8 @@ DWT2_EXPORT int dwt2_inverse_adjoint(const void* g_img, int64_t g_img_pitch_byte
 DWT2_EXPORT size_t dwt2_workspace_bytes_batch(int N, int H, int W, int levels, int wavelet,
                                               int band_dtype) {
     Layout L;
-    if (N < 1 || make_layout(H, W, levels, band_dtype, &L) || wavelet < 0 || wavelet > 2) return 0;
+    if (N < 1 || make_layout(H, W, levels, band_dtype, &L) || wavelet < 0 || wavelet > WV_DD137)
+        return 0;
     return size_t(kHeader + N * ws_region(plan_workspace(H, W, levels, wavelet, DWT2_SCHEME_NONSEP)));
 }
 

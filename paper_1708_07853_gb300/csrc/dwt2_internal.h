@@ -20,9 +20,14 @@ cudaError_t launch_fwd_f53(int mode, int ti, int tb, const CUtensorMap& tm, cons
                            cudaStream_t s);
 cudaError_t launch_fwd_f97(int mode, int ti, int tb, const CUtensorMap& tm, const FwdArgs& a,
                            cudaStream_t s);
+// The Deslauriers-Dubuc wavelets (WV_DD97, WV_DD137): the non-separable scheme only.
+cudaError_t launch_fwd_dd(int wavelet, int mode, int ti, int tb, const CUtensorMap& tm,
+                          const FwdArgs& a, cudaStream_t s);
 // Inverse level launch.  tb = band dtype, to = output-plane dtype; tm = LL, HL, LH, HH maps.
 cudaError_t launch_inv(int wavelet, int tb, int to, const CUtensorMap* tm, const InvArgs& a,
                        cudaStream_t s);
+cudaError_t launch_inv_dd(int wavelet, int tb, int to, const CUtensorMap* tm, const InvArgs& a,
+                          cudaStream_t s);
 
 // Adjoint levels (float wavelets, fp32): W_j^T with the inverse kernel's data flow, W_j^-T with
 // the forward kernel's.

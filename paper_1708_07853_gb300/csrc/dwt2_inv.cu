@@ -30,6 +30,8 @@ cudaError_t launch_inv(int wavelet, int tb, int to, const CUtensorMap* tm,
         return go<WV_CDF53_INT, int32_t, int32_t, int32_t>(tm, a, s);
     case WV_CDF53: return go_float<WV_CDF53>(tb, to, tm, a, s);
     case WV_CDF97: return go_float<WV_CDF97>(tb, to, tm, a, s);
+    case WV_DD97:
+    case WV_DD137: return launch_inv_dd(wavelet, tb, to, tm, a, s);
     default: return cudaErrorNotSupported;
     }
 }

@@ -22,7 +22,10 @@ namespace dwt2 {
 
 constexpr int kQ = 2;  // polyphase quads per lane (adjacent along a row)
 
-enum Wavelet { WV_CDF53_INT = 0, WV_CDF53 = 1, WV_CDF97 = 2 };
+enum Wavelet { WV_CDF53_INT = 0, WV_CDF53 = 1, WV_CDF97 = 2, WV_DD97 = 3, WV_DD137 = 4 };
+// The Deslauriers-Dubuc (interpolating) wavelets: their predict has four taps, and so does the
+// 13/7's update.
+__host__ __device__ constexpr bool is_dd(int wv) { return wv == WV_DD97 || wv == WV_DD137; }
 enum Mode {
     MODE_NONSEP = 0,
     MODE_SEP = 1,
@@ -1065,6 +1068,297 @@ struct InvPipe<WV_CDF53_INT> {
         iu.push(r);
         ip.push(r, t);
         r = t;
+    }
+};
+
+// =============================================================================================
+// Four-tap lifting steps: the Deslauriers-Dubuc 9/7 and 13/7 (Sec. 1 and Sec. 5 hold the schemes
+// for any wavelet).  The predict of an odd sample reads its even neighbours at m, m+1 (inner
+// pair, weight p0) and m-1, m+2 (outer pair, p1): the cubic interpolation, p0 = -9/16,
+// p1 = 1/16.  The update of an even sample reads its odd neighbours at m-1, m (u0) and m-2, m+1
+// (u1): 1/4, 0 for 9/7 and 9/32, -1/32 for 13/7.  No scaling.  The spatial steps are those of
+// Eq. 5 with these P, P*, U, U*, evaluated in the factored form of the two-tap steps above
+// (HH += P*(HL after P) + P(LH); LL += U(HL) + U*(LH after U)).  A warp's window needs two halo
+// lanes on each side (the reach of a level is three quads), so these wavelets run with a
+// narrower output window (halo_q).
+// =============================================================================================
+constexpr float kDDp0 = -9.0f / 16.0f;
+constexpr float kDDp1 = 1.0f / 16.0f;
+constexpr float kDD137u0 = 9.0f / 32.0f;
+constexpr float kDD137u1 = -1.0f / 32.0f;
+
+// v at quad m + K (K = 1, 2) and m - K of each of a lane's kQ quads (K <= kQ).
+template <int K, typename C>
+__device__ __forceinline__ void right_k(const C (&v)[kQ], C (&r)[kQ]) {
+#pragma unroll
+    for (int q = 0; q < kQ; ++q)
+        r[q] = q + K < kQ ? v[q + K] : __shfl_down_sync(kFull, v[q + K - kQ], 1);
+}
+template <int K, typename C>
+__device__ __forceinline__ void left_k(const C (&v)[kQ], C (&l)[kQ]) {
+#pragma unroll
+    for (int q = 0; q < kQ; ++q)
+        l[q] = q - K >= 0 ? v[q - K] : __shfl_up_sync(kFull, v[q - K + kQ], 1);
+}
+
+// P along a row: p0 (v[m] + v[m+1]) + p1 (v[m-1] + v[m+2]).
+__device__ __forceinline__ void predict_h4(const float (&v)[kQ], float p0, float p1,
+                                           float (&o)[kQ]) {
+    float r1[kQ], r2[kQ], l1[kQ];
+    right_k<1>(v, r1);
+    right_k<2>(v, r2);
+    left_k<1>(v, l1);
+#pragma unroll
+    for (int q = 0; q < kQ; ++q) o[q] = fmaf(p0, v[q] + r1[q], p1 * (l1[q] + r2[q]));
+}
+// U along a row: u0 (v[m-1] + v[m]) + u1 (v[m-2] + v[m+1]).
+__device__ __forceinline__ void update_h4(const float (&v)[kQ], float u0, float u1,
+                                          float (&o)[kQ]) {
+    float l1[kQ], l2[kQ], r1[kQ];
+    left_k<1>(v, l1);
+    left_k<2>(v, l2);
+    right_k<1>(v, r1);
+#pragma unroll
+    for (int q = 0; q < kQ; ++q) o[q] = fmaf(u0, l1[q] + v[q], u1 * (l2[q] + r1[q]));
+}
+// A vertical four-tap term from four rows: w0 (x0 + x1) + w1 (xm + x2).
+__device__ __forceinline__ float tap4(float x0, float x1, float xm, float x2, float w0, float w1) {
+    return fmaf(w0, x0 + x1, w1 * (xm + x2));
+}
+
+// Spatial predict with a four-tap P.  push(row n + 2) returns row n (lag 2).
+struct PredictNS4 {
+    float a[3][kQ], b[3][kQ];  // rows n-1, n, n+1: LL and HL after the horizontal step
+    float c[2][kQ], t[2][kQ];  // rows n, n+1: LH and HH + P(LH)
+    __device__ __forceinline__ void init() {
+#pragma unroll
+        for (int q = 0; q < kQ; ++q) {
+            a[0][q] = a[1][q] = a[2][q] = b[0][q] = b[1][q] = b[2][q] = 0.f;
+            c[0][q] = c[1][q] = t[0][q] = t[1][q] = 0.f;
+        }
+    }
+    __device__ __forceinline__ void push(const QRow<float>& y, QRow<float>& o) {
+        float pa[kQ], pc[kQ], yb[kQ], yt[kQ];
+        predict_h4(y.a, kDDp0, kDDp1, pa);
+        predict_h4(y.c, kDDp0, kDDp1, pc);
+#pragma unroll
+        for (int q = 0; q < kQ; ++q) {
+            yb[q] = y.b[q] + pa[q];
+            yt[q] = y.e[q] + pc[q];
+            o.a[q] = a[1][q];
+            o.b[q] = b[1][q];
+            o.c[q] = c[0][q] + tap4(a[1][q], a[2][q], a[0][q], y.a[q], kDDp0, kDDp1);
+            o.e[q] = t[0][q] + tap4(b[1][q], b[2][q], b[0][q], yb[q], kDDp0, kDDp1);
+            a[0][q] = a[1][q];
+            a[1][q] = a[2][q];
+            a[2][q] = y.a[q];
+            b[0][q] = b[1][q];
+            b[1][q] = b[2][q];
+            b[2][q] = yb[q];
+            c[0][q] = c[1][q];
+            c[1][q] = y.c[q];
+            t[0][q] = t[1][q];
+            t[1][q] = yt[q];
+        }
+    }
+};
+
+// Spatial update with a four-tap U.  push(row i + 1) returns row i (lag 1).
+struct UpdateNS4 {
+    float u0, u1;
+    float l[3][kQ], e[3][kQ];  // rows i-2, i-1, i: LH + U(HH), and HH
+    float ta[kQ], hb[kQ];      // row i: LL + U(HL), and HL
+    __device__ __forceinline__ void init(float u0_, float u1_) {
+        u0 = u0_;
+        u1 = u1_;
+#pragma unroll
+        for (int q = 0; q < kQ; ++q) {
+            l[0][q] = l[1][q] = l[2][q] = e[0][q] = e[1][q] = e[2][q] = 0.f;
+            ta[q] = hb[q] = 0.f;
+        }
+    }
+    __device__ __forceinline__ void push(const QRow<float>& x, QRow<float>& o) {
+        float ue[kQ], ub[kQ], xl[kQ], xt[kQ];
+        update_h4(x.e, u0, u1, ue);
+        update_h4(x.b, u0, u1, ub);
+#pragma unroll
+        for (int q = 0; q < kQ; ++q) {
+            xl[q] = x.c[q] + ue[q];
+            xt[q] = x.a[q] + ub[q];
+            o.a[q] = ta[q] + tap4(l[1][q], l[2][q], l[0][q], xl[q], u0, u1);
+            o.b[q] = hb[q] + tap4(e[1][q], e[2][q], e[0][q], x.e[q], u0, u1);
+            o.c[q] = l[2][q];
+            o.e[q] = e[2][q];
+            l[0][q] = l[1][q];
+            l[1][q] = l[2][q];
+            l[2][q] = xl[q];
+            e[0][q] = e[1][q];
+            e[1][q] = e[2][q];
+            e[2][q] = x.e[q];
+            ta[q] = xt[q];
+            hb[q] = x.b[q];
+        }
+    }
+};
+
+// Undoes UpdateNS4.  push(row i + 1) returns row i (lag 1).
+struct InvUpdateNS4 {
+    float u0, u1;
+    float c[3][kQ], e[3][kQ];  // rows i-2, i-1, i: stored LH and HH
+    float a1[kQ], b1[kQ];      // row i: stored LL and HL
+    __device__ __forceinline__ void init(float u0_, float u1_) {
+        u0 = u0_;
+        u1 = u1_;
+#pragma unroll
+        for (int q = 0; q < kQ; ++q) {
+            c[0][q] = c[1][q] = c[2][q] = e[0][q] = e[1][q] = e[2][q] = 0.f;
+            a1[q] = b1[q] = 0.f;
+        }
+    }
+    __device__ __forceinline__ void push(const QRow<float>& x, QRow<float>& o) {
+        float hl[kQ], uh[kQ], ue[kQ];
+#pragma unroll
+        for (int q = 0; q < kQ; ++q)
+            hl[q] = b1[q] - tap4(e[1][q], e[2][q], e[0][q], x.e[q], u0, u1);
+        update_h4(hl, u0, u1, uh);
+        update_h4(e[2], u0, u1, ue);
+#pragma unroll
+        for (int q = 0; q < kQ; ++q) {
+            o.a[q] = a1[q] - tap4(c[1][q], c[2][q], c[0][q], x.c[q], u0, u1) - uh[q];
+            o.b[q] = hl[q];
+            o.c[q] = c[2][q] - ue[q];
+            o.e[q] = e[2][q];
+            c[0][q] = c[1][q];
+            c[1][q] = c[2][q];
+            c[2][q] = x.c[q];
+            e[0][q] = e[1][q];
+            e[1][q] = e[2][q];
+            e[2][q] = x.e[q];
+            a1[q] = x.a[q];
+            b1[q] = x.b[q];
+        }
+    }
+};
+
+// Undoes PredictNS4.  push(row i + 2) returns row i (lag 2).
+struct InvPredictNS4 {
+    float a[3][kQ], b[3][kQ];  // rows i-1, i, i+1: LL and stored HL
+    float c[2][kQ], e[2][kQ];  // rows i, i+1: stored LH and HH
+    __device__ __forceinline__ void init() {
+#pragma unroll
+        for (int q = 0; q < kQ; ++q) {
+            a[0][q] = a[1][q] = a[2][q] = b[0][q] = b[1][q] = b[2][q] = 0.f;
+            c[0][q] = c[1][q] = e[0][q] = e[1][q] = 0.f;
+        }
+    }
+    __device__ __forceinline__ void push(const QRow<float>& y, QRow<float>& o) {
+        float lh[kQ], pa[kQ], pl[kQ];
+#pragma unroll
+        for (int q = 0; q < kQ; ++q)
+            lh[q] = c[0][q] - tap4(a[1][q], a[2][q], a[0][q], y.a[q], kDDp0, kDDp1);
+        predict_h4(a[1], kDDp0, kDDp1, pa);
+        predict_h4(lh, kDDp0, kDDp1, pl);
+#pragma unroll
+        for (int q = 0; q < kQ; ++q) {
+            o.a[q] = a[1][q];
+            o.b[q] = b[1][q] - pa[q];
+            o.c[q] = lh[q];
+            o.e[q] = e[0][q] - tap4(b[1][q], b[2][q], b[0][q], y.b[q], kDDp0, kDDp1) - pl[q];
+            a[0][q] = a[1][q];
+            a[1][q] = a[2][q];
+            a[2][q] = y.a[q];
+            b[0][q] = b[1][q];
+            b[1][q] = b[2][q];
+            b[2][q] = y.b[q];
+            c[0][q] = c[1][q];
+            c[1][q] = y.c[q];
+            e[0][q] = e[1][q];
+            e[1][q] = y.e[q];
+        }
+    }
+};
+
+// One Deslauriers-Dubuc level (the non-separable scheme only).  9/7: the four-tap predict and
+// the two-tap update (lag 2); 13/7: both four-tap (lag 3).
+template <int MODE>
+struct FwdPipe<WV_DD97, MODE> {
+    static_assert(MODE == MODE_NONSEP, "the Deslauriers-Dubuc wavelets have the fused scheme only");
+    static constexpr int kLag = 2;
+    using C = float;
+    PredictNS4 pn;
+    UpdateNS<float> un;
+    float ll_add;
+    __device__ __forceinline__ void init(float ll_add_ = -0.f) {
+        ll_add = ll_add_;
+        pn.init();
+        un.init(0.25f);
+    }
+    __device__ __forceinline__ void push(QRow<float>& r) {
+        QRow<float> t;
+        pn.push(r, t);
+        un.push(t);
+#pragma unroll
+        for (int q = 0; q < kQ; ++q) t.a[q] += ll_add;
+        r = t;
+    }
+};
+
+template <int MODE>
+struct FwdPipe<WV_DD137, MODE> {
+    static_assert(MODE == MODE_NONSEP, "the Deslauriers-Dubuc wavelets have the fused scheme only");
+    static constexpr int kLag = 3;
+    using C = float;
+    PredictNS4 pn;
+    UpdateNS4 un;
+    float ll_add;
+    __device__ __forceinline__ void init(float ll_add_ = -0.f) {
+        ll_add = ll_add_;
+        pn.init();
+        un.init(kDD137u0, kDD137u1);
+    }
+    __device__ __forceinline__ void push(QRow<float>& r) {
+        QRow<float> t, o;
+        pn.push(r, t);
+        un.push(t, o);
+#pragma unroll
+        for (int q = 0; q < kQ; ++q) o.a[q] += ll_add;
+        r = o;
+    }
+};
+
+template <>
+struct InvPipe<WV_DD97> {
+    static constexpr int kLag = 2;
+    using C = float;
+    InvUpdateNS<float> iu;
+    InvPredictNS4 ip;
+    __device__ __forceinline__ void init() {
+        iu.init(0.25f);
+        ip.init();
+    }
+    __device__ __forceinline__ void push(QRow<float>& r) {
+        QRow<float> t;
+        iu.push(r);
+        ip.push(r, t);
+        r = t;
+    }
+};
+
+template <>
+struct InvPipe<WV_DD137> {
+    static constexpr int kLag = 3;
+    using C = float;
+    InvUpdateNS4 iu;
+    InvPredictNS4 ip;
+    __device__ __forceinline__ void init() {
+        iu.init(kDD137u0, kDD137u1);
+        ip.init();
+    }
+    __device__ __forceinline__ void push(QRow<float>& r) {
+        QRow<float> t, o;
+        iu.push(r, t);
+        ip.push(t, o);
+        r = o;
     }
 };
 

@@ -75,7 +75,8 @@ int64_t scratch_offsets(const dwt2_image_desc* imgs, int n, int J, int wavelet,
 int check_plan_args(const dwt2_image_desc* imgs, int n, int wavelet, int J, int img_dtype,
                     int band_dtype, int direction) {
     if (!imgs || n < 1 || !valid_direction(direction)) return DWT2_EINVAL;
-    if (wavelet < WV_CDF53_INT || wavelet > WV_CDF97) return DWT2_EINVAL;
+    if (wavelet < WV_CDF53_INT || wavelet > WV_DD137) return DWT2_EINVAL;
+    if (is_dd(wavelet)) return DWT2_EUNSUPPORTED;  // plans run the CDF wavelets only
     const bool adj = direction == DWT2_DIR_FORWARD_ADJOINT || direction == DWT2_DIR_INVERSE_ADJOINT;
     if (wavelet == WV_CDF53_INT) {
         if (img_dtype != DT_I32 || band_dtype != DT_I32 || adj) return DWT2_EUNSUPPORTED;

@@ -32,9 +32,19 @@ constexpr int kWarpOut = kWarpQ - 2 * kHQ;  // output quads per warp (30 lanes)
 // busy) but 3 strips of 180 (9 of 9), and the batched 3-level transforms of 192 such images ran
 // 21% faster with it (pick_nw chooses per launch).  The stage rows are sized for the wide CTA.
 constexpr int kMaxNW = 4;
-template <int NW>
+// The Deslauriers-Dubuc wavelets reach three quads per level, so their warp windows keep two
+// halo lanes on each side (56 output quads per warp instead of 60).
+template <int WV>
+constexpr int halo_q() {  // halo quads on each side of a warp window
+    return is_dd(WV) ? 2 * kQ : kHQ;
+}
+template <int WV>
+constexpr int warp_out() {  // output quads per warp
+    return kWarpQ - 2 * halo_q<WV>();
+}
+template <int NW, int WV = WV_CDF97>
 constexpr int cta_q() {  // output quads per CTA strip
-    return NW * kWarpOut;
+    return NW * warp_out<WV>();
 }
 template <int NW>
 constexpr int cta_threads() {
@@ -48,7 +58,7 @@ constexpr int kMaxCtaQ = cta_q<kMaxNW>();
 // 5 CTAs per SM (72 registers, no spills) the forward measured 6% and the inverse 9% slower.
 template <int WV, int NW>
 constexpr int min_ctas() {  // the 5/3 kernels at 64 registers (6 wide or 8 narrow CTAs per SM)
-    return WV == 2 ? 1 : (NW == 3 ? 8 : 6);
+    return (WV == WV_CDF97 || is_dd(WV)) ? 1 : (NW == 3 ? 8 : 6);
 }
 // Consumer row loop unrolled by 2 for the 5/3 wavelets: the compiler then renames the row
 // pipeline's registers instead of rotating them (int 5/3 forward 4.7% faster on GB300).  The 9/7
@@ -56,7 +66,7 @@ constexpr int min_ctas() {  // the 5/3 kernels at 64 registers (6 wide or 8 narr
 // executed 19% more instructions (ALU and uniform-pipe work for the pair bookkeeping).
 template <int WV>
 constexpr int row_unroll() {
-    return WV == 2 ? 1 : 2;
+    return (WV == WV_CDF97 || is_dd(WV)) ? 1 : 2;
 }
 // Ring depth (quad rows in flight per CTA) per wavelet and data flow, from same-box A/B runs
 // at 8192^2 over depths 6, 8 and 12: the 5/3 kernels are 2-3% faster with 12 (shared memory
@@ -65,11 +75,11 @@ constexpr int row_unroll() {
 // with 8.
 template <int WV>
 constexpr int fwd_stages() {
-    return WV == 2 ? 6 : 12;
+    return WV == WV_CDF97 ? 6 : is_dd(WV) ? 8 : 12;
 }
 template <int WV>
 constexpr int inv_stages() {
-    return WV == 2 ? 8 : 12;
+    return (WV == WV_CDF97 || is_dd(WV)) ? 8 : 12;
 }
 constexpr int kVHalo = 2;                // halo quad rows above and below a CTA's rows (adjoints)
 
@@ -100,15 +110,15 @@ static_assert(kBRow >= kXLB + kMaxCtaQ + kHQ, "inverse stage row too short");
 // input elements, the inverse x = qx0 - kXLB + kBoxW b band elements, qx0 a multiple of the CTA
 // strip: every term must be a multiple of 16 bytes.  The narrow strip (180 quads) fails this for
 // 16-bit bands in the inverse (odd strips would start 8 bytes off), so those keep the wide CTA.
-template <int NW, typename T>
+template <int NW, typename T, int WV = WV_CDF97>
 constexpr bool fwd_tma_x_aligned() {
-    return (2 * cta_q<NW>() * sizeof(T)) % 16 == 0 && (kXL * sizeof(T)) % 16 == 0 &&
-           (kBoxW * sizeof(T)) % 16 == 0;
+    return (2 * cta_q<NW, WV>() * sizeof(T)) % 16 == 0 && (kXL * sizeof(T)) % 16 == 0 &&
+           (kBoxW * sizeof(T)) % 16 == 0 && 2 * halo_q<WV>() <= kXL;
 }
-template <int NW, typename T>
+template <int NW, typename T, int WV = WV_CDF97>
 constexpr bool inv_tma_x_aligned() {
-    return (cta_q<NW>() * sizeof(T)) % 16 == 0 && (kXLB * sizeof(T)) % 16 == 0 &&
-           (kBoxW * sizeof(T)) % 16 == 0;
+    return (cta_q<NW, WV>() * sizeof(T)) % 16 == 0 && (kXLB * sizeof(T)) % 16 == 0 &&
+           (kBoxW * sizeof(T)) % 16 == 0 && halo_q<WV>() <= kXLB;
 }
 // The narrowest CTA whose inverse band loads stay aligned: band type TB, LL type TL.
 template <typename TB, typename TL>
@@ -848,7 +858,9 @@ __device__ __forceinline__ void drain_ring(const Ring<NS>& r, int issued, int* s
 // forward 140.3 -> 141.3 us and inverse 139.5 -> 145.1 us, and its 192 x 1024^2 batch 10%
 // slower: the 9/7 kernels are bound by instruction issue, and the hinted stores cost them more
 // than the L2 reads save.  The 9/7 kernels therefore keep plain stores and loads.
-__host__ __device__ constexpr bool keeps_ll_in_l2(int wv) { return wv != WV_CDF97; }
+__host__ __device__ constexpr bool keeps_ll_in_l2(int wv) {
+    return wv == WV_CDF53_INT || wv == WV_CDF53;
+}
 
 // Forward levels that take the DC level shift: float lifting (every scheme but the convolution,
 // whose only intermediates are the filter outputs) and not the adjoint (a linear map of
@@ -868,8 +880,10 @@ template <int WV, int MODE, typename TI, typename TB, typename TL, bool kPlain, 
 __global__ void __launch_bounds__(cta_threads<NW>(), min_ctas<WV, NW>())
     k_forward(const __grid_constant__ CUtensorMap tmap, const FwdArgs args) {
     constexpr int kNW = NW;
-    constexpr int kCtaQ = cta_q<NW>();
-    static_assert(fwd_tma_x_aligned<NW, TI>(), "TMA x coordinates of this CTA width misaligned");
+    constexpr int kCtaQ = cta_q<NW, WV>();
+    constexpr int kHaloQ = halo_q<WV>();
+    constexpr int kHaloLanes = kHaloQ / kQ;
+    static_assert(fwd_tma_x_aligned<NW, TI, WV>(), "TMA x coordinates of this CTA width misaligned");
     constexpr bool kAdj = MODE == MODE_ADJ_INV;
     using Pipe = std::conditional_t<kAdj, AdjInvPipe<WV>, FwdPipe<WV, kAdj ? MODE_NONSEP : MODE>>;
     using C = typename Pipe::C;
@@ -919,16 +933,16 @@ __global__ void __launch_bounds__(cta_threads<NW>(), min_ctas<WV, NW>())
     }
 
     // ------------------------------------------------------------------------- consumers
-    const int wq = qx0 - kHQ + warp * kWarpOut;  // first quad of the warp window
-    const int m0 = wq + kQ * lane;               // first quad of this lane
-    const bool store_lane = lane >= 1 && lane <= 30;
+    const int wq = qx0 - kHaloQ + warp * warp_out<WV>();  // first quad of the warp window
+    const int m0 = wq + kQ * lane;                         // first quad of this lane
+    const bool store_lane = lane >= kHaloLanes && lane < 32 - kHaloLanes;
     FwdCols cols;
     cols.init(2 * m0, xs, args.W, !kAdj, (2 * wq < 0) || (2 * wq + 2 * kWarpQ > args.W));
     ConvCols ccols;
     if constexpr (MODE == MODE_CONV)
         ccols.init(2 * m0, xs, args.W, (2 * wq - 4 < 0) || (2 * wq + 2 * kWarpQ + 4 > args.W));
     // a warp whose output quads all lie beyond the plane only cycles the barriers
-    const bool idle = wq + kHQ >= args.nec;
+    const bool idle = wq + kHaloQ >= args.nec;
     LaneW hw;
     if constexpr (kAdj) hw.init(m0, AxisLen{args.nec, args.ndc});
     const AxisLen rows{args.ner, args.ndr};
@@ -1095,8 +1109,10 @@ __global__ void __launch_bounds__(cta_threads<NW>(), min_ctas<WV, NW>())
               const __grid_constant__ CUtensorMap tm_lh, const __grid_constant__ CUtensorMap tm_hh,
               const InvArgs args) {
     constexpr int kNW = NW;
-    constexpr int kCtaQ = cta_q<NW>();
-    static_assert(inv_tma_x_aligned<NW, TB>() && inv_tma_x_aligned<NW, TL>(),
+    constexpr int kCtaQ = cta_q<NW, WV>();
+    constexpr int kHaloQ = halo_q<WV>();
+    constexpr int kHaloLanes = kHaloQ / kQ;
+    static_assert(inv_tma_x_aligned<NW, TB, WV>() && inv_tma_x_aligned<NW, TL, WV>(),
                   "TMA x coordinates of this CTA width misaligned");
     using Pipe = std::conditional_t<ADJ, AdjFwdPipe<WV>, InvPipe<WV>>;
     using C = typename Pipe::C;
@@ -1151,12 +1167,12 @@ __global__ void __launch_bounds__(cta_threads<NW>(), min_ctas<WV, NW>())
     }
 
     // ------------------------------------------------------------------------- consumers
-    const int wq = qx0 - kHQ + warp * kWarpOut;
+    const int wq = qx0 - kHaloQ + warp * warp_out<WV>();
     const int m0 = wq + kQ * lane;
-    const bool store_lane = lane >= 1 && lane <= 30;
+    const bool store_lane = lane >= kHaloLanes && lane < 32 - kHaloLanes;
     InvCols cols;
     cols.init(m0, xb, args.W, !ADJ, (2 * wq < 0) || (2 * wq + 2 * kWarpQ > args.W));
-    const bool idle = wq + kHQ >= args.nec;
+    const bool idle = wq + kHaloQ >= args.nec;
     LaneW hw;
     if constexpr (ADJ) hw.init(m0, AxisLen{args.nec, args.ndc});
     const AxisLen rows{args.ner, args.ndr};
@@ -1398,7 +1414,7 @@ cudaError_t launch_forward_k(const CUtensorMap& tm, FwdArgs a, cudaStream_t st) 
     constexpr size_t smem = fwd_smem_bytes<TI, fwd_stages<WV>()>();
     static const int occ = configure(k, cta_threads<NW>(), smem);
     const LaunchGeom g = pick_geometry(a.ner, a.nec, int64_t(a.H) * a.W * int64_t(sizeof(TI)),
-                                       device_sm_count(), occ, a.nbatch, cta_q<NW>());
+                                       device_sm_count(), occ, a.nbatch, cta_q<NW, WV>());
     a.rpc = g.rpc;
     return launch_pdl(k, g.grid, cta_threads<NW>(), smem, st, tm, a);
 }
@@ -1432,7 +1448,7 @@ cudaError_t launch_forward_direct(FwdArgs a, cudaStream_t st) {
 // Small planes of the non-separable forward take the direct kernel.
 template <int WV, int MODE, typename TI, typename TB, typename TL>
 cudaError_t launch_forward_t(const CUtensorMap& tm, FwdArgs a, cudaStream_t st) {
-    if constexpr (MODE == MODE_NONSEP) {
+    if constexpr (MODE == MODE_NONSEP && !is_dd(WV)) {
         if (takes_direct(a.H, a.W, sizeof(TI), a.nbatch)) {
             using C = std::conditional_t<WV == WV_CDF53_INT, int32_t, float>;
             if constexpr (kShiftable<C, MODE>) {
@@ -1441,7 +1457,7 @@ cudaError_t launch_forward_t(const CUtensorMap& tm, FwdArgs a, cudaStream_t st) 
             return launch_forward_direct<WV, TI, TB, TL, false>(a, st);
         }
     }
-    if constexpr (MODE == MODE_NONSEP || MODE == MODE_ADJ_INV) {
+    if constexpr ((MODE == MODE_NONSEP || MODE == MODE_ADJ_INV) && !is_dd(WV)) {
         if (pick_nw(a.nec, int64_t(a.H) * a.W * int64_t(sizeof(TI)) * a.nbatch) == 3)
             return launch_forward_nw<WV, MODE, TI, TB, TL, 3>(tm, a, st);
     }
@@ -1454,14 +1470,14 @@ cudaError_t launch_inverse_k(const CUtensorMap* tm, InvArgs a, cudaStream_t st) 
     constexpr size_t smem = inv_smem_bytes<TL, TB, inv_stages<WV>()>();
     static const int occ = configure(k, cta_threads<NW>(), smem);
     const LaunchGeom g = pick_geometry(a.ner, a.nec, int64_t(a.H) * a.W * int64_t(sizeof(TL)),
-                                       device_sm_count(), occ, a.nbatch, cta_q<NW>());
+                                       device_sm_count(), occ, a.nbatch, cta_q<NW, WV>());
     a.rpc = g.rpc;
     return launch_pdl(k, g.grid, cta_threads<NW>(), smem, st, tm[0], tm[1], tm[2], tm[3], a);
 }
 
 template <int WV, typename TB, typename TL, typename TO, bool ADJ, bool kShift>
 cudaError_t launch_inverse_s(const CUtensorMap* tm, InvArgs a, cudaStream_t st) {
-    if constexpr (inv_narrow_nw<TB, TL>() == 3) {
+    if constexpr (inv_narrow_nw<TB, TL>() == 3 && !is_dd(WV)) {
         const int64_t bytes = int64_t(a.H) * a.W * int64_t(sizeof(TL)) * a.nbatch;
         if (pick_nw(a.nec, bytes) == 3)
             return launch_inverse_k<WV, TB, TL, TO, ADJ, kShift, 3>(tm, a, st);
@@ -1484,7 +1500,7 @@ cudaError_t launch_inverse_direct(InvArgs a, cudaStream_t st) {
 // Small output planes of the inverse take the direct kernel.
 template <int WV, typename TB, typename TL, typename TO, bool ADJ = false>
 cudaError_t launch_inverse_t(const CUtensorMap* tm, InvArgs a, cudaStream_t st) {
-    if constexpr (!ADJ) {
+    if constexpr (!ADJ && !is_dd(WV)) {
         if (takes_direct(a.H, a.W, sizeof(TL), a.nbatch)) {
             if constexpr (WV != WV_CDF53_INT) {
                 if (a.shift.mode != 0) return launch_inverse_direct<WV, TB, TL, TO, true>(a, st);

@@ -15,7 +15,7 @@ import torch
 _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "libdwt2.so")
 
-WAVELETS = {"cdf53_int": 0, "cdf53": 1, "cdf97": 2}
+WAVELETS = {"cdf53_int": 0, "cdf53": 1, "cdf97": 2, "dd97": 3, "dd137": 4}
 SCHEMES = {"nonsep": 0, "sep_fused": 1, "sep_twopass": 2, "adapted": 3, "conv": 4}
 DT_I32, DT_F32, DT_BF16, DT_F16 = 0, 1, 2, 3
 TORCH_DT = {torch.int32: DT_I32, torch.float32: DT_F32, torch.bfloat16: DT_BF16,
