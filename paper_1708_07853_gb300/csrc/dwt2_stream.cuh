@@ -56,17 +56,22 @@ constexpr int kMaxCtaQ = cta_q<kMaxNW>();
 // 8-stage ring (their 12-stage ring now holds them to 4 CTAs per SM by shared memory, which is
 // faster still).  The CDF 9/7 kernels are left free (78-80 registers, 4 CTAs per SM): bound to
 // 5 CTAs per SM (72 registers, no spills) the forward measured 6% and the inverse 9% slower.
+// The Deslauriers-Dubuc 13/7 kernels are bound to 4 CTAs per SM (96 registers, no spills; 108
+// and 3 CTAs per SM unbound): together with the unrolled row loop below its 8192^2 forward took
+// 190 -> 172 us and its inverse 191 -> 169 us on GB300.
 template <int WV, int NW>
 constexpr int min_ctas() {  // the 5/3 kernels at 64 registers (6 wide or 8 narrow CTAs per SM)
-    return (WV == WV_CDF97 || is_dd(WV)) ? 1 : (NW == 3 ? 8 : 6);
+    return (WV == WV_CDF97 || WV == WV_DD97) ? 1 : WV == WV_DD137 ? 4 : (NW == 3 ? 8 : 6);
 }
 // Consumer row loop unrolled by 2 for the 5/3 wavelets: the compiler then renames the row
 // pipeline's registers instead of rotating them (int 5/3 forward 4.7% faster on GB300).  The 9/7
 // kernels stay rolled: unrolled they measured 2% slower, and a hand-written loop over row pairs
 // executed 19% more instructions (ALU and uniform-pipe work for the pair bookkeeping).
+// The Deslauriers-Dubuc kernels are unrolled by 2 as well (their three-row windows rotate more
+// registers per row; the 9/7 DD inverse took 148.5 -> 142.3 us with it).
 template <int WV>
 constexpr int row_unroll() {
-    return (WV == WV_CDF97 || is_dd(WV)) ? 1 : 2;
+    return WV == WV_CDF97 ? 1 : 2;
 }
 // Ring depth (quad rows in flight per CTA) per wavelet and data flow, from same-box A/B runs
 // at 8192^2 over depths 6, 8 and 12: the 5/3 kernels are 2-3% faster with 12 (shared memory
