@@ -1010,11 +1010,12 @@ __global__ void __launch_bounds__(cta_threads<NW>(), min_ctas<WV, NW>())
 // Direct forward level for small planes (a few MB, in L2 after the previous level wrote them).
 // The streaming kernel's fixed costs -- a producer warp, the stage ring and its barriers, the TMA
 // latency of the first rows and the pipeline fill -- dominate there, and every level costs a
-// few microseconds whatever its size.  Here each warp is one 60-quad window of kDirectRows output
-// quad rows: it loads the kDirectRows + 2 kLag input quad rows it needs straight from global
-// memory (L2) into registers, all at once, then pushes them through the same FwdPipe and stores
-// through the same band rows as the streaming kernel, so the results are the same bits.  The
-// halo rows are loaded and computed again by the windows above and below.
+// few microseconds whatever its size.  Here each warp is one window (60 output quads, 56 for the
+// Deslauriers-Dubuc wavelets) of kDirectRows output quad rows: it loads the kDirectRows + 2 kLag
+// input quad rows it needs straight from global memory (L2) into registers, all at once, then
+// pushes them through the same FwdPipe and stores through the same band rows as the streaming
+// kernel, so the results are the same bits.  The halo rows are loaded and computed again by the
+// windows above and below.
 // =============================================================================================
 constexpr int kDirectRows = 2;     // output quad rows per warp
 constexpr int kDirectWarps = 4;    // warps (windows) per CTA
@@ -1054,15 +1055,17 @@ __global__ void __launch_bounds__(32 * kDirectWarps) k_forward_direct(const FwdA
     constexpr int kRows = kDirectRows + 2 * kLag;  // input quad rows per warp
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int z = blockIdx.z;
+    constexpr int kHaloQ = halo_q<WV>();
+    constexpr int kHaloLanes = kHaloQ / kQ;
     // grid x runs over row blocks (a tall plane may have more than 65535 of them), y over strips
-    const int wq = (blockIdx.y * kDirectWarps + warp) * kWarpOut - kHQ;  // first quad of the window
+    const int wq = (blockIdx.y * kDirectWarps + warp) * warp_out<WV>() - kHaloQ;  // window start
     const int m0 = wq + kQ * lane;
     const int n0 = blockIdx.x * kDirectRows;
     const int n1 = min(n0 + kDirectRows, args.ner);
-    const bool store_lane = lane >= 1 && lane <= 30;
+    const bool store_lane = lane >= kHaloLanes && lane < 32 - kHaloLanes;
     grid_dependency_wait();  // the input plane is the previous level's output
     allow_dependent_launch();
-    if (wq + kHQ >= args.nec) return;  // a window wholly beyond the plane: the warp has no work
+    if (wq + kHaloQ >= args.nec) return;  // a window wholly beyond the plane: no work
 
     const char* base = static_cast<const char*>(args.in) + int64_t(z) * args.in_bstride;
     const bool edge = (2 * wq < 0) || (2 * wq + 2 * kWarpQ > args.W);
@@ -1258,14 +1261,16 @@ __global__ void __launch_bounds__(32 * kDirectWarps) k_inverse_direct(const InvA
     constexpr int kRows = kDirectRows + 2 * kLag;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int z = blockIdx.z;
-    const int wq = (blockIdx.y * kDirectWarps + warp) * kWarpOut - kHQ;
+    constexpr int kHaloQ = halo_q<WV>();
+    constexpr int kHaloLanes = kHaloQ / kQ;
+    const int wq = (blockIdx.y * kDirectWarps + warp) * warp_out<WV>() - kHaloQ;
     const int m0 = wq + kQ * lane;
     const int n0 = blockIdx.x * kDirectRows;
     const int n1 = min(n0 + kDirectRows, args.ner);
-    const bool store_lane = lane >= 1 && lane <= 30;
+    const bool store_lane = lane >= kHaloLanes && lane < 32 - kHaloLanes;
     grid_dependency_wait();
     allow_dependent_launch();
-    if (wq + kHQ >= args.nec) return;
+    if (wq + kHaloQ >= args.nec) return;
 
     // columns: LL / LH hold the even pixel columns 2m, HL / HH the odd ones 2m + 1
     const bool edge = (2 * wq < 0) || (2 * wq + 2 * kWarpQ > args.W);
@@ -1442,7 +1447,7 @@ cudaError_t launch_forward_nw(const CUtensorMap& tm, FwdArgs a, cudaStream_t st)
 template <int WV, typename TI, typename TB, typename TL, bool kShift>
 cudaError_t launch_forward_direct(FwdArgs a, cudaStream_t st) {
     auto k = k_forward_direct<WV, TI, TB, TL, kShift>;
-    const int windows = (a.nec + kWarpOut - 1) / kWarpOut;
+    const int windows = (a.nec + warp_out<WV>() - 1) / warp_out<WV>();
     const dim3 grid((a.ner + kDirectRows - 1) / kDirectRows,
                     (windows + kDirectWarps - 1) / kDirectWarps, std::max(1, a.nbatch));
     a.rpc = kDirectRows;
@@ -1453,7 +1458,7 @@ cudaError_t launch_forward_direct(FwdArgs a, cudaStream_t st) {
 // Small planes of the non-separable forward take the direct kernel.
 template <int WV, int MODE, typename TI, typename TB, typename TL>
 cudaError_t launch_forward_t(const CUtensorMap& tm, FwdArgs a, cudaStream_t st) {
-    if constexpr (MODE == MODE_NONSEP && !is_dd(WV)) {
+    if constexpr (MODE == MODE_NONSEP) {
         if (takes_direct(a.H, a.W, sizeof(TI), a.nbatch)) {
             using C = std::conditional_t<WV == WV_CDF53_INT, int32_t, float>;
             if constexpr (kShiftable<C, MODE>) {
@@ -1495,7 +1500,7 @@ cudaError_t launch_inverse_s(const CUtensorMap* tm, InvArgs a, cudaStream_t st) 
 template <int WV, typename TB, typename TL, typename TO, bool kShift>
 cudaError_t launch_inverse_direct(InvArgs a, cudaStream_t st) {
     auto k = k_inverse_direct<WV, TB, TL, TO, kShift>;
-    const int windows = (a.nec + kWarpOut - 1) / kWarpOut;
+    const int windows = (a.nec + warp_out<WV>() - 1) / warp_out<WV>();
     const dim3 grid((a.ner + kDirectRows - 1) / kDirectRows,
                     (windows + kDirectWarps - 1) / kDirectWarps, std::max(1, a.nbatch));
     a.rpc = kDirectRows;
@@ -1505,7 +1510,7 @@ cudaError_t launch_inverse_direct(InvArgs a, cudaStream_t st) {
 // Small output planes of the inverse take the direct kernel.
 template <int WV, typename TB, typename TL, typename TO, bool ADJ = false>
 cudaError_t launch_inverse_t(const CUtensorMap* tm, InvArgs a, cudaStream_t st) {
-    if constexpr (!ADJ && !is_dd(WV)) {
+    if constexpr (!ADJ) {
         if (takes_direct(a.H, a.W, sizeof(TL), a.nbatch)) {
             if constexpr (WV != WV_CDF53_INT) {
                 if (a.shift.mode != 0) return launch_inverse_direct<WV, TB, TL, TO, true>(a, st);
