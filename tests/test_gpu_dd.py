@@ -84,6 +84,28 @@ def test_dd_16bit_bands(wv, dt):
 
 
 @pytest.mark.parametrize("wv", DD)
+@pytest.mark.parametrize("dt", [torch.bfloat16, torch.float16])
+def test_dd_16bit_image_and_bands(wv, dt):
+    """A 16-bit image: the oracle transforms the same (already rounded) values; the inverse
+    writes a 16-bit image within one rounding of the input."""
+    H, W = 517, 300
+    x = torch.from_numpy(I.field_plus_noise(H, W, I.seed_for(2, W))).to(dt)
+    xs = x.float().numpy().astype(np.float64)
+    c = D.forward(x.cuda(), wv, 4, band_dtype=dt)
+    want = O.forward(xs, wv, 4, "eq5")
+    for v, w in zip(c.band_views(), want):
+        g = v.float().cpu().numpy().astype(np.float64)
+        tol = FLOAT_TOL + np.abs(w) * (0.0 if v.dtype == torch.float32 else REL[dt])
+        assert np.all(np.abs(g - w) <= tol), (wv, dt, np.abs(g - w).max())
+    # the inverse of the stored (rounded) coefficients, against the oracle's inverse of the same
+    # values: fp32 arithmetic plus the rounding of the 16-bit output image
+    r = D.inverse(c, img_dtype=dt).float().cpu().numpy().astype(np.float64)
+    got = [v.float().cpu().numpy().astype(np.float64) for v in c.band_views()]
+    want_r = O.inverse(got, H, W, wv, 4, "eq5")
+    assert np.all(np.abs(r - want_r) <= FLOAT_TOL + np.abs(want_r) * REL[dt]), wv
+
+
+@pytest.mark.parametrize("wv", DD)
 def test_dd_unaligned_pitch_matches_aligned(wv):
     H, W = 301, 1517
     x = np.random.default_rng(9).uniform(0, 255, (H, W)).astype(np.float32)
