@@ -189,8 +189,9 @@ int dwt2_inverse(const void* coeffs, void* img, int64_t img_pitch_bytes, int H, 
                  int img_dtype, void* workspace, size_t ws_bytes, int wavelet, int levels,
                  int band_dtype, void* stream);
 
-/* Adjoints (transposes) of the float transforms, for gradients (float wavelets, DWT2_F32 image
- * and band storage only; the integer wavelet returns DWT2_EUNSUPPORTED).
+/* Adjoints (transposes) of the float transforms, for gradients (the float CDF wavelets, DWT2_F32
+ * image and band storage only; the integer and the Deslauriers-Dubuc wavelets return
+ * DWT2_EUNSUPPORTED).
  *   dwt2_forward_adjoint  applies W^T, the transpose of dwt2_forward: g_coeffs (laid out by
  *                         dwt2_layout) -> g_img (H x W).  Levels levels..1, each level the
  *                         transposed fused steps in reverse order: the transpose of the spatial
@@ -269,7 +270,8 @@ int dwt2_inverse_adjoint_batch(const void* g_img, int64_t g_img_pitch_bytes,
  *                   Without a path a default schedule is used.
  * The plan allocates its own small device buffers (descriptors, tensor maps, counters) at
  * creation and captures [counter reset, kernel] in a graph; buffers are bound at creation.
- * Results are identical to the single-image entry points (bit for bit for the integer wavelet). */
+ * Results are identical to the single-image entry points (bit for bit for the integer wavelet).
+ * Plans cover the CDF wavelets; the Deslauriers-Dubuc wavelets return DWT2_EUNSUPPORTED. */
 typedef struct {
     void* img;
     int64_t img_pitch_bytes;
