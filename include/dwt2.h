@@ -37,8 +37,8 @@
  *                       s[m] += 9/32 (d[m-1] + d[m]) - 1/32 (d[m-2] + d[m+1]); no scaling.
  *     The Deslauriers-Dubuc wavelets run the non-separable scheme of Eq. 5 (their spatial steps
  *     with these P, U) in dwt2_forward, dwt2_inverse, the uniform batch entry points and
- *     dwt2_forward_static; the separable comparators, the adjoints and the batched plans return
- *     DWT2_EUNSUPPORTED for them.
+ *     dwt2_forward_static and the batched plans (forward and inverse directions); the separable
+ *     comparators and the adjoints return DWT2_EUNSUPPORTED for them.
  *   - All arithmetic of the float wavelets is fp32.  DWT2_BF16 / DWT2_F16 are storage types
  *     only: values are widened on load and rounded to nearest-even on store.  With 16-bit
  *     band storage the intermediate LL planes (workspace) and the final LL_J stay fp32.
@@ -271,7 +271,8 @@ int dwt2_inverse_adjoint_batch(const void* g_img, int64_t g_img_pitch_bytes,
  * The plan allocates its own small device buffers (descriptors, tensor maps, counters) at
  * creation and captures [counter reset, kernel] in a graph; buffers are bound at creation.
  * Results are identical to the single-image entry points (bit for bit for the integer wavelet).
- * Plans cover the CDF wavelets; the Deslauriers-Dubuc wavelets return DWT2_EUNSUPPORTED. */
+ * The Deslauriers-Dubuc wavelets take the forward and inverse directions (their adjoint
+ * directions return DWT2_EUNSUPPORTED). */
 typedef struct {
     void* img;
     int64_t img_pitch_bytes;

@@ -42,6 +42,11 @@ cudaError_t launch_fwd_persistent(int wavelet, int mode, int tb, const PersistAr
                                   int ctas_per_sm, cudaStream_t st, int* occ);
 cudaError_t launch_inv_persistent(int wavelet, bool adj, int tb, const PersistArgs<InvUnit>& p,
                                   int ctas_per_sm, cudaStream_t st, int* occ);
+// The Deslauriers-Dubuc wavelets' persistent kernels (forward and inverse; no adjoints).
+cudaError_t launch_fwd_persistent_dd(int wavelet, int mode, int tb, const PersistArgs<FwdUnit>& p,
+                                     int ctas_per_sm, cudaStream_t st, int* occ);
+cudaError_t launch_inv_persistent_dd(int wavelet, bool adj, int tb, const PersistArgs<InvUnit>& p,
+                                     int ctas_per_sm, cudaStream_t st, int* occ);
 
 // dwt2_forward with the status header of the workspace cleared after the argument checks (the
 // built-in scratch of dwt2_forward_static).

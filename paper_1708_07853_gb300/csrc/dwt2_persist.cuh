@@ -100,11 +100,11 @@ struct Tile {
     int qx0, n0, n1, nrows, qfirst;
 };
 
-template <int kVH, int NW, typename Args>
+template <int kVH, int NW, int WV, typename Args>
 __device__ __forceinline__ Tile tile_of(const Args& a, int local, int strips) {
     Tile t;
     const int rb = local / strips, strip = local - rb * strips;
-    t.qx0 = strip * cta_q<NW>();
+    t.qx0 = strip * cta_q<NW, WV>();
     t.n0 = rb * a.rpc;
     t.n1 = min(t.n0 + a.rpc, a.ner);
     t.nrows = t.n1 - t.n0 + 2 * kVH;
@@ -125,7 +125,7 @@ __device__ __forceinline__ void prefetch_unit_maps(const InvUnit& u) {
 // do not fit the single-image kernels' 64-register budget of the 5/3 wavelets without spilling.
 template <int WV>
 constexpr int persist_min_ctas() {
-    return WV == 2 ? 1 : 4;
+    return (WV == WV_CDF97 || is_dd(WV)) ? 1 : 4;
 }
 
 // Plain-load path of the persistent kernels, per wavelet.  The integer 5/3 takes the single-image
@@ -194,7 +194,10 @@ template <int WV, int MODE, typename TI, typename TB, typename TL>
 __global__ void __launch_bounds__(cta_threads<kPersistFwdNW>(), persist_min_ctas<WV>())
     k_forward_persistent(const PersistArgs<FwdUnit> p) {
     constexpr int kNW = kPersistFwdNW;
-    static_assert(fwd_tma_x_aligned<kNW, TI>(), "TMA x coordinates of this CTA width misaligned");
+    constexpr int kHaloQ = halo_q<WV>();
+    constexpr int kHaloLanes = kHaloQ / kQ;
+    static_assert(fwd_tma_x_aligned<kNW, TI, WV>(),
+                  "TMA x coordinates of this CTA width misaligned");
     constexpr bool kAdj = MODE == MODE_ADJ_INV;
     using Pipe = std::conditional_t<kAdj, AdjInvPipe<WV>, FwdPipe<WV, MODE_NONSEP>>;
     using C = typename Pipe::C;
@@ -219,7 +222,7 @@ __global__ void __launch_bounds__(cta_threads<kPersistFwdNW>(), persist_min_ctas
             }
             const FwdUnit& U = p.units[__ldg(&p.item_unit[t])];
             pargs = U.a;
-            const Tile tl = tile_of<kVH, kNW>(pargs, t - __ldg(&U.item_begin), __ldg(&U.strips));
+            const Tile tl = tile_of<kVH, kNW, WV>(pargs, t - __ldg(&U.item_begin), __ldg(&U.strips));
             const int xs = 2 * tl.qx0 - kXL;
             bulk_used |= pargs.tma != 0 || (persist_bulk<WV>() && !kAdj);
             bool alive = true;
@@ -250,7 +253,7 @@ __global__ void __launch_bounds__(cta_threads<kPersistFwdNW>(), persist_min_ctas
 
     // ------------------------------------------------------------------------- consumers
     FwdArgs A;  // the current tile's unit arguments, held in registers (see below)
-    const bool store_lane = lane >= 1 && lane <= 30;
+    const bool store_lane = lane >= kHaloLanes && lane < 32 - kHaloLanes;
     int cur = -1, i = 0, unit = 0;
     Tile tl{};
     FwdCols cols;
@@ -272,12 +275,12 @@ __global__ void __launch_bounds__(cta_threads<kPersistFwdNW>(), persist_min_ctas
             unit = __ldg(&p.item_unit[t]);
             const FwdUnit* U = &p.units[unit];
             A = U->a;
-            tl = tile_of<kVH, kNW>(A, t - __ldg(&U->item_begin), __ldg(&U->strips));
-            const int wq = tl.qx0 - kHQ + warp * kWarpOut;
+            tl = tile_of<kVH, kNW, WV>(A, t - __ldg(&U->item_begin), __ldg(&U->strips));
+            const int wq = tl.qx0 - kHaloQ + warp * warp_out<WV>();
             m0 = wq + kQ * lane;
             const int xs = 2 * tl.qx0 - kXL;
             cols.init(2 * m0, xs, A.W, !kAdj, (2 * wq < 0) || (2 * wq + 2 * kWarpQ > A.W));
-            idle = wq + kHQ >= A.nec;
+            idle = wq + kHaloQ >= A.nec;
             if constexpr (kAdj) hw.init(m0, AxisLen{A.nec, A.ndc});
             bands.init<TB, TL>(A, tl.n0, m0, 0);
             if constexpr (kShift) {
@@ -318,7 +321,9 @@ template <int WV, typename TB, typename TL, typename TO, bool ADJ>
 __global__ void __launch_bounds__(cta_threads<persist_inv_nw<TB, TL>()>(), persist_min_ctas<WV>())
     k_inverse_persistent(const PersistArgs<InvUnit> p) {
     constexpr int kNW = persist_inv_nw<TB, TL>();
-    static_assert(inv_tma_x_aligned<kNW, TB>() && inv_tma_x_aligned<kNW, TL>(),
+    constexpr int kHaloQ = halo_q<WV>();
+    constexpr int kHaloLanes = kHaloQ / kQ;
+    static_assert(inv_tma_x_aligned<kNW, TB, WV>() && inv_tma_x_aligned<kNW, TL, WV>(),
                   "TMA x coordinates of this CTA width misaligned");
     using Pipe = std::conditional_t<ADJ, AdjFwdPipe<WV>, InvPipe<WV>>;
     using C = typename Pipe::C;
@@ -344,7 +349,7 @@ __global__ void __launch_bounds__(cta_threads<persist_inv_nw<TB, TL>()>(), persi
             }
             const InvUnit& U = p.units[__ldg(&p.item_unit[t])];
             pargs = U.a;
-            const Tile tl = tile_of<kVH, kNW>(pargs, t - __ldg(&U.item_begin), __ldg(&U.strips));
+            const Tile tl = tile_of<kVH, kNW, WV>(pargs, t - __ldg(&U.item_begin), __ldg(&U.strips));
             const int xb = tl.qx0 - kXLB;
             const CUtensorMap* maps[4] = {&U.tm[0], &U.tm[1], &U.tm[2], &U.tm[3]};
             tma_used |= pargs.tma != 0;
@@ -374,7 +379,7 @@ __global__ void __launch_bounds__(cta_threads<persist_inv_nw<TB, TL>()>(), persi
 
     // ------------------------------------------------------------------------- consumers
     InvArgs A;  // the current tile's unit arguments, held in registers (see below)
-    const bool store_lane = lane >= 1 && lane <= 30;
+    const bool store_lane = lane >= kHaloLanes && lane < 32 - kHaloLanes;
     int cur = -1, i = 0, unit = 0;
     Tile tl{};
     InvCols cols;
@@ -396,11 +401,11 @@ __global__ void __launch_bounds__(cta_threads<persist_inv_nw<TB, TL>()>(), persi
             unit = __ldg(&p.item_unit[t]);
             const InvUnit* U = &p.units[unit];
             A = U->a;
-            tl = tile_of<kVH, kNW>(A, t - __ldg(&U->item_begin), __ldg(&U->strips));
-            const int wq = tl.qx0 - kHQ + warp * kWarpOut;
+            tl = tile_of<kVH, kNW, WV>(A, t - __ldg(&U->item_begin), __ldg(&U->strips));
+            const int wq = tl.qx0 - kHaloQ + warp * warp_out<WV>();
             m0 = wq + kQ * lane;
             cols.init(m0, tl.qx0 - kXLB, A.W, !ADJ, (2 * wq < 0) || (2 * wq + 2 * kWarpQ > A.W));
-            idle = wq + kHQ >= A.nec;
+            idle = wq + kHaloQ >= A.nec;
             if constexpr (ADJ) hw.init(m0, AxisLen{A.nec, A.ndc});
             out_p = reinterpret_cast<char*>(row_ptr<TO>(A.out, 2 * tl.n0, 0) + 2 * m0);
             if constexpr (kShift) sh.init(A.shift, 0);

@@ -42,6 +42,8 @@ cudaError_t launch_fwd_persistent(int wavelet, int mode, int tb, const PersistAr
         return go<WV_CDF53_INT, MODE_NONSEP, int32_t, int32_t, int32_t>(p, ctas_per_sm, st, occ);
     case WV_CDF53: return go_float<WV_CDF53>(mode, tb, p, ctas_per_sm, st, occ);
     case WV_CDF97: return go_float<WV_CDF97>(mode, tb, p, ctas_per_sm, st, occ);
+    case WV_DD97:
+    case WV_DD137: return launch_fwd_persistent_dd(wavelet, mode, tb, p, ctas_per_sm, st, occ);
     default: return cudaErrorNotSupported;
     }
 }

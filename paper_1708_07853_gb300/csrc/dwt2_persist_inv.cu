@@ -42,6 +42,8 @@ cudaError_t launch_inv_persistent(int wavelet, bool adj, int tb, const PersistAr
         return go<WV_CDF53_INT, int32_t, int32_t, int32_t, false>(p, ctas_per_sm, st, occ);
     case WV_CDF53: return go_float<WV_CDF53>(adj, tb, p, ctas_per_sm, st, occ);
     case WV_CDF97: return go_float<WV_CDF97>(adj, tb, p, ctas_per_sm, st, occ);
+    case WV_DD97:
+    case WV_DD137: return launch_inv_persistent_dd(wavelet, adj, tb, p, ctas_per_sm, st, occ);
     default: return cudaErrorNotSupported;
     }
 }

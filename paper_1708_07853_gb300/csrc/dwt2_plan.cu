@@ -76,7 +76,6 @@ int check_plan_args(const dwt2_image_desc* imgs, int n, int wavelet, int J, int 
                     int band_dtype, int direction) {
     if (!imgs || n < 1 || !valid_direction(direction)) return DWT2_EINVAL;
     if (wavelet < WV_CDF53_INT || wavelet > WV_DD137) return DWT2_EINVAL;
-    if (is_dd(wavelet)) return DWT2_EUNSUPPORTED;  // plans run the CDF wavelets only
     const bool adj = direction == DWT2_DIR_FORWARD_ADJOINT || direction == DWT2_DIR_INVERSE_ADJOINT;
     if (wavelet == WV_CDF53_INT) {
         if (img_dtype != DT_I32 || band_dtype != DT_I32 || adj) return DWT2_EUNSUPPORTED;
@@ -85,6 +84,7 @@ int check_plan_args(const dwt2_image_desc* imgs, int n, int wavelet, int J, int 
         if (band_dtype != DT_F32 && band_dtype != DT_BF16 && band_dtype != DT_F16)
             return DWT2_EUNSUPPORTED;
         if (adj && band_dtype != DT_F32) return DWT2_EUNSUPPORTED;
+        if (adj && is_dd(wavelet)) return DWT2_EUNSUPPORTED;  // no adjoints for these wavelets
     }
     for (int i = 0; i < n; ++i) {
         const dwt2_image_desc& d = imgs[i];
@@ -99,12 +99,16 @@ int check_plan_args(const dwt2_image_desc* imgs, int n, int wavelet, int J, int 
 }
 
 // Quad columns of a tile: the strip of the persistent kernel the plan launches (its CTA width
-// depends on the data flow and, for the inverse flow, on the band type).
-int plan_cta_q(const dwt2_plan* P) {
-    if (P->fwd_flow) return cta_q<kPersistFwdNW>();
+// depends on the data flow, for the inverse flow on the band type, and on the wavelet's halo).
+template <int WV>
+static int plan_cta_q_w(const dwt2_plan* P) {
+    if (P->fwd_flow) return cta_q<kPersistFwdNW, WV>();
     if (P->band_dtype == DT_BF16 || P->band_dtype == DT_F16)
-        return cta_q<persist_inv_nw<__nv_bfloat16, float>()>();
-    return cta_q<persist_inv_nw<float, float>()>();
+        return cta_q<persist_inv_nw<__nv_bfloat16, float>(), WV>();
+    return cta_q<persist_inv_nw<float, float>(), WV>();
+}
+int plan_cta_q(const dwt2_plan* P) {
+    return is_dd(P->wavelet) ? plan_cta_q_w<WV_DD97>(P) : plan_cta_q_w<WV_CDF97>(P);
 }
 
 // Upper bound on the quad rows per tile at level j, for `rows` at level 1: halved at every level
@@ -471,7 +475,8 @@ int autotune(dwt2_plan* P, int occ) {
 // ==================================================================================== C ABI
 DWT2_EXPORT size_t dwt2_plan_workspace_bytes(const dwt2_image_desc* imgs, int n, int wavelet,
                                              int levels, int band_dtype) {
-    if (!imgs || n < 1 || wavelet < 0 || wavelet > 2 || band_dtype < 0 || band_dtype > 3) return 0;
+    if (!imgs || n < 1 || wavelet < 0 || wavelet > WV_DD137 || band_dtype < 0 || band_dtype > 3)
+        return 0;
     for (int i = 0; i < n; ++i)
         if (imgs[i].H < 1 || imgs[i].W < 1 || levels < 1 || levels > dwt2_max_levels(imgs[i].H, imgs[i].W))
             return 0;

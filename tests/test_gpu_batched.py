@@ -52,7 +52,10 @@ SIZES = I.batch_sizes(20, I.seed_for(3, 1), lo=17, hi=700) + [(63, 1500), (1023,
                                                ("cdf53", torch.float32, D.DT_F32),
                                                ("cdf97", torch.float32, D.DT_F32),
                                                ("cdf97", torch.float32, D.DT_BF16),
-                                               ("cdf53", torch.float32, D.DT_F16)])
+                                               ("cdf53", torch.float32, D.DT_F16),
+                                               ("dd97", torch.float32, D.DT_F32),
+                                               ("dd137", torch.float32, D.DT_F32),
+                                               ("dd137", torch.float32, D.DT_BF16)])
 def test_forward_plan_equals_single_image(wavelet, dtype, bdt):
     imgs = _images(SIZES, dtype, 11)
     plan, coeffs = D.plan_forward(imgs, wavelet, 4, band_dtype=bdt)
@@ -75,7 +78,8 @@ def test_forward_plan_equals_single_image(wavelet, dtype, bdt):
     assert D.check_status(plan.workspace) == 0
 
 
-@pytest.mark.parametrize("wavelet,dtype", [("cdf53_int", torch.int32), ("cdf97", torch.float32)])
+@pytest.mark.parametrize("wavelet,dtype", [("cdf53_int", torch.int32), ("cdf97", torch.float32),
+                                           ("dd97", torch.float32), ("dd137", torch.float32)])
 def test_inverse_plan_equals_single_image(wavelet, dtype):
     imgs = _images(SIZES, dtype, 12)
     coeffs = [D.forward(x, wavelet, 4) for x in imgs]
@@ -165,7 +169,8 @@ def test_log_uniform_batch_64():
             _same(c, D.forward(x, wavelet, 4))
 
 
-@pytest.mark.parametrize("wavelet,dtype", [("cdf53_int", torch.int32), ("cdf97", torch.float32)])
+@pytest.mark.parametrize("wavelet,dtype", [("cdf53_int", torch.int32), ("cdf97", torch.float32),
+                                           ("dd137", torch.float32)])
 def test_large_image_plan_many_row_blocks(wavelet, dtype):
     """One 4100 x 3000 image (plus two small ones), 5 levels: many tiles per level and many
     CTAs waiting on each level's completion counter, forward and inverse, bit for bit against

@@ -2,8 +2,8 @@
 non-separable scheme of Eq. 5) against the CPU oracle: forward coefficients, the inverse of the
 oracle's coefficients and the GPU round trip within 1e-3 on [0, 255] inputs (fp32), ragged and
 tiny sizes at every level count, 16-bit band storage within its rounding, unaligned rows, uniform
-batches and the 8192^2 five-level workload.  The entry points that do not cover these wavelets
-(separable comparators, adjoints, plans) must refuse them."""
+batches and the 8192^2 five-level workload (plans: test_gpu_batched.py).  The entry points that
+do not cover these wavelets (separable comparators, adjoints) must refuse them."""
 import numpy as np
 import pytest
 import torch
@@ -158,5 +158,6 @@ def test_dd_unsupported_entry_points_refuse(wv):
         D.forward(x, wv, 2, scheme="sep_fused")
     with pytest.raises(D.Dwt2Error):
         D.inverse_adjoint(x, wv, 2)
+    outs = [D.alloc_coeffs(64, 64, 2, wv, D.DT_F32, "cuda")]
     with pytest.raises(D.Dwt2Error):
-        D.plan_forward([x], wv, 2)
+        D.Plan([x], outs, wv, 2, "inverse_adjoint", D.DT_F32)
