@@ -723,6 +723,12 @@ def main():
             ms = run_case(lambda: D.forward(x, wv, LEVELS, scheme=scheme, out=c, workspace=ws),
                           args.steps, args.warmup)
             cases[f"fwd_{wv}_{scheme}"] = summarise(ms)
+    # the two-pass comparator of the four-tap Deslauriers-Dubuc 13/7
+    cd2, wsd2, _ = make("dd137", x_f32, "sep_twopass")
+    cases["fwd_dd137_sep_twopass"] = summarise(run_case(
+        lambda: D.forward(x_f32, "dd137", LEVELS, scheme="sep_twopass", out=cd2, workspace=wsd2),
+        args.steps, args.warmup))
+    del cd2, wsd2
     # the adapted non-separable scheme (Sec. 3; float wavelets): the ablation of its split
     c, ws, _ = make("cdf97", x_f32, "adapted")
     cases["fwd_cdf97_adapted"] = summarise(run_case(
@@ -739,6 +745,8 @@ def main():
             cases[f"fwd_{wv}_{sc}"]["ms"] / cases[f"fwd_{wv}_{ref}"]["ms"], 3)
         for wv, ref in (("cdf97", "f32_nonsep"), ("cdf53_int", "nonsep"))
         for sc in ("sep_fused", "sep_twopass")}
+    comparison["dd137_nonsep_speedup_vs_sep_twopass"] = round(
+        cases["fwd_dd137_sep_twopass"]["ms"] / cases["fwd_dd137_f32_nonsep"]["ms"], 3)
     correct_inv = bool(torch.equal(D.inverse(ci, out=out_i, workspace=wsi), x_i32))
     clocks = sampler.summary(t0, t1)  # the headline window (extended into these cases if short)
     sampler.stop()

@@ -37,8 +37,9 @@
  *                       s[m] += 9/32 (d[m-1] + d[m]) - 1/32 (d[m-2] + d[m+1]); no scaling.
  *     The Deslauriers-Dubuc wavelets run the non-separable scheme of Eq. 5 (their spatial steps
  *     with these P, U) in dwt2_forward, dwt2_inverse, the uniform batch entry points and
- *     dwt2_forward_static and the batched plans (forward and inverse directions); the separable
- *     comparators and the adjoints return DWT2_EUNSUPPORTED for them.
+ *     dwt2_forward_static and the batched plans (forward and inverse directions), and the
+ *     two-pass separable comparator (DWT2_SCHEME_SEP_TWOPASS, fp32); the other comparators and
+ *     the adjoints return DWT2_EUNSUPPORTED for them.
  *   - All arithmetic of the float wavelets is fp32.  DWT2_BF16 / DWT2_F16 are storage types
  *     only: values are widened on load and rounded to nearest-even on store.  With 16-bit
  *     band storage the intermediate LL planes (workspace) and the final LL_J stay fp32.

@@ -311,7 +311,8 @@ static int forward_impl(const void* img, int64_t img_pitch, int H, int W, int im
                     band_dtype != DT_F32))
         return DWT2_EUNSUPPORTED;
     if (scheme < DWT2_SCHEME_NONSEP || scheme > DWT2_SCHEME_CONV) return DWT2_EINVAL;
-    if (is_dd(wavelet) && scheme != DWT2_SCHEME_NONSEP) return DWT2_EUNSUPPORTED;
+    if (is_dd(wavelet) && scheme != DWT2_SCHEME_NONSEP && scheme != DWT2_SCHEME_SEP_TWOPASS)
+        return DWT2_EUNSUPPORTED;
     if (scheme != DWT2_SCHEME_NONSEP && (img_dtype != band_dtype || bt.N != 1))
         return DWT2_EUNSUPPORTED;
     if ((scheme == DWT2_SCHEME_ADAPTED || scheme == DWT2_SCHEME_CONV) &&

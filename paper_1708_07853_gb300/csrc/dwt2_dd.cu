@@ -33,8 +33,22 @@ cudaError_t inv(int tb, int to, const CUtensorMap* tm, const InvArgs& a, cudaStr
 }
 }  // namespace
 
+// The two-pass separable comparator: the row pass and the column pass (fp32 only).
+template <int WV>
+cudaError_t twopass(int mode, int ti, int tb, const CUtensorMap& tm, const FwdArgs& a,
+                    cudaStream_t s) {
+    if (ti != DT_F32 || tb != DT_F32) return cudaErrorNotSupported;
+    if (mode == MODE_ROWS) return launch_forward_t<WV, MODE_ROWS, float, float, float>(tm, a, s);
+    return launch_forward_t<WV, MODE_COLS, float, float, float>(tm, a, s);
+}
+
 cudaError_t launch_fwd_dd(int wavelet, int mode, int ti, int tb, const CUtensorMap& tm,
                           const FwdArgs& a, cudaStream_t s) {
+    if (mode == MODE_ROWS || mode == MODE_COLS) {
+        if (wavelet == WV_DD97) return twopass<WV_DD97>(mode, ti, tb, tm, a, s);
+        if (wavelet == WV_DD137) return twopass<WV_DD137>(mode, ti, tb, tm, a, s);
+        return cudaErrorNotSupported;
+    }
     if (mode != MODE_NONSEP) return cudaErrorNotSupported;
     if (wavelet == WV_DD97) return fwd<WV_DD97>(ti, tb, tm, a, s);
     if (wavelet == WV_DD137) return fwd<WV_DD137>(ti, tb, tm, a, s);

@@ -1278,51 +1278,153 @@ struct InvPredictNS4 {
     }
 };
 
+// The two-pass separable comparator for the four-tap wavelets: the row pass applies P then U
+// along each pixel row (lag 0); the column pass applies P* (lag 2) then U* (lag 1 with four taps,
+// lag 0 with two, the existing UpdateCol) along the columns.
+template <int WV>
+__device__ __forceinline__ void rows_only_dd(QRow<float>& r) {
+    float pa[kQ], pc[kQ], ub[kQ], ue[kQ];
+    predict_h4(r.a, kDDp0, kDDp1, pa);
+    predict_h4(r.c, kDDp0, kDDp1, pc);
+#pragma unroll
+    for (int q = 0; q < kQ; ++q) {
+        r.b[q] += pa[q];
+        r.e[q] += pc[q];
+    }
+    const float u0 = WV == WV_DD97 ? 0.25f : kDD137u0;
+    const float u1 = WV == WV_DD97 ? 0.f : kDD137u1;
+    update_h4(r.b, u0, u1, ub);
+    update_h4(r.e, u0, u1, ue);
+#pragma unroll
+    for (int q = 0; q < kQ; ++q) {
+        r.a[q] += ub[q];
+        r.c[q] += ue[q];
+    }
+}
+
+// P* along the columns with four taps: push(row n + 2) returns row n (lag 2).
+struct PredictCol4 {
+    float a[3][kQ], b[3][kQ];  // rows n-1, n, n+1: the even pixel rows (LL, HL positions)
+    float c[2][kQ], e[2][kQ];  // rows n, n+1: the odd pixel rows
+    __device__ __forceinline__ void init() {
+#pragma unroll
+        for (int q = 0; q < kQ; ++q) {
+            a[0][q] = a[1][q] = a[2][q] = b[0][q] = b[1][q] = b[2][q] = 0.f;
+            c[0][q] = c[1][q] = e[0][q] = e[1][q] = 0.f;
+        }
+    }
+    __device__ __forceinline__ void push(const QRow<float>& y, QRow<float>& o) {
+#pragma unroll
+        for (int q = 0; q < kQ; ++q) {
+            o.a[q] = a[1][q];
+            o.b[q] = b[1][q];
+            o.c[q] = c[0][q] + tap4(a[1][q], a[2][q], a[0][q], y.a[q], kDDp0, kDDp1);
+            o.e[q] = e[0][q] + tap4(b[1][q], b[2][q], b[0][q], y.b[q], kDDp0, kDDp1);
+            a[0][q] = a[1][q];
+            a[1][q] = a[2][q];
+            a[2][q] = y.a[q];
+            b[0][q] = b[1][q];
+            b[1][q] = b[2][q];
+            b[2][q] = y.b[q];
+            c[0][q] = c[1][q];
+            c[1][q] = y.c[q];
+            e[0][q] = e[1][q];
+            e[1][q] = y.e[q];
+        }
+    }
+};
+
+// U* along the columns with four taps: push(row i + 1) returns row i (lag 1).
+struct UpdateCol4 {
+    float c[3][kQ], e[3][kQ];  // rows i-2, i-1, i: the odd pixel rows after P*
+    float a1[kQ], b1[kQ];      // row i: the even pixel rows
+    __device__ __forceinline__ void init() {
+#pragma unroll
+        for (int q = 0; q < kQ; ++q) {
+            c[0][q] = c[1][q] = c[2][q] = e[0][q] = e[1][q] = e[2][q] = 0.f;
+            a1[q] = b1[q] = 0.f;
+        }
+    }
+    __device__ __forceinline__ void push(const QRow<float>& x, QRow<float>& o) {
+#pragma unroll
+        for (int q = 0; q < kQ; ++q) {
+            o.a[q] = a1[q] + tap4(c[1][q], c[2][q], c[0][q], x.c[q], kDD137u0, kDD137u1);
+            o.b[q] = b1[q] + tap4(e[1][q], e[2][q], e[0][q], x.e[q], kDD137u0, kDD137u1);
+            o.c[q] = c[2][q];
+            o.e[q] = e[2][q];
+            c[0][q] = c[1][q];
+            c[1][q] = c[2][q];
+            c[2][q] = x.c[q];
+            e[0][q] = e[1][q];
+            e[1][q] = e[2][q];
+            e[2][q] = x.e[q];
+            a1[q] = x.a[q];
+            b1[q] = x.b[q];
+        }
+    }
+};
+
 // One Deslauriers-Dubuc level (the non-separable scheme only).  9/7: the four-tap predict and
 // the two-tap update (lag 2); 13/7: both four-tap (lag 3).
 template <int MODE>
 struct FwdPipe<WV_DD97, MODE> {
-    static_assert(MODE == MODE_NONSEP, "the Deslauriers-Dubuc wavelets have the fused scheme only");
-    static constexpr int kLag = 2;
+    static_assert(MODE == MODE_NONSEP || MODE == MODE_ROWS || MODE == MODE_COLS,
+                  "the Deslauriers-Dubuc wavelets have the fused scheme and the two-pass one");
+    static constexpr int kLag = MODE == MODE_ROWS ? 0 : 2;
     using C = float;
     PredictNS4 pn;
     UpdateNS<float> un;
+    PredictCol4 pcol;
+    UpdateCol<float> ucol;
     float ll_add;
     __device__ __forceinline__ void init(float ll_add_ = -0.f) {
         ll_add = ll_add_;
-        pn.init();
-        un.init(0.25f);
+        if constexpr (MODE == MODE_NONSEP) { pn.init(); un.init(0.25f); }
+        if constexpr (MODE == MODE_COLS) { pcol.init(); ucol.init(0.25f); }
     }
     __device__ __forceinline__ void push(QRow<float>& r) {
-        QRow<float> t;
-        pn.push(r, t);
-        un.push(t);
+        if constexpr (MODE == MODE_ROWS) {
+            rows_only_dd<WV_DD97>(r);
+            return;
+        } else {
+            QRow<float> t;
+            if constexpr (MODE == MODE_NONSEP) { pn.push(r, t); un.push(t); }
+            if constexpr (MODE == MODE_COLS) { pcol.push(r, t); ucol.push(t); }
 #pragma unroll
-        for (int q = 0; q < kQ; ++q) t.a[q] += ll_add;
-        r = t;
+            for (int q = 0; q < kQ; ++q) t.a[q] += ll_add;
+            r = t;
+        }
     }
 };
 
 template <int MODE>
 struct FwdPipe<WV_DD137, MODE> {
-    static_assert(MODE == MODE_NONSEP, "the Deslauriers-Dubuc wavelets have the fused scheme only");
-    static constexpr int kLag = 3;
+    static_assert(MODE == MODE_NONSEP || MODE == MODE_ROWS || MODE == MODE_COLS,
+                  "the Deslauriers-Dubuc wavelets have the fused scheme and the two-pass one");
+    static constexpr int kLag = MODE == MODE_ROWS ? 0 : 3;
     using C = float;
     PredictNS4 pn;
     UpdateNS4 un;
+    PredictCol4 pcol;
+    UpdateCol4 ucol;
     float ll_add;
     __device__ __forceinline__ void init(float ll_add_ = -0.f) {
         ll_add = ll_add_;
-        pn.init();
-        un.init(kDD137u0, kDD137u1);
+        if constexpr (MODE == MODE_NONSEP) { pn.init(); un.init(kDD137u0, kDD137u1); }
+        if constexpr (MODE == MODE_COLS) { pcol.init(); ucol.init(); }
     }
     __device__ __forceinline__ void push(QRow<float>& r) {
-        QRow<float> t, o;
-        pn.push(r, t);
-        un.push(t, o);
+        if constexpr (MODE == MODE_ROWS) {
+            rows_only_dd<WV_DD137>(r);
+            return;
+        } else {
+            QRow<float> t, o;
+            if constexpr (MODE == MODE_NONSEP) { pn.push(r, t); un.push(t, o); }
+            if constexpr (MODE == MODE_COLS) { pcol.push(r, t); ucol.push(t, o); }
 #pragma unroll
-        for (int q = 0; q < kQ; ++q) o.a[q] += ll_add;
-        r = o;
+            for (int q = 0; q < kQ; ++q) o.a[q] += ll_add;
+            r = o;
+        }
     }
 };
 

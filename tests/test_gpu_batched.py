@@ -191,15 +191,16 @@ def test_large_image_plan_many_row_blocks(wavelet, dtype):
         assert torch.equal(o, D.inverse(c))
 
 
+@pytest.mark.parametrize("wavelet", ["cdf97", "dd137"])
 @pytest.mark.parametrize("bdt", [D.DT_BF16, D.DT_F16])
-def test_inverse_plan_16bit_bands(bdt):
+def test_inverse_plan_16bit_bands(bdt, wavelet):
     """Inverse plans read 16-bit detail bands (fp32 LL) and reconstruct fp32 images bit for bit
     as the single-image inverse does."""
     imgs = _images(SIZES[:12], torch.float32, 19)
-    plan, coeffs = D.plan_forward(imgs, "cdf97", 4, band_dtype=bdt)
+    plan, coeffs = D.plan_forward(imgs, wavelet, 4, band_dtype=bdt)
     plan.run()
     outs = [torch.empty_like(x) for x in imgs]
-    inv = D.Plan(outs, coeffs, "cdf97", 4, "inverse", bdt)
+    inv = D.Plan(outs, coeffs, wavelet, 4, "inverse", bdt)
     inv.run()
     torch.cuda.synchronize()
     assert D.check_status(inv.workspace) == 0

@@ -55,6 +55,18 @@ def test_float_separable(scheme, wavelet, H, W):
                      (scheme, wavelet, H, W, lv))
 
 
+@pytest.mark.parametrize("wavelet", ["dd97", "dd137"])
+@pytest.mark.parametrize("H,W", SIZES + [(1030, 1101)])
+def test_dd_two_pass(wavelet, H, W):
+    """The two-pass comparator of the four-tap wavelets (row kernel, then column kernel)."""
+    rng = np.random.default_rng(H + 19 * W)
+    x = rng.uniform(0, 255, (H, W)).astype(np.float32)
+    for lv in sorted({1, min(5, D.max_levels(H, W))}):
+        c = D.forward(to_gpu(x, torch.float32), wavelet, lv, scheme="sep_twopass")
+        assert_bands(gpu_bands(c), O.forward(x.astype(np.float64), wavelet, lv, "rows"),
+                     FLOAT_TOL, ("sep_twopass", wavelet, H, W, lv))
+
+
 def test_full_size_8192_separable_matches_nonseparable():
     """At the benchmark's size every scheme computes the same transform."""
     x = I.field(8192, 8192, I.seed_for(1))

@@ -41,7 +41,8 @@ def _static_forward(lib, x: torch.Tensor, wavelet: int, levels: int, bdt: int) -
 
 @pytest.mark.parametrize("wavelet,dtype,band", [(0, torch.int32, torch.int32),
                                                  (2, torch.float32, torch.float32),
-                                                 (2, torch.float32, torch.bfloat16)])
+                                                 (2, torch.float32, torch.bfloat16),
+                                                 (4, torch.float32, torch.float32)])
 def test_static_matches_workspace_entry_point_two_calls(lib, wavelet, dtype, band):
     """Both entry points run the same kernels on the same input, so the coefficients must be the
     same bits; any difference would come from the scratch (an aliased or stale LL plane).  The
