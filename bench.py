@@ -291,15 +291,31 @@ def run_only(args, D, dev, x_f32, x_i32, flush, stream):
         "conv_cdf97": ("cdf97", x_f32, LEVELS, False, "conv"),
         "plan_cdf97": ("cdf97", x_f32, LEVELS, False, "plan"),
         "plan_cdf53_int": ("cdf53_int", x_i32, LEVELS, False, "plan"),
+        "batch_plan_cdf97": ("cdf97", x_f32, 4, False, "batch_plan"),
+        "batch_plan_cdf53_int": ("cdf53_int", x_i32, 4, False, "batch_plan"),
     }[args.only]
     if args.levels:
         lv = args.levels
     bdt = D.TORCH_DT[x.dtype]
     out = torch.empty_like(x)
+    ab = alg_bytes(H, W, lv)
     if scheme == "plan":
         # the same image through a one-image plan: all levels in one persistent launch
         plan, (c,) = D.plan_forward([x], wv, lv)
         ws = plan.workspace
+
+        def step():
+            plan.run()
+    elif scheme == "batch_plan":
+        # the default run's 512 uneven images (or the first --images of them) through one plan
+        # (default tile rows, no autotuner launches before the timed ones)
+        from paper_1708_07853_gb300 import inputs as I
+        sizes = I.batch_sizes(512, I.seed_for(3))[:args.images]
+        imgs = [I.field_device(h, w, I.seed_for(3, k), dev).to(x.dtype)
+                for k, (h, w) in enumerate(sizes)]
+        plan, _ = D.plan_forward(imgs, wv, lv)
+        ws = plan.workspace
+        ab = sum(alg_bytes(h, w, lv) for h, w in sizes)
 
         def step():
             plan.run()
@@ -327,7 +343,8 @@ def run_only(args, D, dev, x_f32, x_i32, flush, stream):
     torch.cuda.synchronize()
     ms = float(np.mean([s.elapsed_time(e) for s, e in evs]))
     print(json.dumps({"only": args.only, "ms": ms, "levels": lv,
-                      "gb_s": alg_bytes(H, W, lv) / (ms * 1e-3) / 1e9,
+                      "gb_s": ab / (ms * 1e-3) / 1e9,
+                      "plan": plan.info() if scheme in ("plan", "batch_plan") else None,
                       "status": D.check_status(ws)}), flush=True)
 
 
@@ -584,10 +601,13 @@ def main():
     ap.add_argument("--only", default=None,
                     choices=["fwd_l1_cdf97", "fwd_cdf97", "inv_cdf97", "fwd_cdf53_int",
                              "inv_cdf53_int", "fwd_dd137", "inv_dd137", "twopass_cdf97", "sepfused_cdf97", "adapted_cdf97",
-                             "conv_cdf97", "plan_cdf97", "plan_cdf53_int"],
+                             "conv_cdf97", "plan_cdf97", "plan_cdf53_int", "batch_plan_cdf97",
+                             "batch_plan_cdf53_int"],
                     help="run one case only (for profiler captures); prints a short line")
     ap.add_argument("--levels-table", action="store_true",
                     help="8192x8192: per-level forward and inverse times of each wavelet")
+    ap.add_argument("--images", type=int, default=512,
+                    help="with --only batch_plan_*: the first N images of the 512-image batch")
     ap.add_argument("--levels", type=int, default=0,
                     help="with --only: decomposition levels instead of the case's own")
     args = ap.parse_args()
