@@ -17,7 +17,7 @@ from oracle import oracle as O
 from paper_1708_07853_gb300 import dwt2 as D
 from paper_1708_07853_gb300 import inputs as I
 
-from test_gpu_parity import FLOAT_TOL, gpu_bands
+from test_gpu_parity import FLOAT_TOL, assert_bands, gpu_bands
 
 pytestmark = pytest.mark.gpu
 
@@ -206,3 +206,44 @@ def test_inverse_plan_16bit_bands(bdt, wavelet):
     assert D.check_status(inv.workspace) == 0
     for o, c in zip(outs, coeffs):
         assert torch.equal(o, D.inverse(c, img_dtype=torch.float32))
+
+
+def test_full_batch_512_uneven_against_oracle(tmp_path):
+    """The batching workload at full size, in the benchmark's launch configuration: the 512
+    seeded sizes (each side log-uniform on [63, 4096]), 4 levels, one plan autotuned into a fresh
+    tune cache.  Every image equals the single-image calls bit for bit; sampled images (the
+    largest, the smallest, the median, the largest whose rows TMA can address and three with
+    widths that are not a multiple of 4, which take the plain-load path) are checked against the
+    oracle: bit-exact for the reversible 5/3,
+    within the fp32 bound for 9/7.  The sampled images get their content from the host-side
+    generator (the oracle's input); the others are drawn on the device."""
+    sizes = I.batch_sizes(512, I.seed_for(3))
+    area = np.array([h * w for h, w in sizes])
+    order = np.argsort(area, kind="stable")
+    odd = [k for k, (h, w) in enumerate(sizes) if w % 4][::97][:3]
+    aligned = max((k for k, (h, w) in enumerate(sizes) if w % 4 == 0), key=lambda k: area[k])
+    picks = sorted({int(order[-1]), int(order[0]), int(order[len(order) // 2]), aligned, *odd})
+    host = {k: I.field(*sizes[k], I.seed_for(3, k)) for k in picks}
+    for wavelet, dtype in (("cdf53_int", torch.int32), ("cdf97", torch.float32)):
+        imgs = [torch.from_numpy(host[k]).cuda().to(dtype) if k in host else
+                I.field_device(h, w, I.seed_for(3, k), "cuda").to(dtype)
+                for k, (h, w) in enumerate(sizes)]
+        plan, coeffs = D.plan_forward(imgs, wavelet, 4,
+                                      tune_cache=str(tmp_path / f"tune_{wavelet}.txt"))
+        plan.run()
+        torch.cuda.synchronize()
+        assert D.check_status(plan.workspace) == 0
+        for x, c in zip(imgs, coeffs):
+            _same(c, D.forward(x, wavelet, 4))
+        for k in picks:
+            x = host[k]
+            if wavelet == "cdf53_int":
+                want = O.forward(x.astype(np.int64), wavelet, 4)
+                tol = 0
+            else:
+                want = O.forward(x.astype(np.float64), wavelet, 4)
+                tol = FLOAT_TOL
+            assert_bands(gpu_bands(coeffs[k]), want, tol, (wavelet, k, sizes[k]))
+        plan.close()
+        del imgs, coeffs, plan
+        torch.cuda.empty_cache()

@@ -168,9 +168,12 @@ def test_full_size_8192_int53_five_levels():
     assert torch.equal(r, t)
 
 
-def _full_size_float(x: np.ndarray, what: str):
+def _full_size_float(x: np.ndarray, what: str, storage16: bool = False):
     """Forward against the oracle, inverse of the oracle's coefficients against the oracle's
-    inverse, and the GPU round trip against x: every element, bound FLOAT_TOL."""
+    inverse, and the GPU round trip against x: every element, bound FLOAT_TOL.  With storage16,
+    also the forward with bf16 and fp16 band storage against the same oracle coefficients: per
+    element FLOAT_TOL + |v| 2^-8 (bf16) or |v| 2^-10 (fp16), the rounding of the stored value
+    (the final LL stays fp32, bound FLOAT_TOL)."""
     H, W = x.shape
     t = to_gpu(x, torch.float32)
     want = O.forward(x.astype(np.float64), "cdf97", 5)
@@ -187,6 +190,18 @@ def _full_size_float(x: np.ndarray, what: str):
     want_x = O.inverse(want, H, W, "cdf97", 5)
     err = np.abs(r2 - want_x).max()
     assert err <= FLOAT_TOL, ("inv", what, err)
+    del r2, cc, want_x
+    if storage16:
+        for bdt, rel in ((torch.bfloat16, 2.0 ** -8), (torch.float16, 2.0 ** -10)):
+            c16 = D.forward(t, "cdf97", 5, band_dtype=bdt)
+            for k, (v, w) in enumerate(zip(c16.band_views(), want)):
+                assert v.dtype == (torch.float32 if k == 0 else bdt)
+                if w.size == 0:
+                    continue
+                g = v.float().cpu().numpy().astype(np.float64)
+                tol = FLOAT_TOL + (0.0 if k == 0 else rel) * np.abs(w)
+                assert (np.abs(g - w) <= tol).all(), ("fwd 16-bit", what, str(bdt), k)
+            del c16
 
 
 def test_full_size_8192_cdf97_five_levels():
@@ -196,8 +211,8 @@ def test_full_size_8192_cdf97_five_levels():
 
 def test_full_size_16384_cdf97_five_levels():
     """16384 x 16384 field plus uniform noise in [0, 255], CDF 9/7 fp32, 5 levels (the band
-    storage workload's fp32 case)."""
-    _full_size_float(I.field_plus_noise(16384, 16384, I.seed_for(3)), "16384 97")
+    storage workload: fp32, bf16 and fp16 band storage)."""
+    _full_size_float(I.field_plus_noise(16384, 16384, I.seed_for(3)), "16384 97", storage16=True)
 
 
 def test_constant_image_exact_with_level_shift():
