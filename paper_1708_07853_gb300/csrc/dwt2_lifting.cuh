@@ -1101,22 +1101,55 @@ __device__ __forceinline__ void left_k(const C (&v)[kQ], C (&l)[kQ]) {
         l[q] = q - K >= 0 ? v[q - K] : __shfl_up_sync(kFull, v[q - K + kQ], 1);
 }
 
-// P along a row: p0 (v[m] + v[m+1]) + p1 (v[m-1] + v[m+2]).
+// v at quads m + 1 and m + 2 (or m - 1 and m - 2) of each of a lane's two quads, taking the
+// shuffle the two share once: 2 shuffles instead of 3.
+template <typename C>
+__device__ __forceinline__ void right_12(const C (&v)[kQ], C (&r1)[kQ], C (&r2)[kQ]) {
+    static_assert(kQ == 2, "two quads per lane");
+    const C s = __shfl_down_sync(kFull, v[0], 1);  // quad m + 2 of quad 0, m + 1 of quad 1
+    r1[0] = v[1];
+    r1[1] = s;
+    r2[0] = s;
+    r2[1] = __shfl_down_sync(kFull, v[1], 1);
+}
+template <typename C>
+__device__ __forceinline__ void left_12(const C (&v)[kQ], C (&l1)[kQ], C (&l2)[kQ]) {
+    static_assert(kQ == 2, "two quads per lane");
+    const C s = __shfl_up_sync(kFull, v[1], 1);  // quad m - 1 of quad 0, m - 2 of quad 1
+    l1[0] = s;
+    l1[1] = v[0];
+    l2[0] = __shfl_up_sync(kFull, v[0], 1);
+    l2[1] = s;
+}
+
+// P along a row: p0 (v[m] + v[m+1]) + p1 (v[m-1] + v[m+2]).  kShared takes the neighbours with
+// right_12 (3 shuffles instead of 4, the same values).  The 13/7 inverse steps use it; in the
+// 13/7 forward, whose registers are capped for 4 CTAs per SM, it spilled (level 1 111 -> 129 us).
+template <bool kShared = false>
 __device__ __forceinline__ void predict_h4(const float (&v)[kQ], float p0, float p1,
                                            float (&o)[kQ]) {
     float r1[kQ], r2[kQ], l1[kQ];
-    right_k<1>(v, r1);
-    right_k<2>(v, r2);
+    if constexpr (kShared) {
+        right_12(v, r1, r2);
+    } else {
+        right_k<1>(v, r1);
+        right_k<2>(v, r2);
+    }
     left_k<1>(v, l1);
 #pragma unroll
     for (int q = 0; q < kQ; ++q) o[q] = fmaf(p0, v[q] + r1[q], p1 * (l1[q] + r2[q]));
 }
-// U along a row: u0 (v[m-1] + v[m]) + u1 (v[m-2] + v[m+1]).
+// U along a row: u0 (v[m-1] + v[m]) + u1 (v[m-2] + v[m+1]).  kShared as in predict_h4.
+template <bool kShared = false>
 __device__ __forceinline__ void update_h4(const float (&v)[kQ], float u0, float u1,
                                           float (&o)[kQ]) {
     float l1[kQ], l2[kQ], r1[kQ];
-    left_k<1>(v, l1);
-    left_k<2>(v, l2);
+    if constexpr (kShared) {
+        left_12(v, l1, l2);
+    } else {
+        left_k<1>(v, l1);
+        left_k<2>(v, l2);
+    }
     right_k<1>(v, r1);
 #pragma unroll
     for (int q = 0; q < kQ; ++q) o[q] = fmaf(u0, l1[q] + v[q], u1 * (l2[q] + r1[q]));
@@ -1201,7 +1234,8 @@ struct UpdateNS4 {
     }
 };
 
-// Undoes UpdateNS4.  push(row i + 1) returns row i (lag 1).
+// Undoes UpdateNS4.  push(row i + 1) returns row i (lag 1).  kShared as in InvPredictNS4.
+template <bool kShared>
 struct InvUpdateNS4 {
     float u0, u1;
     float c[3][kQ], e[3][kQ];  // rows i-2, i-1, i: stored LH and HH
@@ -1220,8 +1254,8 @@ struct InvUpdateNS4 {
 #pragma unroll
         for (int q = 0; q < kQ; ++q)
             hl[q] = b1[q] - tap4(e[1][q], e[2][q], e[0][q], x.e[q], u0, u1);
-        update_h4(hl, u0, u1, uh);
-        update_h4(e[2], u0, u1, ue);
+        update_h4<kShared>(hl, u0, u1, uh);
+        update_h4<kShared>(e[2], u0, u1, ue);
 #pragma unroll
         for (int q = 0; q < kQ; ++q) {
             o.a[q] = a1[q] - tap4(c[1][q], c[2][q], c[0][q], x.c[q], u0, u1) - uh[q];
@@ -1240,7 +1274,13 @@ struct InvUpdateNS4 {
     }
 };
 
-// Undoes PredictNS4.  push(row i + 2) returns row i (lag 2).
+// Undoes PredictNS4.  push(row i + 2) returns row i (lag 2).  kShared: the horizontal
+// neighbours with one shuffle fewer (predict_h4, update_h4), the same values.  Measured on
+// GB300, 8192^2, 5 levels, with it in both inverse steps: the 13/7 inverse with fp32 bands
+// 167.4 -> 164.3-165.3 us, but with bf16 bands 179.7 -> 181.7 us (a 4-byte spill under the
+// 96-register bound), and the 9/7 inverse, whose update is the two-tap one, 141.2 -> 143.0 us.
+// So only the 13/7 inverse with 32-bit bands takes it (InvPipeOf).
+template <bool kShared>
 struct InvPredictNS4 {
     float a[3][kQ], b[3][kQ];  // rows i-1, i, i+1: LL and stored HL
     float c[2][kQ], e[2][kQ];  // rows i, i+1: stored LH and HH
@@ -1256,8 +1296,8 @@ struct InvPredictNS4 {
 #pragma unroll
         for (int q = 0; q < kQ; ++q)
             lh[q] = c[0][q] - tap4(a[1][q], a[2][q], a[0][q], y.a[q], kDDp0, kDDp1);
-        predict_h4(a[1], kDDp0, kDDp1, pa);
-        predict_h4(lh, kDDp0, kDDp1, pl);
+        predict_h4<kShared>(a[1], kDDp0, kDDp1, pa);
+        predict_h4<kShared>(lh, kDDp0, kDDp1, pl);
 #pragma unroll
         for (int q = 0; q < kQ; ++q) {
             o.a[q] = a[1][q];
@@ -1433,7 +1473,7 @@ struct InvPipe<WV_DD97> {
     static constexpr int kLag = 2;
     using C = float;
     InvUpdateNS<float> iu;
-    InvPredictNS4 ip;
+    InvPredictNS4<false> ip;
     __device__ __forceinline__ void init() {
         iu.init(0.25f);
         ip.init();
@@ -1446,12 +1486,12 @@ struct InvPipe<WV_DD97> {
     }
 };
 
-template <>
-struct InvPipe<WV_DD137> {
+template <bool kShared>
+struct InvPipeDD137 {
     static constexpr int kLag = 3;
     using C = float;
-    InvUpdateNS4 iu;
-    InvPredictNS4 ip;
+    InvUpdateNS4<kShared> iu;
+    InvPredictNS4<kShared> ip;
     __device__ __forceinline__ void init() {
         iu.init(kDD137u0, kDD137u1);
         ip.init();
@@ -1462,6 +1502,21 @@ struct InvPipe<WV_DD137> {
         ip.push(t, o);
         r = o;
     }
+};
+
+template <>
+struct InvPipe<WV_DD137> : InvPipeDD137<false> {};
+
+// The inverse pipeline of the streaming kernel whose band planes are of type TB: InvPipe, but
+// the 13/7 with 32-bit bands takes the shared-shuffle steps (see InvPredictNS4).  Both forms give
+// the same bits.
+template <int WV, typename TB>
+struct InvPipeOf {
+    using type = InvPipe<WV>;
+};
+template <typename TB>
+struct InvPipeOf<WV_DD137, TB> {
+    using type = InvPipeDD137<sizeof(TB) == 4>;
 };
 
 }  // namespace dwt2

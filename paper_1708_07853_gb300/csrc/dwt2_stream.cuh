@@ -1122,7 +1122,7 @@ __global__ void __launch_bounds__(cta_threads<NW>(), min_ctas<WV, NW>())
     constexpr int kHaloLanes = kHaloQ / kQ;
     static_assert(inv_tma_x_aligned<NW, TB, WV>() && inv_tma_x_aligned<NW, TL, WV>(),
                   "TMA x coordinates of this CTA width misaligned");
-    using Pipe = std::conditional_t<ADJ, AdjFwdPipe<WV>, InvPipe<WV>>;
+    using Pipe = std::conditional_t<ADJ, AdjFwdPipe<WV>, typename InvPipeOf<WV, TB>::type>;
     using C = typename Pipe::C;
     constexpr size_t kStageBytes = size_t(kBRow) * (sizeof(TL) + 3 * sizeof(TB));
     constexpr int kS = inv_stages<WV>();
