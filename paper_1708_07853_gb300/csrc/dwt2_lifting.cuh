@@ -1078,9 +1078,9 @@ struct InvPipe<WV_CDF53_INT> {
 // p1 = 1/16.  The update of an even sample reads its odd neighbours at m-1, m (u0) and m-2, m+1
 // (u1): 1/4, 0 for 9/7 and 9/32, -1/32 for 13/7.  No scaling.  The spatial steps are those of
 // Eq. 5 with these P, P*, U, U*, evaluated in the factored form of the two-tap steps above
-// (HH += P*(HL after P) + P(LH); LL += U(HL) + U*(LH after U)).  A warp's window needs two halo
-// lanes on each side (the reach of a level is three quads), so these wavelets run with a
-// narrower output window (halo_q).
+// (HH += P*(HL after P) + P(LH); LL += U(HL) + U*(LH after U)).  A level of the 13/7 reaches
+// three quads each way, so its warp windows keep two halo lanes on each side (a narrower output
+// window, halo_q); the 9/7, with the two-tap update, reaches two, as the CDF wavelets do.
 // =============================================================================================
 constexpr float kDDp0 = -9.0f / 16.0f;
 constexpr float kDDp1 = 1.0f / 16.0f;

@@ -108,7 +108,7 @@ static int plan_cta_q_w(const dwt2_plan* P) {
     return cta_q<persist_inv_nw<float, float>(), WV>();
 }
 int plan_cta_q(const dwt2_plan* P) {
-    return is_dd(P->wavelet) ? plan_cta_q_w<WV_DD97>(P) : plan_cta_q_w<WV_CDF97>(P);
+    return P->wavelet == WV_DD137 ? plan_cta_q_w<WV_DD137>(P) : plan_cta_q_w<WV_CDF97>(P);
 }
 
 // Upper bound on the quad rows per tile at level j, for `rows` at level 1: halved at every level

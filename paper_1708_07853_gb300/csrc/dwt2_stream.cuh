@@ -32,11 +32,13 @@ constexpr int kWarpOut = kWarpQ - 2 * kHQ;  // output quads per warp (30 lanes)
 // busy) but 3 strips of 180 (9 of 9), and the batched 3-level transforms of 192 such images ran
 // 21% faster with it (pick_nw chooses per launch).  The stage rows are sized for the wide CTA.
 constexpr int kMaxNW = 4;
-// The Deslauriers-Dubuc wavelets reach three quads per level, so their warp windows keep two
-// halo lanes on each side (56 output quads per warp instead of 60).
+// Halo quads on each side of a warp window: the reach of one level.  The CDF wavelets and the
+// Deslauriers-Dubuc 9/7 reach two quads each way (9/7: the four-tap predict m-1 .. m+2, then the
+// two-tap update m-1, m), one halo lane; the 13/7's four-tap update (m-2 .. m+1) makes three, so
+// its windows keep two halo lanes on each side (56 output quads per warp instead of 60).
 template <int WV>
-constexpr int halo_q() {  // halo quads on each side of a warp window
-    return is_dd(WV) ? 2 * kQ : kHQ;
+constexpr int halo_q() {
+    return WV == WV_DD137 ? 2 * kQ : kHQ;
 }
 template <int WV>
 constexpr int warp_out() {  // output quads per warp
