@@ -77,3 +77,37 @@ def test_padding_stays_zero_and_layout_roundtrip():
     A.idwt2(cr, H, W, "cdf97", lv).pow(2).sum().backward()
     assert (cr.grad[~mask] == 0).all()
     assert torch.equal(A.padding_index(H, W, lv, "cuda"), torch.nonzero(~mask[0]).ravel())
+
+
+def test_autograd_full_size_64x3x1024():
+    """The differentiation workload at full size, as the benchmark runs it: 64 x 3 images of
+    1024 x 1024 in [0, 1], 3 levels of 9/7, one forward + backward through the autograd
+    Functions (batched entry points).  Three sampled images (first, middle, last) are checked
+    against the fp64 oracle gradient; they get their content from the host-side generator,
+    the others are drawn on the device."""
+    B, C, H, W, lv = 64, 3, 1024, 1024, 3
+    n_img = B * C
+    picks = (0, n_img // 2, n_img - 1)
+    host = {k: I.field(H, W, I.seed_for(4, k)) / 255.0 for k in picks}
+    x = torch.empty((B, C, H, W), device="cuda")
+    flat = x.view(-1, H, W)
+    for k in range(n_img):
+        if k in host:
+            flat[k] = torch.from_numpy(host[k].astype(np.float32)).cuda()
+        else:
+            flat[k] = I.field_device(H, W, I.seed_for(4, k), "cuda") / 255.0
+    x.requires_grad_(True)
+    loss, c = _loss(x, "cdf97", lv)
+    loss.backward()
+    views = A.band_views(c, H, W, lv)
+    N = x.numel()
+    for k in picks:
+        got = x.grad.view(-1, H, W)[k].cpu().numpy().astype(np.float64)
+        xi = host[k].astype(np.float32).astype(np.float64)
+        signs = [np.zeros((v.shape[-2], v.shape[-1])) for v in views[:1]] + \
+                [np.sign(v.reshape(n_img, *v.shape[-2:])[k].detach().cpu().numpy()).astype(np.float64)
+                 for v in views[1:]]
+        g = oracle_grad(xi, signs, "cdf97", lv)
+        g1 = O.forward_adjoint(signs, H, W, "cdf97", lv)
+        want = g1 + (g - g1) * (xi.size / N)
+        assert np.abs(got - want).max() <= 1e-4 * max(1.0, np.abs(want).max()), k
