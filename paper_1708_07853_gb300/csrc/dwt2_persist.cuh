@@ -141,9 +141,16 @@ constexpr bool persist_vec() {
     return WV == WV_CDF53_INT;
 }
 
-// Ring depth of the persistent kernels: 8 stages for every wavelet (the single-image depths, 6
-// for the 9/7 forward and 12 for the 5/3, made the 512-image batch 1.4% and 0.4% slower).
+// Ring depth of the persistent kernels: 8 stages (the single-image depths, 6 for the 9/7 forward
+// and 12 for the 5/3, made the 512-image batch 1.4% and 0.4% slower), 10 for the 9/7 forward
+// data flow.  Same box, 512-image batch, default tile rows: 9/7 1.1669 -> 1.1615 ms with 10
+// stages (its 5 CTAs per SM are set by registers); the int 5/3 1.0018 -> 1.0368 ms, as 10 stages
+// of shared memory leave it 5 CTAs per SM instead of 6.
 constexpr int kPersistStages = 8;
+template <int WV>
+constexpr int persist_fwd_stages() {
+    return WV == WV_CDF97 ? 10 : kPersistStages;
+}
 
 // Per-tile arguments.  Each warp copies its tile's unit arguments into a local variable once per
 // tile; every helper that reads them is inlined, so the compiler keeps the fields the per-row
@@ -202,7 +209,7 @@ __global__ void __launch_bounds__(cta_threads<kPersistFwdNW>(), persist_min_ctas
     using Pipe = std::conditional_t<kAdj, AdjInvPipe<WV>, FwdPipe<WV, MODE_NONSEP>>;
     using C = typename Pipe::C;
     constexpr int kVH = vhalo<Pipe, kAdj>();
-    constexpr int kS = kPersistStages;
+    constexpr int kS = persist_fwd_stages<WV>();
     extern __shared__ __align__(128) uint8_t smem_raw[];
     const Ring<kS> ring = make_ring<kS>(smem_raw, size_t(2) * kSRow * sizeof(TI));
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;

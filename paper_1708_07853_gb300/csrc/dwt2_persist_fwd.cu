@@ -8,7 +8,7 @@ namespace {
 template <int WV, int MODE, typename TI, typename TB, typename TL>
 cudaError_t go(const PersistArgs<FwdUnit>& p, int ctas_per_sm, cudaStream_t st, int* occ_out) {
     auto k = k_forward_persistent<WV, MODE, TI, TB, TL>;
-    constexpr size_t smem = fwd_smem_bytes<TI, kPersistStages>();
+    constexpr size_t smem = fwd_smem_bytes<TI, persist_fwd_stages<WV>()>();
     static const int occ = configure(k, cta_threads<kPersistFwdNW>(), smem);
     if (occ_out) {
         *occ_out = occ;
